@@ -9,7 +9,8 @@ translation invariance costs no extra inversions.
 
 Readings (the paper gives the factors only):
 
-* noise vector n has entries xi_n(x, alpha, a) = (s_re + i s_im) / sqrt(2) with
+* noise vector n has entries xi_n(x, alpha, a) = (s_re + i s_im) / sqrt(2), the
+  magnitude 1/sqrt(2) being the double nearest to it (sqrt(0.5)), with
   signs s = +-1 drawn by Philox4x64-10 under key (seed, 0) and counter
   (i >> 2, n, 0, 0), i the lexicographic site index: 64-bit word (i & 3) of the
   output block belongs to site i; component c = 3*alpha + a takes its real sign
@@ -68,7 +69,7 @@ def z2_noise(dims, seed: int, n: int) -> np.ndarray:
             bim = (word >> np.uint64(2 * c + 1)) & np.uint64(1)
             sre = 1.0 - 2.0 * bre.astype(np.float64)
             sim = 1.0 - 2.0 * bim.astype(np.float64)
-            out[..., alpha, a] = (sre + 1j * sim) / np.sqrt(2.0)
+            out[..., alpha, a] = (sre + 1j * sim) * np.sqrt(0.5)
     return out
 
 
