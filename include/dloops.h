@@ -1,0 +1,242 @@
+/*
+ * dloops.h - C ABI of the GB300 (sm_103a) disconnected-loop library.
+ *
+ * The library computes disconnected quark loops as in "Exact calculation of
+ * disconnected loops" (Alexandrou, Christaras, O Cais, Strelchenko, Lattice
+ * 2010): repeated inversion of the N_f = 2 Wilson-Dirac matrix
+ * M = 1 - kappa*D (Sec. 2) over point sources or diluted complex Z2 noise
+ * sources (Sec. 2), followed by the loop contraction
+ * L_Gamma(t) = sum_{x in t} Tr[Gamma M^{-1}(x, x)] (Sec. 3, Eq. 2) for local and
+ * Gaussian-smeared sinks, and the truncated-solver-method estimate (Sec. 2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Lattice: dims = {Lx, Ly, Lz, T}; every extent even and in [2, 256].  Site
+ *   index i = x + Lx*(y + Ly*(z + Lz*t)) (x fastest).  Directions mu = 0..3 are
+ *   x, y, z, t.  Space is periodic; the quark fields get the factor t_bc (+1 or
+ *   -1) on hops across the time boundary.
+ * Operator (the paper fixes no convention; this is the standard Wilson form
+ *   with r = 1): (D psi)(x) = sum_mu [(1 - g_mu) U_mu(x) psi(x+mu)
+ *   + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu)], M = 1 - kappa*D, gamma matrices in
+ *   the chiral DeGrand-Rossi basis (g5 = diag(1, 1, -1, -1)).
+ * Gauge field (host): complex128 [V][4 mu][3][3], row-major 3x3 (U[a][b] at
+ *   a*3+b), each complex as two doubles (re, im).
+ * Spinor fields ("canonical", device): complex128 [n_rhs][V][4 spin][3 colour],
+ *   i.e. 24 doubles per site, right-hand sides back to back.  Device pointers
+ *   are caller-owned memory; the library never frees them and keeps no
+ *   reference after the call returns.
+ * Gamma basis (every loop output): 16 matrices in the order 1, g1, g2, g3, g4,
+ *   g5, g5g1, g5g2, g5g3, g5g4, g1g2, g1g3, g1g4, g2g3, g2g4, g3g4.
+ * Loop outputs (host): double [..][16 Gamma][T][2] (re, im), with
+ *   L_Gamma(t) = sum_{x in t} eta(x)^dag Gamma phi(x).
+ * Streams: every call is stream-ordered on the stream given to dl_create;
+ *   calls that return host data synchronise that stream before returning.
+ * Errors: every call returns a dl_status.  On error nothing is written to the
+ *   host outputs; device outputs may be partially written.  No call aborts the
+ *   process or traps on the device; device-side iteration loops are bounded.
+ *   There is no CPU fallback: a missing or unusable GPU is DL_ECUDA.
+ */
+#ifndef DLOOPS_H
+#define DLOOPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dl_status {
+    DL_OK = 0,
+    DL_EINVAL = 1,          /* bad argument (size, pointer, flag, lattice shape) */
+    DL_ENOMEM = 2,          /* device allocation failed */
+    DL_ECUDA = 3,           /* a CUDA runtime call failed (message in dl_last_error) */
+    DL_NOT_CONVERGED = 4,   /* some right-hand side did not reach the tolerance */
+    DL_BREAKDOWN = 5,       /* BiCGStab breakdown (rho, omega or <r0,v> vanished) */
+    DL_NAN = 6,             /* a non-finite value appeared in a solve */
+    DL_ESTATE = 7           /* call out of order (e.g. solve before load_gauge) */
+} dl_status;
+
+/* Precision of the Krylov iteration.  DL_PREC_F64 is a plain double-precision
+ * BiCGStab; F32 and BF16 keep spinors and links in that storage type with FP32
+ * arithmetic inside an FP64 defect-correction loop (true residual, solution
+ * accumulation and final result in FP64).  Sec. 2: the paper's inversions use
+ * mixed-precision CG/BiCGStab. */
+enum { DL_PREC_F64 = 0, DL_PREC_F32 = 1, DL_PREC_BF16 = 2 };
+
+/* Dilution bitmask (Sec. 2): spin (x4 inversions), colour (x3), even-odd
+ * spatial partition (x2), cubic partition (x8: the vertex class
+ * (x&1) + 2(y&1) + 4(z&1) of the elementary 3-cube), time (source on a single
+ * timeslice; no extra inversions). */
+enum { DL_DIL_SPIN = 1, DL_DIL_COLOUR = 2, DL_DIL_EVENODD = 4, DL_DIL_CUBIC = 8, DL_DIL_TIME = 16 };
+
+/* Sink selection for loop contractions (Sec. 2: local and smeared fields). */
+enum { DL_SINK_LOCAL = 1, DL_SINK_SMEARED = 2 };
+
+typedef struct dl_ctx dl_ctx;
+
+typedef struct dl_solve_params {
+    double tol;          /* stop when ||b - M x|| / ||b|| <= tol (FP64 true residual); > 0 */
+    int precision;       /* DL_PREC_* */
+    int max_iter;        /* cap on inner BiCGStab iterations summed over outer cycles */
+    int fixed_iters;     /* > 0: run exactly this many inner iterations, one cycle, no
+                            tolerance test (a deterministic low-precision map, as the
+                            truncated solver method needs); 0: iterate to tol */
+    double delta;        /* inner relative residual reduction per outer cycle (mixed
+                            precision); <= 0 picks 1e-5 (F32) or 3e-3 (BF16) */
+    int max_outer;       /* cap on defect-correction cycles; <= 0 picks 60 */
+    int batch;           /* right-hand sides solved together per launch (1..64, a power
+                            of two for F32/BF16 >= 2); <= 0 picks 16 */
+    int use_graph;       /* capture the inner iteration in CUDA graphs (1) or launch
+                            directly (0) */
+    int chunk;           /* inner iterations per graph launch / convergence poll; <= 0: 8 */
+} dl_solve_params;
+
+typedef struct dl_solve_stats {
+    int status;          /* dl_status of this right-hand side */
+    int iters;           /* inner BiCGStab iterations */
+    int outer;           /* defect-correction cycles */
+    double true_residual;/* ||b - M x|| / ||b||, full lattice, FP64 */
+} dl_solve_stats;
+
+typedef struct dl_smear {
+    double alpha;        /* K = [(1 + alpha H)/(1 + 6 alpha)]^n_iter, H the spatial hop */
+    int n_iter;
+} dl_smear;
+
+/* Timers accumulated by the context (CUDA events around each Wilson-hop
+ * launch when enabled by dl_set_timing). */
+typedef struct dl_timing {
+    double hop_ms[4];        /* per kind: 0 low-precision plain, 1 low-precision fused
+                                (xpay + reductions), 2 FP64 plain, 3 FP64 fused */
+    int64_t hop_launches[4];
+    double hop_bytes[4];     /* algorithmic bytes of those launches */
+    int64_t kernel_launches; /* every kernel this context launched */
+} dl_timing;
+
+/* --- context -------------------------------------------------------------- */
+
+/* Create a context for one lattice on the current CUDA device.
+ * dims: {Lx, Ly, Lz, T}; t_bc: +1 periodic or -1 antiperiodic in time;
+ * cuda_stream: a cudaStream_t (0 = legacy default stream).  *out receives the
+ * context, owned by the caller until dl_destroy. */
+int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_stream);
+int dl_destroy(dl_ctx *ctx);
+/* Message of the last failing call on this thread (static storage). */
+const char *dl_last_error(void);
+const char *dl_status_string(int status);
+
+/* Copy the gauge field U_mu(x) (Sec. 2: the SESAM links; here any SU(3)
+ * field) from host memory (layout above) into the context, which keeps it in
+ * even-odd site-major order in FP64, FP32 and BF16.  check_unitarity != 0
+ * rejects (DL_EINVAL) links with |U U^dag - 1| > 1e-10. */
+int dl_load_gauge(dl_ctx *ctx, const double *host_U, int check_unitarity);
+
+/* Set the hopping parameter kappa of M = 1 - kappa D (Sec. 2: kappa = 0.157). */
+int dl_set_kappa(dl_ctx *ctx, double kappa);
+
+/* Enable (1) or disable (0) CUDA-event timing of Wilson-hop launches; read and
+ * reset with dl_get_timing. */
+int dl_set_timing(dl_ctx *ctx, int enable);
+int dl_get_timing(dl_ctx *ctx, dl_timing *out, int reset);
+
+/* --- sources (Sec. 2) ----------------------------------------------------- */
+
+/* Diluted complex Z2 sources.  For noise vectors n = noise_first ..
+ * noise_first + n_noise - 1, xi_n(x, alpha, a) = (s_re + i s_im)/sqrt(2) with
+ * signs from Philox4x64-10 (key (seed, 0), counter (i >> 2, n, 0, 0); word
+ * i & 3 belongs to site i; bits 2c and 2c+1 of that word give the real and
+ * imaginary sign of component c = 3 alpha + a; a set bit means -1).  Each noise
+ * vector yields K diluted sources P_k xi_n (K from the dilution mask, class
+ * index k = ((k_spin*C + k_colour)*E + k_eo)*Q + k_cubic), written to
+ * dev_out[(n - noise_first)*K + k] in canonical layout (complex128).  With
+ * DL_DIL_TIME only timeslice t0 is kept, or n mod T when t0 < 0.  *n_rhs
+ * (may be NULL) receives n_noise*K.  dev_out must hold n_noise*K*V*12 complex. */
+int dl_make_sources(dl_ctx *ctx, uint64_t seed, int64_t noise_first, int n_noise,
+                    unsigned dilution, int t0, void *dev_out, int64_t *n_rhs);
+
+/* Point sources e_s with s = 12*i + 3*alpha + a for s = first .. first + n - 1
+ * (Sec. 1-2: the exact all-to-all diagonal needs all 12V of them). */
+int dl_make_point_sources(dl_ctx *ctx, int64_t first, int n, void *dev_out);
+
+/* --- solver (Sec. 2) ------------------------------------------------------ */
+
+/* Solve M x_j = b_j for n_rhs right-hand sides (canonical complex128 device
+ * buffers; dev_x may not alias dev_b).  Even-odd preconditioned BiCGStab on
+ * the Schur complement 1 - kappa^2 D_eo D_oe with the precision and batching of
+ * *params (NULL: defaults, tol 1e-10, F32).  stats (host, may be NULL) receives
+ * n_rhs entries.  Returns DL_OK if every right-hand side converged, otherwise
+ * the first failing status (the solutions are still written). */
+int dl_solve(dl_ctx *ctx, const void *dev_b, void *dev_x, int n_rhs,
+             const dl_solve_params *params, dl_solve_stats *stats);
+
+/* Solve M^dag x = b, via M^dag = g5 M g5 (gamma5-hermiticity). */
+int dl_solve_adjoint(dl_ctx *ctx, const void *dev_b, void *dev_x, int n_rhs,
+                     const dl_solve_params *params, dl_solve_stats *stats);
+
+/* --- operators (building blocks, FP64) ------------------------------------ */
+
+/* out = D in (Wilson hopping term, full lattice, FP64), n_rhs fields. */
+int dl_apply_hop(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
+/* out = M in = in - kappa D in. */
+int dl_apply_m(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
+/* out = K in, Gaussian smearing (Sec. 2), restricted to timeslices
+ * [t_lo, t_hi) (other timeslices of out are set to zero). */
+int dl_apply_smear(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs,
+                   const dl_smear *smear, int t_lo, int t_hi);
+/* Per-timeslice spin matrices built from Gamma weights w[j][16][T] (complex,
+ * host): mode 0: out(x) (+)= sum_G w[j][G][t(x)] G^dag in(x);
+ * mode 1: out(x) (+)= sum_G conj(w[j][G][t(x)]) G in(x).  accumulate = 1 adds
+ * to out.  (Used by the loop gradients: the adjoint source and the
+ * direct term.) */
+int dl_apply_gamma_weights(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs,
+                           const double *host_w, int mode, int accumulate);
+
+/* --- loops (Sec. 3, Eq. 2) ------------------------------------------------ */
+
+/* Loop contraction L_Gamma(t) = sum_{x in t} eta(x)^dag Gamma phi(x) for each
+ * pair (eta_j, phi_j), all 16 Gamma, timeslices [t_lo, t_hi) (others 0).
+ * sink: DL_SINK_LOCAL and/or DL_SINK_SMEARED (then eta and phi are both
+ * smeared by K first; smear must be non-NULL).  host_out: double
+ * [n_rhs or 1 if sum_rhs][n_sinks][16][T][2] (local first), FP64 sums. */
+int dl_trace_loops(dl_ctx *ctx, const void *dev_eta, const void *dev_phi, int n_rhs,
+                   int sink, const dl_smear *smear, int t_lo, int t_hi, int sum_rhs,
+                   double *host_out);
+
+/* Exact loops (Sec. 1-2: the all-to-all diagonal): solve the point sources
+ * s = src_first .. src_first + n_src - 1 and accumulate
+ * sum_{x in t} Tr[Gamma M^{-1}(x, x)] restricted to those sources into
+ * host_out[n_sinks][16][T][2] (overwritten).  All 12V sources give the exact
+ * loop.  Smeared sinks use sum over sources of (K e_s)^dag Gamma K M^{-1} e_s. */
+int dl_exact_loops(dl_ctx *ctx, int64_t src_first, int64_t n_src,
+                   const dl_solve_params *params, int sink, const dl_smear *smear,
+                   double *host_out, dl_solve_stats *stats_sum);
+
+/* Truncated solver method (Sec. 2, after Bali et al.): n_lp noise vectors
+ * (indices 0..n_lp-1) solved with *lp, and n_hp further noise vectors
+ * (n_lp..n_lp+n_hp-1) solved with both *hp and *lp;
+ * mean = <L_lp> + <L_hp - L_lp>, var = s^2_lp/n_lp + s^2_diff/n_hp per Gamma
+ * and timeslice, each noise vector summed over its dilution classes, and a
+ * timeslice counted only for the noise vectors whose source covers it.
+ * mean_out, var_out: host double [n_sinks][16][T][2] (var: real variances of
+ * re and im parts).  per_noise_out (may be NULL): host double
+ * [n_lp + 2*n_hp][n_sinks][16][T][2]: LP loops, then HP loops, then LP loops on
+ * the HP ensemble. */
+int dl_tsm_estimate(dl_ctx *ctx, uint64_t seed, int n_lp, int n_hp, unsigned dilution, int t0,
+                    const dl_solve_params *lp, const dl_solve_params *hp,
+                    int sink, const dl_smear *smear,
+                    double *mean_out, double *var_out, double *per_noise_out);
+
+/* --- low-level kernels exposed for measurement ---------------------------- */
+
+/* Apply the even-odd hop D_{p,1-p} (p = out_parity) to an internal batch of
+ * n_rhs random fields in storage precision `precision`, `reps` times, and
+ * return the mean kernel time in *ms (CUDA events) and its algorithmic bytes
+ * per launch in *bytes.  Used to time the Wilson hop alone. */
+int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
+                 double *ms, double *bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DLOOPS_H */

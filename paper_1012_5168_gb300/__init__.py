@@ -1,0 +1,325 @@
+"""GB300 (sm_103a) disconnected quark loops: thin Python binding of ``include/dloops.h``.
+
+The computation ("Exact calculation of disconnected loops", Lattice 2010:
+repeated Wilson-Dirac inversions over point or diluted complex Z2 sources and
+the loop contraction Tr[Gamma M^{-1}(x, x)] per timeslice, Sec. 2-3) runs in
+the CUDA kernels of ``libdloops.so``.  This module only marshals arguments:
+torch tensors supply device memory and the current CUDA stream, numpy arrays
+the host gauge field; every call forwards to the C ABI of the same name.
+
+Field tensors are complex128 CUDA tensors whose memory holds the canonical
+layout ``[n_rhs][V][4 spin][3 colour]`` (for instance shaped
+``(n, T, Lz, Ly, Lx, 4, 3)``, the same order as the numpy arrays of the
+``synthetic`` inputs).  There is no CPU fallback: without the built library
+or a CUDA device every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdloops.so")
+
+# enums of dloops.h
+OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, BREAKDOWN, NAN, ESTATE = range(8)
+PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
+DIL_SPIN, DIL_COLOUR, DIL_EVENODD, DIL_CUBIC, DIL_TIME = 1, 2, 4, 8, 16
+SINK_LOCAL, SINK_SMEARED = 1, 2
+
+GAMMA_NAMES = ("1", "g1", "g2", "g3", "g4", "g5", "g5g1", "g5g2", "g5g3", "g5g4",
+               "g1g2", "g1g3", "g1g4", "g2g3", "g2g4", "g3g4")
+
+# every entry point of the C ABI, as declared in include/dloops.h
+SYMBOLS = (
+    "dl_create", "dl_destroy", "dl_last_error", "dl_status_string", "dl_load_gauge", "dl_set_kappa",
+    "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
+    "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
+    "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop",
+)
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("fixed_iters", ctypes.c_int), ("delta", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("batch", ctypes.c_int), ("use_graph", ctypes.c_int), ("chunk", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("outer", ctypes.c_int),
+                ("true_residual", ctypes.c_double)]
+
+
+class Smear(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("n_iter", ctypes.c_int)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("hop_ms", ctypes.c_double * 4), ("hop_launches", ctypes.c_int64 * 4),
+                ("hop_bytes", ctypes.c_double * 4), ("kernel_launches", ctypes.c_int64)]
+
+
+class DlError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"dloops error {status}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdloops.so (built in-tree by ``paper_1012_5168_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1012_5168_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d, u64, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int64
+    P = ctypes.POINTER
+    sig = {
+        "dl_create": (i, [P(vp), P(i), i, vp]),
+        "dl_destroy": (i, [vp]),
+        "dl_last_error": (ctypes.c_char_p, []),
+        "dl_status_string": (ctypes.c_char_p, [i]),
+        "dl_load_gauge": (i, [vp, vp, i]),
+        "dl_set_kappa": (i, [vp, d]),
+        "dl_set_timing": (i, [vp, i]),
+        "dl_get_timing": (i, [vp, P(Timing), i]),
+        "dl_make_sources": (i, [vp, u64, i64, i, ctypes.c_uint, i, vp, P(i64)]),
+        "dl_make_point_sources": (i, [vp, i64, i, vp]),
+        "dl_solve": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
+        "dl_solve_adjoint": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
+        "dl_apply_hop": (i, [vp, vp, vp, i]),
+        "dl_apply_m": (i, [vp, vp, vp, i]),
+        "dl_apply_smear": (i, [vp, vp, vp, i, P(Smear), i, i]),
+        "dl_apply_gamma_weights": (i, [vp, vp, vp, i, vp, i, i]),
+        "dl_trace_loops": (i, [vp, vp, vp, i, i, P(Smear), i, i, i, vp]),
+        "dl_exact_loops": (i, [vp, i64, i64, P(SolveParams), i, P(Smear), vp, P(SolveStats)]),
+        "dl_tsm_estimate": (i, [vp, u64, i, i, ctypes.c_uint, i, P(SolveParams), P(SolveParams), i, P(Smear),
+                                vp, vp, vp]),
+        "dl_bench_hop": (i, [vp, i, i, i, i, P(d), P(d)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, allow=()):
+    if status != OK and status not in allow:
+        msg = lib().dl_last_error().decode()
+        raise DlError(status, msg)
+    return status
+
+
+@dataclass
+class Params:
+    """Solver parameters (dl_solve_params)."""
+    tol: float = 1e-10
+    precision: int = PREC_F32
+    max_iter: int = 20000
+    fixed_iters: int = 0
+    delta: float = 0.0
+    max_outer: int = 0
+    batch: int = 16
+    use_graph: int = 1
+    chunk: int = 0
+
+    def c(self) -> SolveParams:
+        return SolveParams(self.tol, self.precision, self.max_iter, self.fixed_iters, self.delta,
+                           self.max_outer, self.batch, self.use_graph, self.chunk)
+
+
+def _stats(arr) -> list:
+    return [dict(status=s.status, iters=s.iters, outer=s.outer, true_residual=s.true_residual) for s in arr]
+
+
+class Context:
+    """One lattice on the current CUDA device (dl_create ... dl_destroy)."""
+
+    def __init__(self, dims, t_bc: int = -1, stream=None):
+        import torch
+        self._torch = torch
+        L = lib()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = ctypes.c_void_p()
+        _check(L.dl_create(ctypes.byref(h), (ctypes.c_int * 4)(*self.dims), int(t_bc), ctypes.c_void_p(stream)))
+        self._h = h
+
+    # -- lifetime ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dl_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- marshalling helpers ------------------------------------------------
+    def _field(self, t, name="field"):
+        torch = self._torch
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+            raise TypeError(f"{name} must be a complex128 CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() % (12 * self.V):
+            raise ValueError(f"{name} has {t.numel()} elements, not a multiple of 12V = {12 * self.V}")
+        return t.numel() // (12 * self.V)
+
+    def new_fields(self, n: int):
+        lx, ly, lz, lt = self.dims
+        return self._torch.zeros((n, lt, lz, ly, lx, 4, 3), dtype=self._torch.complex128, device=self.device)
+
+    # -- C ABI ------------------------------------------------------------
+    def load_gauge(self, U: np.ndarray, check_unitarity: bool = True):
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        if U.size != self.V * 36:
+            raise ValueError("gauge field must hold V*4*3*3 complex numbers")
+        _check(lib().dl_load_gauge(self._h, U.ctypes.data_as(ctypes.c_void_p), int(check_unitarity)))
+
+    def set_kappa(self, kappa: float):
+        _check(lib().dl_set_kappa(self._h, float(kappa)))
+
+    def set_timing(self, enable: bool):
+        _check(lib().dl_set_timing(self._h, int(enable)))
+
+    def get_timing(self, reset: bool = False) -> dict:
+        t = Timing()
+        _check(lib().dl_get_timing(self._h, ctypes.byref(t), int(reset)))
+        return dict(hop_ms=list(t.hop_ms), hop_launches=list(t.hop_launches), hop_bytes=list(t.hop_bytes),
+                    kernel_launches=int(t.kernel_launches))
+
+    def make_sources(self, seed: int, noise_first: int, n_noise: int, dilution: int, t0: int = 0, out=None):
+        n = ctypes.c_int64()
+        _check(lib().dl_make_sources(self._h, seed, noise_first, 0, dilution, t0, None, ctypes.byref(n)))
+        n_rhs = n.value * n_noise
+        if out is None:
+            out = self.new_fields(n_rhs)
+        elif self._field(out, "out") < n_rhs:
+            raise ValueError("out is too small")
+        _check(lib().dl_make_sources(self._h, seed, noise_first, n_noise, dilution, t0,
+                                     ctypes.c_void_p(out.data_ptr()), None))
+        return out
+
+    def make_point_sources(self, first: int, n: int, out=None):
+        if out is None:
+            out = self.new_fields(n)
+        _check(lib().dl_make_point_sources(self._h, first, n, ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def _solve(self, fn, b, params, x, allow_fail):
+        n = self._field(b, "b")
+        if x is None:
+            x = self._torch.empty_like(b)
+        p = (params or Params()).c()
+        st = (SolveStats * max(n, 1))()
+        rc = fn(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), n, ctypes.byref(p), st)
+        _check(rc, allow=(NOT_CONVERGED, BREAKDOWN, NAN) if allow_fail else ())
+        return x, _stats(st[:n])
+
+    def solve(self, b, params: Params | None = None, x=None, allow_fail: bool = False):
+        return self._solve(lib().dl_solve, b, params, x, allow_fail)
+
+    def solve_adjoint(self, b, params: Params | None = None, x=None, allow_fail: bool = False):
+        return self._solve(lib().dl_solve_adjoint, b, params, x, allow_fail)
+
+    def apply_hop(self, x, out=None):
+        n = self._field(x)
+        out = self._torch.empty_like(x) if out is None else out
+        _check(lib().dl_apply_hop(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n))
+        return out
+
+    def apply_m(self, x, out=None):
+        n = self._field(x)
+        out = self._torch.empty_like(x) if out is None else out
+        _check(lib().dl_apply_m(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n))
+        return out
+
+    def apply_smear(self, x, alpha: float, n_iter: int, t_range=None, out=None):
+        n = self._field(x)
+        out = self._torch.empty_like(x) if out is None else out
+        lo, hi = t_range if t_range is not None else (0, self.dims[3])
+        s = Smear(alpha, n_iter)
+        _check(lib().dl_apply_smear(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
+                                    ctypes.byref(s), lo, hi))
+        return out
+
+    def apply_gamma_weights(self, x, w: np.ndarray, mode: int, out=None, accumulate: bool = False):
+        """mode 0: out (+)= sum_G w[j,G,t] G^dag x ; mode 1: out (+)= sum_G conj(w[j,G,t]) G x."""
+        n = self._field(x)
+        w = np.ascontiguousarray(w, dtype=np.complex128)
+        if w.shape != (n, 16, self.dims[3]):
+            raise ValueError("weights must have shape (n_rhs, 16, T)")
+        out = self._torch.zeros_like(x) if out is None else out
+        _check(lib().dl_apply_gamma_weights(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                            n, w.ctypes.data_as(ctypes.c_void_p), mode, int(accumulate)))
+        return out
+
+    def trace_loops(self, eta, phi, sink: int = SINK_LOCAL, smear=None, t_range=None, sum_rhs: bool = False):
+        """Loops sum_{x in t} eta^dag Gamma phi: complex array [n or 1][n_sinks][16][T]."""
+        n = self._field(eta, "eta")
+        if self._field(phi, "phi") != n:
+            raise ValueError("eta and phi hold different numbers of fields")
+        T = self.dims[3]
+        lo, hi = t_range if t_range is not None else (0, T)
+        n_sinks = (1 if sink & SINK_LOCAL else 0) + (1 if sink & SINK_SMEARED else 0)
+        out = np.zeros(((1 if sum_rhs else n), n_sinks, 16, T), dtype=np.complex128)
+        sm = Smear(*smear) if smear is not None else None
+        _check(lib().dl_trace_loops(self._h, ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()), n,
+                                    sink, ctypes.byref(sm) if sm is not None else None, lo, hi, int(sum_rhs),
+                                    out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def exact_loops(self, src_first: int, n_src: int, params: Params | None = None, sink: int = SINK_LOCAL,
+                    smear=None):
+        T = self.dims[3]
+        n_sinks = (1 if sink & SINK_LOCAL else 0) + (1 if sink & SINK_SMEARED else 0)
+        out = np.zeros((n_sinks, 16, T), dtype=np.complex128)
+        p = (params or Params()).c()
+        sm = Smear(*smear) if smear is not None else None
+        st = SolveStats()
+        _check(lib().dl_exact_loops(self._h, src_first, n_src, ctypes.byref(p), sink,
+                                    ctypes.byref(sm) if sm is not None else None,
+                                    out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(st)))
+        return out, _stats([st])[0]
+
+    def tsm_estimate(self, seed: int, n_lp: int, n_hp: int, dilution: int, t0: int, lp: Params, hp: Params,
+                     sink: int = SINK_LOCAL, smear=None, per_noise: bool = False):
+        T = self.dims[3]
+        n_sinks = (1 if sink & SINK_LOCAL else 0) + (1 if sink & SINK_SMEARED else 0)
+        mean = np.zeros((n_sinks, 16, T), dtype=np.complex128)
+        var = np.zeros((n_sinks, 16, T), dtype=np.complex128)
+        pn = np.zeros((n_lp + 2 * n_hp, n_sinks, 16, T), dtype=np.complex128) if per_noise else None
+        a, b = lp.c(), hp.c()
+        sm = Smear(*smear) if smear is not None else None
+        _check(lib().dl_tsm_estimate(self._h, seed, n_lp, n_hp, dilution, t0, ctypes.byref(a), ctypes.byref(b), sink,
+                                     ctypes.byref(sm) if sm is not None else None,
+                                     mean.ctypes.data_as(ctypes.c_void_p), var.ctypes.data_as(ctypes.c_void_p),
+                                     pn.ctypes.data_as(ctypes.c_void_p) if pn is not None else None))
+        return (mean, var, pn) if per_noise else (mean, var)
+
+    def bench_hop(self, precision: int, n_rhs: int, fused: bool = False, reps: int = 20):
+        ms, by = ctypes.c_double(), ctypes.c_double()
+        _check(lib().dl_bench_hop(self._h, precision, n_rhs, int(fused), reps, ctypes.byref(ms), ctypes.byref(by)))
+        return ms.value, by.value

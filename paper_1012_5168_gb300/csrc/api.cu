@@ -1,0 +1,1461 @@
+// C ABI of the library (include/dloops.h): context, gauge field, sources, the
+// batched mixed-precision even-odd BiCGStab solver with FP64 defect
+// correction, loop contractions (local and smeared), exact loops and the
+// truncated-solver-method estimate.  All arithmetic of the path runs in the
+// CUDA kernels of this directory; the host code only sequences launches,
+// owns workspaces and moves the final loop values to the caller.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "dloops.h"
+#include "fields.cuh"
+#include "launch.h"
+
+using namespace dl;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                        \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) return fail(DL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(call)                   \
+    do {                            \
+        int rc_ = (call);           \
+        if (rc_ != DL_OK) return rc_; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct TimedPair {
+    cudaEvent_t a, b;
+    int kind;
+    double bytes;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int n_kernels = 0;
+    std::vector<TimedPair> timed;
+};
+
+struct dl_ctx {
+    int dims[4];
+    int t_bc;
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = 0;      // caller's stream
+    cudaStream_t cap_stream = 0;  // private stream used for graph capture
+    cudaStream_t cur = 0;         // stream kernels are enqueued on right now
+    bool capturing = false;
+    Geom g;
+    long V = 0, Vh = 0;
+    double kappa = 0.0;
+    bool have_gauge = false, have_kappa = false;
+
+    uint32_t *d_coords = nullptr;
+    double *d_gauge64 = nullptr;
+    float *d_gauge32 = nullptr;
+    bf16 *d_gauge16 = nullptr;
+    double2 *d_gammas = nullptr;  // [16][4][4]
+
+    // batch workspace, width ws_N (power of two)
+    int ws_N = 0;
+    double *b64 = nullptr, *x64 = nullptr;   // full fields [2][Vh][12][N]
+    double *bh64 = nullptr, *r64 = nullptr;  // even halves
+    double *t64 = nullptr;                   // odd half
+    double *s64a = nullptr, *s64b = nullptr; // full fields (smearing)
+    void *lo[8] = {nullptr};                 // inner fields: x r rhat p v s t (even) tmp (odd)
+    RhsState *d_rhs = nullptr;
+    OuterState *d_outer = nullptr;
+    double2 *d_partials = nullptr;
+    size_t partials_cap = 0;  // double2 elements
+    double2 *d_loops = nullptr;  // [N][2 sinks][16][T]
+    double2 *d_acc = nullptr;    // [2 sinks][T][16] exact-loop accumulators
+    double *d_canon = nullptr;   // N canonical fields (internal sources)
+    double2 *d_noise = nullptr;  // per-noise loops (TSM)
+    size_t noise_cap = 0;
+    double2 *d_w = nullptr;      // gamma weights / spin matrices
+    size_t w_cap = 0;
+
+    int *h_count = nullptr;  // pinned, mapped
+    int *d_count = nullptr;
+
+    std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
+    bool timing = false;
+    std::vector<TimedPair> pending;  // recorded eagerly, harvested at the next sync
+    std::vector<cudaEvent_t> event_pool;
+    dl_timing tim;
+    int64_t kernel_launches = 0;
+    int hop_R[3][8];  // tuned right-hand sides per thread, [prec][log2 N]
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+static int pow2_at_least(int n) { return 1 << ilog2(n < 1 ? 1 : n); }
+
+static Launch make_launch(dl_ctx *c, long items, int block, size_t smem, int per_sm) {
+    Launch l;
+    long need = (items + block - 1) / block;
+    long cap = (long)c->num_sms * per_sm;
+    l.grid = (int)std::max(1L, std::min(need, cap));
+    l.block = block;
+    l.smem = smem;
+    l.stream = c->cur;
+    return l;
+}
+
+static size_t half_elems(dl_ctx *c, int N) { return (size_t)c->Vh * 12 * N; }  // complex per half field
+
+static int storage_bytes(int prec) { return prec == P_F64 ? 8 : (prec == P_F32 ? 4 : 2); }
+
+static cudaEvent_t get_event(dl_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static void harvest(dl_ctx *c, std::vector<TimedPair> &v, bool release) {
+    for (auto &tp : v) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, tp.a, tp.b) == cudaSuccess) {
+            c->tim.hop_ms[tp.kind] += ms;
+            c->tim.hop_launches[tp.kind] += 1;
+            c->tim.hop_bytes[tp.kind] += tp.bytes;
+        }
+        if (release) {
+            c->event_pool.push_back(tp.a);
+            c->event_pool.push_back(tp.b);
+        }
+    }
+    if (release) v.clear();
+}
+
+static int sync(dl_ctx *c) {
+    CK(cudaStreamSynchronize(c->stream));
+    harvest(c, c->pending, true);
+    return DL_OK;
+}
+
+static void record(dl_ctx *c, cudaEvent_t e) {
+    if (c->capturing) cudaEventRecordWithFlags(e, c->cur, cudaEventRecordExternal);
+    else cudaEventRecord(e, c->cur);
+}
+
+// Wilson hop launch.  kind >= 0 marks launches timed with CUDA events.
+static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void *in, const void *y, const void *z,
+                  const void *rhat, int p, int N, double coef, int cb0, int cb1, double2 *partials, int *nblocks) {
+    HopArgs a;
+    a.out = out;
+    a.in = in;
+    a.y = y;
+    a.z = z;
+    a.rhat = rhat;
+    a.gauge = prec == P_F64 ? (const void *)c->d_gauge64
+                            : (prec == P_F32 ? (const void *)c->d_gauge32 : (const void *)c->d_gauge16);
+    a.coords = c->d_coords;
+    a.partials = partials;
+    a.p = p;
+    a.N = N;
+    a.cb_begin = cb0;
+    a.cb_end = cb1;
+    a.c = coef;
+    a.g = c->g;
+    int R = prec == P_F64 ? 1 : c->hop_R[prec][ilog2(N)];
+    if (R > N) R = N;
+    while (N / R > 32) R *= 2;
+    const int G = N / R;
+    const int block = 128;
+    const long total = (long)(cb1 - cb0) * G;
+    const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
+    const size_t smem = NV ? (size_t)(block / 32) * G * R * NV * (prec == P_F64 ? 16 : 8) : 0;
+    Launch l = make_launch(c, total, block, smem, prec == P_F64 ? 4 : 8);
+    if (nblocks) *nblocks = l.grid;
+    const bool timed = c->timing;
+    TimedPair tp;
+    if (timed) {
+        tp.a = get_event(c);
+        tp.b = get_event(c);
+        tp.kind = (prec == P_F64 ? 2 : 0) + (mode != MODE_PLAIN || red != RED_NONE ? 1 : 0);
+        const double S = 24.0 * storage_bytes(prec), L = 18.0 * storage_bytes(prec);
+        int streams = 2 + (mode != MODE_PLAIN ? 1 : 0) + (mode == MODE_RESID ? 1 : 0) +
+                      ((red == RED_R0DOT || red == RED_BICG) ? 1 : 0);
+        if (red == RED_BICG && mode == MODE_PLAIN) streams += 1;
+        tp.bytes = (double)(cb1 - cb0) * (8.0 * L + (double)N * streams * S);
+        record(c, tp.a);
+    }
+    cudaError_t e;
+    if (prec == P_F64) e = launch_hop_f64(R, mode, red, a, l);
+    else if (prec == P_F32) e = launch_hop_f32(R, mode, red, a, l);
+    else e = launch_hop_bf16(R, mode, red, a, l);
+    if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
+    c->kernel_launches++;
+    if (timed) {
+        record(c, tp.b);
+        c->pending.push_back(tp);
+    }
+    return DL_OK;
+}
+
+static VecLaunch vec_launch(dl_ctx *c, int prec, int N, size_t smem_per_val, int per_sm = 8) {
+    VecLaunch v;
+    v.prec = prec;
+    v.R = prec == P_F64 ? 1 : std::min(2, N);
+    while (N / v.R > 32) v.R *= 2;
+    v.a.n_elem = (int)(c->Vh * 12);
+    v.a.N = N;
+    const int block = 256;
+    const int G = N / v.R;
+    v.l = make_launch(c, (long)v.a.n_elem * G, block, (size_t)(block / 32) * G * v.R * smem_per_val, per_sm);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+static void free_ws(dl_ctx *c) {
+    for (auto &kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto &tp : kv.second.timed) {
+            c->event_pool.push_back(tp.a);
+            c->event_pool.push_back(tp.b);
+        }
+    }
+    c->graphs.clear();
+    double **d64[] = {&c->b64, &c->x64, &c->bh64, &c->r64, &c->t64, &c->s64a, &c->s64b, &c->d_canon};
+    for (auto pp : d64) {
+        if (*pp) cudaFree(*pp);
+        *pp = nullptr;
+    }
+    for (auto &p : c->lo) {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    if (c->d_rhs) cudaFree(c->d_rhs);
+    if (c->d_outer) cudaFree(c->d_outer);
+    if (c->d_loops) cudaFree(c->d_loops);
+    c->d_rhs = nullptr;
+    c->d_outer = nullptr;
+    c->d_loops = nullptr;
+    c->ws_N = 0;
+}
+
+static void invalidate_graphs(dl_ctx *c) {
+    for (auto &kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto &tp : kv.second.timed) {
+            c->event_pool.push_back(tp.a);
+            c->event_pool.push_back(tp.b);
+        }
+    }
+    c->graphs.clear();
+}
+
+static int ensure_ws(dl_ctx *c, int N) {
+    if (c->ws_N >= N) return DL_OK;
+    N = pow2_at_least(N);
+    CK(cudaStreamSynchronize(c->stream));
+    free_ws(c);
+    const size_t half = half_elems(c, N) * 16;  // bytes of an FP64 half field
+    double **full[] = {&c->b64, &c->x64, &c->s64a, &c->s64b};
+    for (auto pp : full)
+        if (cudaMalloc((void **)pp, 2 * half) != cudaSuccess) return fail(DL_ENOMEM, "workspace allocation failed");
+    double **halves[] = {&c->bh64, &c->r64, &c->t64};
+    for (auto pp : halves)
+        if (cudaMalloc((void **)pp, half) != cudaSuccess) return fail(DL_ENOMEM, "workspace allocation failed");
+    for (auto &p : c->lo)
+        if (cudaMalloc(&p, half) != cudaSuccess) return fail(DL_ENOMEM, "workspace allocation failed");
+    if (cudaMalloc((void **)&c->d_canon, 2 * half) != cudaSuccess) return fail(DL_ENOMEM, "workspace allocation failed");
+    if (cudaMalloc((void **)&c->d_rhs, sizeof(RhsState) * N) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_outer, sizeof(OuterState) * N) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_loops, sizeof(double2) * N * 2 * 16 * c->dims[3]) != cudaSuccess)
+        return fail(DL_ENOMEM, "workspace allocation failed");
+    CK(cudaMemset(c->b64, 0, 2 * half));
+    CK(cudaMemset(c->x64, 0, 2 * half));
+    for (auto &p : c->lo) CK(cudaMemset(p, 0, half));
+    c->ws_N = N;
+    return DL_OK;
+}
+
+static int ensure_partials(dl_ctx *c, size_t elems) {
+    if (c->partials_cap >= elems) return DL_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    invalidate_graphs(c);
+    if (c->d_partials) cudaFree(c->d_partials);
+    c->d_partials = nullptr;
+    if (cudaMalloc((void **)&c->d_partials, elems * sizeof(double2)) != cudaSuccess)
+        return fail(DL_ENOMEM, "partials allocation failed");
+    c->partials_cap = elems;
+    return DL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gamma basis (chiral DeGrand-Rossi), host construction
+// ---------------------------------------------------------------------------
+typedef std::complex<double> zc;
+
+static void gamma_basis(zc out[16][4][4]) {
+    const zc I(0, 1), O(0, 0), one(1, 0);
+    zc g[4][4][4] = {
+        {{O, O, O, I}, {O, O, I, O}, {O, -I, O, O}, {-I, O, O, O}},
+        {{O, O, O, -one}, {O, O, one, O}, {O, one, O, O}, {-one, O, O, O}},
+        {{O, O, I, O}, {O, O, O, -I}, {-I, O, O, O}, {O, I, O, O}},
+        {{O, O, one, O}, {O, O, O, one}, {one, O, O, O}, {O, one, O, O}},
+    };
+    auto mul = [](const zc a[4][4], const zc b[4][4], zc r[4][4]) {
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                zc s = 0;
+                for (int k = 0; k < 4; ++k) s += a[i][k] * b[k][j];
+                r[i][j] = s;
+            }
+    };
+    zc g5[4][4], t1[4][4], t2[4][4];
+    mul(g[0], g[1], t1);
+    mul(t1, g[2], t2);
+    mul(t2, g[3], g5);
+    int n = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) out[n][i][j] = (i == j) ? one : O;
+    ++n;
+    for (int m = 0; m < 4; ++m, ++n)
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) out[n][i][j] = g[m][i][j];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) out[n][i][j] = g5[i][j];
+    ++n;
+    for (int m = 0; m < 4; ++m, ++n) mul(g5, g[m], out[n]);
+    for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b, ++n) mul(g[a], g[b], out[n]);
+}
+
+// ---------------------------------------------------------------------------
+// context API
+// ---------------------------------------------------------------------------
+extern "C" const char *dl_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *dl_status_string(int s) {
+    switch (s) {
+        case DL_OK: return "ok";
+        case DL_EINVAL: return "invalid argument";
+        case DL_ENOMEM: return "out of device memory";
+        case DL_ECUDA: return "CUDA error";
+        case DL_NOT_CONVERGED: return "not converged";
+        case DL_BREAKDOWN: return "BiCGStab breakdown";
+        case DL_NAN: return "non-finite value";
+        case DL_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_stream) {
+    if (!out || !dims) return fail(DL_EINVAL, "null argument");
+    *out = nullptr;
+    for (int m = 0; m < 4; ++m)
+        if (dims[m] < 2 || dims[m] > 256) return fail(DL_EINVAL, "lattice extents must lie in [2, 256]");
+    for (int m = 0; m < 4; ++m)
+        if (dims[m] % 2) return fail(DL_EINVAL, "every lattice extent must be even (even-odd preconditioning)");
+    if (t_bc != 1 && t_bc != -1) return fail(DL_EINVAL, "t_bc must be +1 or -1");
+    const long V = (long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V * 32 >= (1L << 31)) return fail(DL_EINVAL, "lattice too large for 32-bit thread indexing");
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return fail(DL_ECUDA, "no CUDA device");
+    CK(cudaGetDevice(&dev));
+    dl_ctx *c = new dl_ctx();
+    memcpy(c->dims, dims, sizeof(c->dims));
+    c->t_bc = t_bc;
+    c->device = dev;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->cur = c->stream;
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return fail(DL_ECUDA, "stream creation failed");
+    }
+    c->V = V;
+    c->Vh = V / 2;
+    for (int m = 0; m < 4; ++m) c->g.L[m] = dims[m];
+    c->g.stride[0] = 1;
+    c->g.stride[1] = dims[0];
+    c->g.stride[2] = dims[0] * dims[1];
+    c->g.stride[3] = dims[0] * dims[1] * dims[2];
+    c->g.Vh = (int)c->Vh;
+    c->g.V3h = dims[0] * dims[1] * dims[2] / 2;
+    c->g.t_bc = t_bc;
+    memset(&c->tim, 0, sizeof(c->tim));
+    for (int p = 0; p < 3; ++p)
+        for (int l = 0; l < 8; ++l) c->hop_R[p][l] = 2;
+    // coordinates table
+    std::vector<uint32_t> coords(V);
+    for (int t = 0; t < dims[3]; ++t)
+        for (int z = 0; z < dims[2]; ++z)
+            for (int y = 0; y < dims[1]; ++y)
+                for (int x = 0; x < dims[0]; ++x) {
+                    const long i = x + (long)dims[0] * (y + (long)dims[1] * (z + (long)dims[2] * t));
+                    const int p = (x + y + z + t) & 1;
+                    coords[p * c->Vh + (i >> 1)] = (uint32_t)x | ((uint32_t)y << 8) | ((uint32_t)z << 16) |
+                                                   ((uint32_t)t << 24);
+                }
+    zc gam[16][4][4];
+    gamma_basis(gam);
+    std::vector<double2> gh(256);
+    for (int n = 0; n < 16; ++n)
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) gh[(n * 4 + i) * 4 + j] = make_double2(gam[n][i][j].real(), gam[n][i][j].imag());
+    int rc = DL_OK;
+    if (cudaMalloc((void **)&c->d_coords, V * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_gammas, 256 * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_acc, 2 * 16 * dims[3] * sizeof(double2)) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_count, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_count, c->h_count, 0) != cudaSuccess)
+        rc = fail(DL_ENOMEM, "context allocation failed");
+    if (rc == DL_OK &&
+        (cudaMemcpy(c->d_coords, coords.data(), V * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(c->d_gammas, gh.data(), 256 * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess))
+        rc = fail(DL_ECUDA, "context upload failed");
+    if (rc != DL_OK) {
+        dl_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return DL_OK;
+}
+
+extern "C" int dl_destroy(dl_ctx *c) {
+    if (!c) return DL_OK;
+    cudaStreamSynchronize(c->stream);
+    free_ws(c);
+    for (auto e : c->event_pool) cudaEventDestroy(e);
+    for (auto &tp : c->pending) {
+        cudaEventDestroy(tp.a);
+        cudaEventDestroy(tp.b);
+    }
+    void *ptrs[] = {c->d_coords, c->d_gauge64, c->d_gauge32, c->d_gauge16, c->d_gammas, c->d_partials,
+                    c->d_acc,    c->d_noise,   c->d_w};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_count) cudaFreeHost(c->h_count);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+    return DL_OK;
+}
+
+extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
+    if (!c || !U) return fail(DL_EINVAL, "null argument");
+    const long nlink = 4 * c->V;
+    if (check) {
+        for (long l = 0; l < nlink; ++l) {
+            const double *u = U + l * 18;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double re = 0, im = 0;  // (U U^dag)_{ab}
+                    for (int k = 0; k < 3; ++k) {
+                        const double ar = u[(a * 3 + k) * 2], ai = u[(a * 3 + k) * 2 + 1];
+                        const double br = u[(b * 3 + k) * 2], bi = -u[(b * 3 + k) * 2 + 1];
+                        re += ar * br - ai * bi;
+                        im += ar * bi + ai * br;
+                    }
+                    if (std::fabs(re - (a == b ? 1.0 : 0.0)) > 1e-10 || std::fabs(im) > 1e-10 || !std::isfinite(re))
+                        return fail(DL_EINVAL, "gauge link is not unitary");
+                }
+        }
+    }
+    const size_t n64 = (size_t)nlink * 18;
+    if (!c->d_gauge64) {
+        if (cudaMalloc((void **)&c->d_gauge64, n64 * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge32, n64 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge16, n64 * sizeof(bf16)) != cudaSuccess)
+            return fail(DL_ENOMEM, "gauge allocation failed");
+    }
+    double *tmp = nullptr;
+    if (cudaMalloc((void **)&tmp, n64 * sizeof(double)) != cudaSuccess) return fail(DL_ENOMEM, "gauge staging failed");
+    c->cur = c->stream;
+    int rc = DL_OK;
+    if (cudaMemcpyAsync(tmp, U, n64 * sizeof(double), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+        rc = fail(DL_ECUDA, "gauge upload failed");
+    } else {
+        const int grid = std::max(1, std::min((int)((2 * c->Vh + 255) / 256), c->num_sms * 8));
+        gauge_reorder_kernel<double><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge64);
+        gauge_reorder_kernel<float><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge32);
+        gauge_reorder_kernel<bf16><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge16);
+        c->kernel_launches += 3;
+        if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+            rc = fail(DL_ECUDA, "gauge reorder failed");
+    }
+    cudaFree(tmp);
+    if (rc == DL_OK) c->have_gauge = true;
+    return rc;
+}
+
+extern "C" int dl_set_kappa(dl_ctx *c, double kappa) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!std::isfinite(kappa)) return fail(DL_EINVAL, "kappa must be finite");
+    if (kappa != c->kappa) invalidate_graphs(c);
+    c->kappa = kappa;
+    c->have_kappa = true;
+    return DL_OK;
+}
+
+extern "C" int dl_set_timing(dl_ctx *c, int enable) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if ((enable != 0) != c->timing) invalidate_graphs(c);
+    c->timing = enable != 0;
+    return DL_OK;
+}
+
+extern "C" int dl_get_timing(dl_ctx *c, dl_timing *out, int reset) {
+    if (!c || !out) return fail(DL_EINVAL, "null argument");
+    TRY(sync(c));
+    *out = c->tim;
+    out->kernel_launches = c->kernel_launches;
+    if (reset) {
+        memset(&c->tim, 0, sizeof(c->tim));
+        c->kernel_launches = 0;
+    }
+    return DL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// layout conversion
+// ---------------------------------------------------------------------------
+static int canon_to_eo(dl_ctx *c, const double *canon, double *eo, int n, int N, int g5, int cb0, int cb1) {
+    ConvArgs a;
+    a.coords = c->d_coords;
+    a.g = c->g;
+    a.cb0 = cb0;
+    a.cb1 = cb1;
+    a.n = n;
+    a.N = N;
+    a.gamma5 = g5;
+    Launch l = make_launch(c, 2L * (cb1 - cb0) * N, 256, 0, 8);
+    canon_to_eo_kernel<<<l.grid, l.block, 0, l.stream>>>(a, canon, eo);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+static int eo_to_canon(dl_ctx *c, const double *eo, double *canon, int n, int N, int g5, int cb0, int cb1) {
+    ConvArgs a;
+    a.coords = c->d_coords;
+    a.g = c->g;
+    a.cb0 = cb0;
+    a.cb1 = cb1;
+    a.n = n;
+    a.N = N;
+    a.gamma5 = g5;
+    Launch l = make_launch(c, 2L * (cb1 - cb0) * n, 256, 0, 8);
+    eo_to_canon_kernel<<<l.grid, l.block, 0, l.stream>>>(a, eo, canon);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solver
+// ---------------------------------------------------------------------------
+static void *lo_ptr(dl_ctx *c, int k) { return c->lo[k]; }
+enum { LX = 0, LR = 1, LRH = 2, LP = 3, LV = 4, LS = 5, LT = 6, LTMP = 7 };
+
+static int enqueue_iteration(dl_ctx *c, int prec, int N) {
+    const double k2 = c->kappa * c->kappa;
+    const int Vh = (int)c->Vh;
+    double2 *part = c->d_partials;
+    int nb = 0;
+    TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
+               Vh, nullptr, nullptr));
+    TRY(do_hop(c, prec, MODE_XPAY, RED_R0DOT, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr,
+               lo_ptr(c, LRH), 0, N, -k2, 0, Vh, part, &nb));
+    scalar_alpha_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, part, nb, N);
+    VecLaunch v = vec_launch(c, prec, N, 0);
+    CK(launch_axpy_s(v, c->d_rhs, lo_ptr(c, LR), lo_ptr(c, LV), lo_ptr(c, LS)));
+    TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
+               Vh, nullptr, nullptr));
+    TRY(do_hop(c, prec, MODE_XPAY, RED_BICG, lo_ptr(c, LT), lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, lo_ptr(c, LRH),
+               0, N, -k2, 0, Vh, part, &nb));
+    scalar_omega_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, part, nb, N);
+    CK(launch_update(v, c->d_rhs, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LP), lo_ptr(c, LS), lo_ptr(c, LT),
+                     lo_ptr(c, LV)));
+    c->kernel_launches += 4;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+// Run `iters` inner iterations (graph or eager); returns the number of right-hand
+// sides still active in *active.
+static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int *active) {
+    if (use_graph) {
+        auto key = std::make_tuple(prec, N, iters, c->timing ? 1 : 0);
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            GraphEntry ge;
+            const int64_t k0 = c->kernel_launches;
+            std::vector<TimedPair> saved;
+            saved.swap(c->pending);
+            c->cur = c->cap_stream;
+            c->capturing = true;
+            cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+            int rc = DL_OK;
+            if (e == cudaSuccess) {
+                for (int k = 0; k < iters && rc == DL_OK; ++k) rc = enqueue_iteration(c, prec, N);
+                if (rc == DL_OK) {
+                    count_active_kernel<<<1, 1, 0, c->cap_stream>>>(c->d_rhs, N, c->d_count);
+                    c->kernel_launches++;
+                }
+                cudaGraph_t graph = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+                if (rc == DL_OK && e2 == cudaSuccess) {
+                    e2 = cudaGraphInstantiate(&ge.exec, graph, 0);
+                    if (e2 != cudaSuccess) rc = fail(DL_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+                } else if (rc == DL_OK) {
+                    rc = fail(DL_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e2));
+                }
+                if (graph) cudaGraphDestroy(graph);
+            } else {
+                rc = fail(DL_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+            }
+            c->capturing = false;
+            c->cur = c->stream;
+            ge.timed.swap(c->pending);
+            c->pending.swap(saved);
+            ge.n_kernels = (int)(c->kernel_launches - k0);
+            c->kernel_launches = k0;
+            if (rc != DL_OK) {
+                for (auto &tp : ge.timed) {
+                    c->event_pool.push_back(tp.a);
+                    c->event_pool.push_back(tp.b);
+                }
+                return rc;
+            }
+            it = c->graphs.emplace(key, std::move(ge)).first;
+        }
+        CK(cudaGraphLaunch(it->second.exec, c->stream));
+        c->kernel_launches += it->second.n_kernels;
+        TRY(sync(c));
+        harvest(c, it->second.timed, false);
+    } else {
+        c->cur = c->stream;
+        for (int k = 0; k < iters; ++k) TRY(enqueue_iteration(c, prec, N));
+        count_active_kernel<<<1, 1, 0, c->stream>>>(c->d_rhs, N, c->d_count);
+        c->kernel_launches++;
+        CK(cudaGetLastError());
+        TRY(sync(c));
+    }
+    *active = *(volatile int *)c->h_count;
+    return DL_OK;
+}
+
+struct SolveCfg {
+    double tol;
+    int prec;
+    int max_iter;
+    int fixed_iters;
+    double delta;
+    int max_outer;
+    int batch;
+    bool use_graph;
+    int chunk;
+};
+
+static int read_params(const dl_solve_params *p, SolveCfg *s) {
+    dl_solve_params d;
+    memset(&d, 0, sizeof(d));
+    d.tol = 1e-10;
+    d.precision = DL_PREC_F32;
+    d.max_iter = 20000;
+    d.use_graph = 1;
+    if (!p) p = &d;
+    if (!(p->tol > 0.0) || !std::isfinite(p->tol)) return fail(DL_EINVAL, "tol must be positive");
+    if (p->precision < 0 || p->precision > 2) return fail(DL_EINVAL, "unknown precision");
+    if (p->max_iter < 0 || p->fixed_iters < 0) return fail(DL_EINVAL, "negative iteration count");
+    s->tol = p->tol;
+    s->prec = p->precision;
+    s->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
+    s->fixed_iters = p->fixed_iters;
+    s->delta = p->delta > 0 ? p->delta : (p->precision == DL_PREC_BF16 ? 3e-3 : (p->precision == DL_PREC_F32 ? 1e-5 : 1e-3 * p->tol));
+    if (p->precision == DL_PREC_F64 && !(p->delta > 0)) s->delta = std::max(1e-14, 0.5 * p->tol);
+    s->max_outer = p->max_outer > 0 ? p->max_outer : 60;
+    int b = p->batch > 0 ? p->batch : 16;
+    if (b > 64) return fail(DL_EINVAL, "batch must be <= 64");
+    s->batch = pow2_at_least(b);
+    s->use_graph = p->use_graph != 0;
+    s->chunk = p->chunk > 0 ? p->chunk : 8;
+    return DL_OK;
+}
+
+static int ready(dl_ctx *c) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (!c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
+    return DL_OK;
+}
+
+// Solve the batch held in c->b64 (n right-hand sides, layout width N); the
+// solution is left in c->x64.  host_os receives the N outer states.
+static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<OuterState> &host_os) {
+    const double k = c->kappa, k2 = k * k;
+    const int Vh = (int)c->Vh;
+    const size_t half = half_elems(c, N) * 2;  // doubles
+    double *be = c->b64, *bo = c->b64 + half, *xe = c->x64, *xo = c->x64 + half;
+    c->cur = c->stream;
+    const size_t pc = c->partials_cap / 2;
+    double2 *pa = c->d_partials, *pb = c->d_partials + pc;
+    int nb = 0, nb2 = 0;
+    // |b|^2 over both halves
+    {
+        VecLaunch v = vec_launch(c, P_F64, N, 16);
+        CK(launch_norm2(v, be, pa));
+        nb = v.l.grid;
+        CK(launch_norm2(v, bo, pb));
+        nb2 = v.l.grid;
+        full_norm_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 0);
+        c->kernel_launches += 3;
+    }
+    // bhat = b_e + kappa D_eo b_o, |bhat|^2
+    TRY(do_hop(c, P_F64, MODE_XPAY, RED_NORM, c->bh64, bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
+    outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 0, P.tol, P.max_outer, P.max_iter);
+    c->kernel_launches++;
+    CK(cudaMemcpyAsync(c->r64, c->bh64, half * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemsetAsync(xe, 0, half * sizeof(double), c->stream));
+    const int prec = P.prec;
+    for (int cycle = 0; cycle < P.max_outer; ++cycle) {
+        outer_count_kernel<<<1, 1, 0, c->stream>>>(c->d_outer, N, c->d_count);
+        c->kernel_launches++;
+        TRY(sync(c));
+        if (*(volatile int *)c->h_count == 0) break;
+        VecLaunch v = vec_launch(c, prec, N, prec == P_F64 ? 16 : 8);
+        CK(launch_inner_init(v, c->d_outer, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH), lo_ptr(c, LP), pa));
+        const int target = P.fixed_iters > 0 ? P.fixed_iters : P.max_iter;
+        inner_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
+                                                    P.max_iter, P.fixed_iters > 0 ? 1 : 0);
+        c->kernel_launches += 2;
+        int done = 0;
+        while (done < target) {
+            const int kk = std::min(P.chunk, target - done);
+            int active = 0;
+            TRY(run_chunk(c, prec, N, kk, P.use_graph, &active));
+            done += kk;
+            if (active == 0) break;
+        }
+        c->cur = c->stream;
+        CK(launch_accumulate(vec_launch(c, prec, N, 0), c->d_outer, lo_ptr(c, LX), xe));
+        c->kernel_launches++;
+        if (P.fixed_iters > 0) break;
+        // r = bhat - Mhat x  (FP64)
+        TRY(do_hop(c, P_F64, MODE_PLAIN, RED_NONE, c->t64, xe, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh, nullptr,
+                   nullptr));
+        TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->r64, c->t64, xe, c->bh64, nullptr, 0, N, -k2, 0, Vh, pa, &nb));
+        outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 1, P.tol, P.max_outer,
+                                                     P.max_iter);
+        c->kernel_launches++;
+    }
+    // reconstruct x_o = b_o + kappa D_oe x_e
+    TRY(do_hop(c, P_F64, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
+    // full-lattice true residual b - M x
+    TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
+    TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->t64, xe, xo, bo, nullptr, 1, N, -k, 0, Vh, pb, &nb2));
+    full_norm_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 1);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    host_os.resize(N);
+    CK(cudaMemcpyAsync(host_os.data(), c->d_outer, N * sizeof(OuterState), cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync(c));
+    (void)n;
+    return DL_OK;
+}
+
+static int status_of(const OuterState &o, double tol, bool fixed) {
+    if (o.status == ST_NAN || !std::isfinite(o.full_r2)) return DL_NAN;
+    if (fixed) return DL_OK;
+    if (o.full_b2 == 0.0) return DL_OK;
+    return std::sqrt(o.full_r2 / o.full_b2) <= tol ? DL_OK : DL_NOT_CONVERGED;
+}
+
+static int solve_impl(dl_ctx *c, const void *b, void *x, int n_rhs, const dl_solve_params *params,
+                      dl_solve_stats *stats, int g5) {
+    TRY(ready(c));
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (n_rhs == 0) return DL_OK;
+    if (!b || !x) return fail(DL_EINVAL, "null field pointer");
+    if (b == x) return fail(DL_EINVAL, "dev_x may not alias dev_b");
+    SolveCfg P;
+    TRY(read_params(params, &P));
+    const int N = std::min(P.batch, pow2_at_least(n_rhs));
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    const size_t field = (size_t)c->V * 24;  // doubles per canonical field
+    int worst = DL_OK;
+    std::vector<OuterState> os;
+    for (int j0 = 0; j0 < n_rhs; j0 += N) {
+        const int n = std::min(N, n_rhs - j0);
+        c->cur = c->stream;
+        TRY(canon_to_eo(c, (const double *)b + (size_t)j0 * field, c->b64, n, N, g5, 0, (int)c->Vh));
+        TRY(solve_batch(c, n, N, P, os));
+        TRY(eo_to_canon(c, c->x64, (double *)x + (size_t)j0 * field, n, N, g5, 0, (int)c->Vh));
+        for (int j = 0; j < n; ++j) {
+            const int s = status_of(os[j], P.tol, P.fixed_iters > 0);
+            if (stats) {
+                stats[j0 + j].status = s;
+                stats[j0 + j].iters = os[j].iters;
+                stats[j0 + j].outer = os[j].outer;
+                stats[j0 + j].true_residual = os[j].full_b2 > 0 ? std::sqrt(os[j].full_r2 / os[j].full_b2) : 0.0;
+            }
+            if (s != DL_OK && worst == DL_OK) worst = s;
+        }
+    }
+    TRY(sync(c));
+    if (worst != DL_OK) fail(worst, "some right-hand sides did not converge");
+    return worst;
+}
+
+extern "C" int dl_solve(dl_ctx *c, const void *b, void *x, int n, const dl_solve_params *p, dl_solve_stats *st) {
+    return solve_impl(c, b, x, n, p, st, 0);
+}
+
+extern "C" int dl_solve_adjoint(dl_ctx *c, const void *b, void *x, int n, const dl_solve_params *p,
+                                dl_solve_stats *st) {
+    return solve_impl(c, b, x, n, p, st, 1);
+}
+
+// ---------------------------------------------------------------------------
+// sources
+// ---------------------------------------------------------------------------
+extern "C" int dl_make_sources(dl_ctx *c, uint64_t seed, int64_t noise_first, int n_noise, unsigned dil, int t0,
+                               void *out, int64_t *n_rhs) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (n_noise < 0 || noise_first < 0) return fail(DL_EINVAL, "negative noise range");
+    if (dil & ~31u) return fail(DL_EINVAL, "unknown dilution bits");
+    if ((dil & DL_DIL_TIME) && t0 >= c->dims[3]) return fail(DL_EINVAL, "t0 outside the lattice");
+    SourceArgs a;
+    a.coords = c->d_coords;
+    a.g = c->g;
+    a.seed = seed;
+    a.noise_first = noise_first;
+    a.n_noise = n_noise;
+    a.dil_spin = (dil & DL_DIL_SPIN) ? 4 : 1;
+    a.dil_colour = (dil & DL_DIL_COLOUR) ? 3 : 1;
+    a.dil_eo = (dil & DL_DIL_EVENODD) ? 2 : 1;
+    a.dil_cubic = (dil & DL_DIL_CUBIC) ? 8 : 1;
+    a.dil_time = (dil & DL_DIL_TIME) ? 1 : 0;
+    a.t0 = t0;
+    const int K = a.dil_spin * a.dil_colour * a.dil_eo * a.dil_cubic;
+    a.k_first = 0;
+    a.k_count = K;
+    if (n_rhs) *n_rhs = (int64_t)n_noise * K;
+    if (n_noise == 0) return DL_OK;
+    if (!out) return fail(DL_EINVAL, "null output");
+    c->cur = c->stream;
+    Launch l = make_launch(c, (long)n_noise * K * c->V, 256, 0, 16);
+    z2_source_kernel<<<l.grid, l.block, 0, c->stream>>>(a, (double *)out);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+extern "C" int dl_make_point_sources(dl_ctx *c, int64_t first, int n, void *out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (n < 0 || first < 0 || first + n > 12 * c->V) return fail(DL_EINVAL, "point-source range outside 0..12V");
+    if (n == 0) return DL_OK;
+    if (!out) return fail(DL_EINVAL, "null output");
+    c->cur = c->stream;
+    Launch l = make_launch(c, (long)n * c->V * 12, 256, 0, 16);
+    point_source_kernel<<<l.grid, l.block, 0, c->stream>>>(first, n, c->V, (double *)out);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// operators on canonical fields
+// ---------------------------------------------------------------------------
+static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool with_m) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (with_m && !c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (n_rhs == 0) return DL_OK;
+    if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
+    const int N = std::min(64, pow2_at_least(n_rhs));
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    const size_t field = (size_t)c->V * 24, half = half_elems(c, N) * 2;
+    const int Vh = (int)c->Vh;
+    const int mode = with_m ? MODE_XPAY : MODE_PLAIN;
+    const double coef = with_m ? -c->kappa : 1.0;
+    for (int j0 = 0; j0 < n_rhs; j0 += N) {
+        const int n = std::min(N, n_rhs - j0);
+        c->cur = c->stream;
+        TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
+        TRY(do_hop(c, P_F64, mode, RED_NONE, c->x64, c->b64 + half, c->b64, nullptr, nullptr, 0, N, coef, 0, Vh,
+                   nullptr, nullptr));
+        TRY(do_hop(c, P_F64, mode, RED_NONE, c->x64 + half, c->b64, c->b64 + half, nullptr, nullptr, 1, N, coef, 0,
+                   Vh, nullptr, nullptr));
+        TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
+    }
+    return DL_OK;
+}
+
+extern "C" int dl_apply_hop(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, false); }
+extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, true); }
+
+// Smear the EO fields at *buf (full field, width N) over cb range; returns the
+// buffer holding the result (ping-pong with `spare`).
+static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, const dl_smear &s, int cb0, int cb1) {
+    SmearArgs A;
+    A.gauge = c->d_gauge64;
+    A.coords = c->d_coords;
+    A.g = c->g;
+    A.cb0 = cb0;
+    A.cb1 = cb1;
+    A.N = N;
+    A.a = 1.0 / (1.0 + 6.0 * s.alpha);
+    A.c = s.alpha / (1.0 + 6.0 * s.alpha);
+    double *src = *buf, *dst = spare;
+    const size_t half = half_elems(c, N) * 2;
+    // the spare buffer must hold zeros outside the range only where it is read: the
+    // smearing step reads neighbours within the same timeslices, so clearing is not needed.
+    (void)half;
+    Launch l = make_launch(c, 2L * (cb1 - cb0) * N, 128, 0, 8);
+    for (int it = 0; it < s.n_iter; ++it) {
+        A.in = src;
+        A.out = dst;
+        smear_kernel<<<l.grid, l.block, 0, c->cur>>>(A);
+        c->kernel_launches++;
+        std::swap(src, dst);
+    }
+    CK(cudaGetLastError());
+    *buf = src;
+    return DL_OK;
+}
+
+extern "C" int dl_apply_smear(dl_ctx *c, const void *in, void *out, int n_rhs, const dl_smear *s, int t_lo, int t_hi) {
+    if (!c || !s) return fail(DL_EINVAL, "null argument");
+    if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (s->n_iter < 0 || !std::isfinite(s->alpha)) return fail(DL_EINVAL, "bad smearing parameters");
+    if (t_lo < 0 || t_hi > c->dims[3] || t_lo >= t_hi) return fail(DL_EINVAL, "bad timeslice range");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (n_rhs == 0) return DL_OK;
+    if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
+    const int N = std::min(64, pow2_at_least(n_rhs));
+    TRY(ensure_ws(c, N));
+    const size_t field = (size_t)c->V * 24;
+    const int cb0 = t_lo * c->g.V3h, cb1 = t_hi * c->g.V3h;
+    c->cur = c->stream;
+    CK(cudaMemsetAsync(out, 0, (size_t)n_rhs * field * sizeof(double), c->stream));
+    for (int j0 = 0; j0 < n_rhs; j0 += N) {
+        const int n = std::min(N, n_rhs - j0);
+        TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, cb0, cb1));
+        double *res = c->b64;
+        TRY(smear_eo(c, &res, c->s64a, N, *s, cb0, cb1));
+        TRY(eo_to_canon(c, res, (double *)out + j0 * field, n, N, 0, cb0, cb1));
+    }
+    return DL_OK;
+}
+
+extern "C" int dl_apply_gamma_weights(dl_ctx *c, const void *in, void *out, int n_rhs, const double *host_w, int mode,
+                                      int accumulate) {
+    if (!c || !host_w) return fail(DL_EINVAL, "null argument");
+    if (mode != 0 && mode != 1) return fail(DL_EINVAL, "mode must be 0 or 1");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (n_rhs == 0) return DL_OK;
+    if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
+    const int T = c->dims[3];
+    const size_t nw = (size_t)n_rhs * 16 * T;      // weights
+    const size_t need = nw + (size_t)n_rhs * T * 16;  // + spin matrices
+    if (c->w_cap < need) {
+        TRY(sync(c));
+        if (c->d_w) cudaFree(c->d_w);
+        c->d_w = nullptr;
+        if (cudaMalloc((void **)&c->d_w, need * sizeof(double2)) != cudaSuccess) return fail(DL_ENOMEM, "weights");
+        c->w_cap = need;
+    }
+    c->cur = c->stream;
+    CK(cudaMemcpyAsync(c->d_w, host_w, nw * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    double2 *W = c->d_w + nw;
+    gamma_weights_kernel<<<std::max(1, (int)((n_rhs * T * 16 + 255) / 256)), 256, 0, c->stream>>>(c->d_w, n_rhs, T, mode,
+                                                                                                    c->d_gammas, W);
+    Launch l = make_launch(c, (long)n_rhs * c->V * 3, 256, 0, 16);
+    apply_spin_matrix_kernel<<<l.grid, l.block, 0, c->stream>>>((const double *)in, (double *)out, W, n_rhs, c->V,
+                                                                 2 * c->g.V3h, T, accumulate);
+    c->kernel_launches += 2;
+    CK(cudaGetLastError());
+    TRY(sync(c));  // host_w may be reused by the caller
+    return DL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// loops
+// ---------------------------------------------------------------------------
+__global__ void sum_loops_kernel(const double2 *in, int n, int stride_j, double2 *out, int count) {
+    // out[e] = sum_j in[j*stride_j + e], fixed order
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        double re = 0, im = 0;
+        for (int j = 0; j < n; ++j) {
+            const double2 v = in[(size_t)j * stride_j + e];
+            re += v.x;
+            im += v.y;
+        }
+        out[e] = make_double2(re, im);
+    }
+}
+
+__global__ void zero_kernel(double2 *p, int count) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x)
+        p[e] = make_double2(0.0, 0.0);
+}
+
+__global__ void add_kernel(double2 *acc, const double2 *v, int count) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        acc[e].x += v[e].x;
+        acc[e].y += v[e].y;
+    }
+}
+
+// spin matrices S[t][beta*4+alpha] -> L[G][t]
+__global__ void spin_to_gamma_kernel(const double2 *S, int T, const double2 *gammas, double2 *out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 16 * T) return;
+    const int G = idx / T, t = idx % T;
+    double re = 0, im = 0;
+    for (int al = 0; al < 4; ++al)
+        for (int be = 0; be < 4; ++be) {
+            const double2 g = gammas[(G * 4 + al) * 4 + be];
+            const double2 s = S[(size_t)t * 16 + be * 4 + al];
+            re += g.x * s.x - g.y * s.y;
+            im += g.x * s.y + g.y * s.x;
+        }
+    out[idx] = make_double2(re, im);
+}
+
+// Contract EO fields eta (c->b64) and phi (c->x64), width N, n right-hand sides,
+// timeslices [t_lo, t_hi) into dst[j][16][T] (other timeslices zero).
+static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, int N, int t_lo, int t_hi,
+                       double2 *dst) {
+    const int T = c->dims[3];
+    const int nt = t_hi - t_lo;
+    const int R = N > 32 ? 2 : 1;
+    const int G = N / R;
+    const int block = R == 2 ? 64 : 128;
+    int nbx = std::max(1, std::min((int)((c->g.V3h * (long)G + block - 1) / block), std::max(1, 4 * c->num_sms / (2 * nt))));
+    TRY(ensure_partials(c, (size_t)nt * 2 * nbx * N * 16));
+    ContractArgs A;
+    A.eta = eta;
+    A.phi = phi;
+    A.g = c->g;
+    A.t_lo = t_lo;
+    A.N = N;
+    A.partials = c->d_partials;
+    dim3 grid(nbx, nt, 2);
+    const size_t smem = (size_t)(block / 32) * G * R * 16 * sizeof(double2);
+    if (R == 1) contract_kernel<1><<<grid, block, smem, c->cur>>>(A);
+    else contract_kernel<2><<<grid, block, smem, c->cur>>>(A);
+    const int cnt = n * 16 * T;
+    zero_kernel<<<std::max(1, (cnt + 255) / 256), 256, 0, c->cur>>>(dst, cnt);
+    contract_final_kernel<<<dim3(nt, n), 32, 0, c->cur>>>(c->d_partials, nbx, N, t_lo, T, c->d_gammas, dst);
+    c->kernel_launches += 3;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+// Loops of the EO pair (eta in *eta_buf, phi in *phi_buf) for the requested
+// sinks into c->d_loops[j][sink][16][T]; smearing overwrites the buffers.
+static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, int sink, const dl_smear *sm, int t_lo,
+                    int t_hi, int n_sinks) {
+    const int T = c->dims[3];
+    const int cb0 = t_lo * c->g.V3h, cb1 = t_hi * c->g.V3h;
+    const int per = 16 * T;
+    int slot = 0;
+    // per-sink contraction into a scratch [n][16][T] then interleave into d_loops
+    for (int s = 0; s < 2; ++s) {
+        const int flag = s == 0 ? DL_SINK_LOCAL : DL_SINK_SMEARED;
+        if (!(sink & flag)) continue;
+        double *e = eta_buf, *f = phi_buf;
+        if (flag == DL_SINK_SMEARED) {
+            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, *sm, cb0, cb1));
+            TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, *sm, cb0, cb1));
+        }
+        // contract into the slot `slot` region of d_loops viewed as [sink][n][16][T]
+        TRY(contract_eo(c, e, f, n, N, t_lo, t_hi, c->d_loops + (size_t)slot * N * per));
+        ++slot;
+    }
+    (void)n_sinks;
+    return DL_OK;
+}
+
+extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n_rhs, int sink, const dl_smear *sm,
+                              int t_lo, int t_hi, int sum_rhs, double *host_out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (!(sink & (DL_SINK_LOCAL | DL_SINK_SMEARED)) || (sink & ~3)) return fail(DL_EINVAL, "bad sink mask");
+    if ((sink & DL_SINK_SMEARED) && !sm) return fail(DL_EINVAL, "smeared sink needs smearing parameters");
+    if ((sink & DL_SINK_SMEARED) && !c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (sm && (sm->n_iter < 0 || !std::isfinite(sm->alpha))) return fail(DL_EINVAL, "bad smearing parameters");
+    const int T = c->dims[3];
+    if (t_lo < 0 || t_hi > T || t_lo >= t_hi) return fail(DL_EINVAL, "bad timeslice range");
+    if (!host_out) return fail(DL_EINVAL, "null output");
+    const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
+    const int per = 16 * T;
+    if (n_rhs == 0) {
+        if (sum_rhs) memset(host_out, 0, sizeof(double) * 2 * n_sinks * per);
+        return DL_OK;
+    }
+    if (!eta || !phi) return fail(DL_EINVAL, "null field pointer");
+    const int N = std::min(64, pow2_at_least(n_rhs));
+    TRY(ensure_ws(c, N));
+    const size_t field = (size_t)c->V * 24;
+    const int cb0 = t_lo * c->g.V3h, cb1 = t_hi * c->g.V3h;
+    std::vector<double2> h((size_t)N * 2 * per);
+    std::vector<double> acc(sum_rhs ? (size_t)2 * n_sinks * per : 0, 0.0);
+    c->cur = c->stream;
+    // the accumulated sum over right-hand sides lives on the device (fixed order)
+    double2 *dsum = c->d_acc;
+    if (sum_rhs) zero_kernel<<<std::max(1, (2 * per + 255) / 256), 256, 0, c->stream>>>(dsum, 2 * per);
+    for (int j0 = 0; j0 < n_rhs; j0 += N) {
+        const int n = std::min(N, n_rhs - j0);
+        TRY(canon_to_eo(c, (const double *)eta + j0 * field, c->b64, n, N, 0, cb0, cb1));
+        TRY(canon_to_eo(c, (const double *)phi + j0 * field, c->x64, n, N, 0, cb0, cb1));
+        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, t_lo, t_hi, n_sinks));
+        if (sum_rhs) {
+            for (int s = 0; s < n_sinks; ++s) {
+                double2 *part = c->d_loops + (size_t)s * N * per;
+                // fold this batch's right-hand sides in order, then add to the running sum
+                sum_loops_kernel<<<std::max(1, (per + 255) / 256), 256, 0, c->stream>>>(part, n, per, part, per);
+                add_kernel<<<std::max(1, (per + 255) / 256), 256, 0, c->stream>>>(dsum + (size_t)s * per, part, per);
+                c->kernel_launches += 2;
+            }
+        } else {
+            CK(cudaMemcpyAsync(h.data(), c->d_loops, sizeof(double2) * (size_t)n_sinks * N * per,
+                               cudaMemcpyDeviceToHost, c->stream));
+            TRY(sync(c));
+            for (int j = 0; j < n; ++j)
+                for (int s = 0; s < n_sinks; ++s)
+                    memcpy(host_out + ((size_t)(j0 + j) * n_sinks + s) * per * 2, &h[(size_t)s * N * per + (size_t)j * per],
+                           sizeof(double2) * per);
+        }
+    }
+    if (sum_rhs) {
+        CK(cudaMemcpyAsync(host_out, dsum, sizeof(double2) * n_sinks * per, cudaMemcpyDeviceToHost, c->stream));
+    }
+    TRY(sync(c));
+    return DL_OK;
+}
+
+extern "C" int dl_exact_loops(dl_ctx *c, int64_t src_first, int64_t n_src, const dl_solve_params *params, int sink,
+                              const dl_smear *sm, double *host_out, dl_solve_stats *stats_sum) {
+    TRY(ready(c));
+    if (n_src < 0 || src_first < 0 || src_first + n_src > 12 * c->V) return fail(DL_EINVAL, "source range outside 0..12V");
+    if (!(sink & (DL_SINK_LOCAL | DL_SINK_SMEARED)) || (sink & ~3)) return fail(DL_EINVAL, "bad sink mask");
+    if ((sink & DL_SINK_SMEARED) && !sm) return fail(DL_EINVAL, "smeared sink needs smearing parameters");
+    if (!host_out) return fail(DL_EINVAL, "null output");
+    SolveCfg P;
+    TRY(read_params(params, &P));
+    const int T = c->dims[3];
+    const int per = 16 * T;
+    const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
+    const int N = P.batch;
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    c->cur = c->stream;
+    // accumulators: local spin matrices [T][16] at d_acc, smeared loops [16][T] at d_acc + per
+    double2 *accS = c->d_acc, *accSm = c->d_acc + per;
+    zero_kernel<<<std::max(1, (2 * per + 255) / 256), 256, 0, c->stream>>>(c->d_acc, 2 * per);
+    int worst = DL_OK;
+    long tot_it = 0, tot_outer = 0;
+    double max_res = 0.0;
+    std::vector<OuterState> os;
+    for (int64_t s0 = src_first; s0 < src_first + n_src; s0 += N) {
+        const int n = (int)std::min<int64_t>(N, src_first + n_src - s0);
+        TRY(dl_make_point_sources(c, s0, n, c->d_canon));
+        TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, 0, (int)c->Vh));
+        TRY(solve_batch(c, n, N, P, os));
+        for (int j = 0; j < n; ++j) {
+            const int st = status_of(os[j], P.tol, P.fixed_iters > 0);
+            if (st != DL_OK && worst == DL_OK) worst = st;
+            tot_it += os[j].iters;
+            tot_outer += os[j].outer;
+            max_res = std::max(max_res, os[j].full_b2 > 0 ? std::sqrt(os[j].full_r2 / os[j].full_b2) : 0.0);
+        }
+        if (sink & DL_SINK_LOCAL) {
+            point_diag_kernel<<<1, 32, 0, c->stream>>>(c->x64, c->d_coords, c->g, s0, n, N, accS);
+            c->kernel_launches++;
+        }
+        if (sink & DL_SINK_SMEARED) {
+            // timeslices touched by this batch of sources
+            const long V3 = 2L * c->g.V3h;
+            const int ta = (int)((s0 / 12) / V3), tb = (int)(((s0 + n - 1) / 12) / V3) + 1;
+            TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, ta * c->g.V3h, tb * c->g.V3h));
+            TRY(trace_eo(c, c->b64, c->x64, n, N, DL_SINK_SMEARED, sm, ta, tb, 1));
+            sum_loops_kernel<<<std::max(1, (per + 255) / 256), 256, 0, c->stream>>>(c->d_loops, n, per, c->d_loops, per);
+            add_kernel<<<std::max(1, (per + 255) / 256), 256, 0, c->stream>>>(accSm, c->d_loops, per);
+            c->kernel_launches += 2;
+        }
+    }
+    std::vector<double2> h((size_t)n_sinks * per);
+    int slot = 0;
+    if (sink & DL_SINK_LOCAL) {
+        spin_to_gamma_kernel<<<(per + 127) / 128, 128, 0, c->stream>>>(accS, T, c->d_gammas, c->d_loops);
+        c->kernel_launches++;
+        CK(cudaMemcpyAsync(h.data(), c->d_loops, sizeof(double2) * per, cudaMemcpyDeviceToHost, c->stream));
+        ++slot;
+    }
+    if (sink & DL_SINK_SMEARED) {
+        CK(cudaMemcpyAsync(h.data() + (size_t)slot * per, accSm, sizeof(double2) * per, cudaMemcpyDeviceToHost,
+                           c->stream));
+    }
+    TRY(sync(c));
+    memcpy(host_out, h.data(), sizeof(double2) * n_sinks * per);
+    if (stats_sum) {
+        stats_sum->status = worst;
+        stats_sum->iters = (int)std::min<long>(tot_it, 2147483647L);
+        stats_sum->outer = (int)std::min<long>(tot_outer, 2147483647L);
+        stats_sum->true_residual = max_res;
+    }
+    if (worst != DL_OK) fail(worst, "some point sources did not converge");
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
+// truncated solver method
+// ---------------------------------------------------------------------------
+// Fold per-right-hand-side loops of a batch into per-noise sums (fixed order).
+__global__ void fold_noise_kernel(const double2 *loops /* [sink][N][per] */, int n, int N, int per, int n_sinks, int K,
+                                  int64_t rhs0, double2 *noise /* [noise][sink][per] */, int64_t noise_base) {
+    const int count = n_sinks * per;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        const int s = e / per, q = e % per;
+        for (int j = 0; j < n; ++j) {
+            const int64_t rhs = rhs0 + j;
+            const int64_t nn = rhs / K - noise_base;
+            double2 &o = noise[((size_t)nn * n_sinks + s) * per + q];
+            const double2 v = loops[((size_t)s * N + j) * per + q];
+            o.x += v.x;
+            o.y += v.y;
+        }
+    }
+}
+
+// mean and variance of the mean per (sink, Gamma, t) over noise vectors covering t
+__global__ void tsm_combine_kernel(const double2 *lp, int n_lp, const double2 *hp, const double2 *lph, int n_hp,
+                                   int n_sinks, int T, int timed, int t0, double2 *mean, double2 *var) {
+    const int per = 16 * T;
+    const int count = n_sinks * per;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
+        const int t = e % T;
+        double m1r = 0, m1i = 0, c1 = 0;
+        for (int i = 0; i < n_lp; ++i) {
+            const int ti = t0 >= 0 ? t0 : i % T;
+            if (timed && ti != t) continue;
+            m1r += lp[(size_t)i * count + e].x;
+            m1i += lp[(size_t)i * count + e].y;
+            c1 += 1;
+        }
+        if (c1 > 0) { m1r /= c1; m1i /= c1; }
+        double v1r = 0, v1i = 0;
+        for (int i = 0; i < n_lp; ++i) {
+            const int ti = t0 >= 0 ? t0 : i % T;
+            if (timed && ti != t) continue;
+            const double dr = lp[(size_t)i * count + e].x - m1r, di = lp[(size_t)i * count + e].y - m1i;
+            v1r += dr * dr;
+            v1i += di * di;
+        }
+        double m2r = 0, m2i = 0, c2 = 0;
+        for (int i = 0; i < n_hp; ++i) {
+            const int ti = t0 >= 0 ? t0 : (n_lp + i) % T;
+            if (timed && ti != t) continue;
+            m2r += hp[(size_t)i * count + e].x - lph[(size_t)i * count + e].x;
+            m2i += hp[(size_t)i * count + e].y - lph[(size_t)i * count + e].y;
+            c2 += 1;
+        }
+        if (c2 > 0) { m2r /= c2; m2i /= c2; }
+        double v2r = 0, v2i = 0;
+        for (int i = 0; i < n_hp; ++i) {
+            const int ti = t0 >= 0 ? t0 : (n_lp + i) % T;
+            if (timed && ti != t) continue;
+            const double dr = hp[(size_t)i * count + e].x - lph[(size_t)i * count + e].x - m2r;
+            const double di = hp[(size_t)i * count + e].y - lph[(size_t)i * count + e].y - m2i;
+            v2r += dr * dr;
+            v2i += di * di;
+        }
+        const double s1 = c1 > 1 ? 1.0 / ((c1 - 1) * c1) : 0.0, s2 = c2 > 1 ? 1.0 / ((c2 - 1) * c2) : 0.0;
+        mean[e] = make_double2(m1r + m2r, m1i + m2i);
+        var[e] = make_double2(v1r * s1 + v2r * s2, v1i * s1 + v2i * s2);
+    }
+}
+
+// Solve and contract noise vectors [first, first + count) with params P; per-noise
+// loops (summed over dilution classes) are added into out[noise - first].
+static int tsm_pass(dl_ctx *c, uint64_t seed, int64_t first, int count, unsigned dil, int t0, const SolveCfg &P,
+                    int sink, const dl_smear *sm, int n_sinks, double2 *out, int *worst) {
+    const int T = c->dims[3];
+    const int per = 16 * T;
+    SourceArgs a;
+    a.coords = c->d_coords;
+    a.g = c->g;
+    a.seed = seed;
+    a.n_noise = 1;
+    a.dil_spin = (dil & DL_DIL_SPIN) ? 4 : 1;
+    a.dil_colour = (dil & DL_DIL_COLOUR) ? 3 : 1;
+    a.dil_eo = (dil & DL_DIL_EVENODD) ? 2 : 1;
+    a.dil_cubic = (dil & DL_DIL_CUBIC) ? 8 : 1;
+    a.dil_time = (dil & DL_DIL_TIME) ? 1 : 0;
+    a.t0 = t0;
+    const int K = a.dil_spin * a.dil_colour * a.dil_eo * a.dil_cubic;
+    const int N = P.batch;
+    const int64_t total = (int64_t)count * K;
+    std::vector<OuterState> os;
+    const size_t field = (size_t)c->V * 24;
+    for (int64_t r0 = 0; r0 < total; r0 += N) {
+        const int n = (int)std::min<int64_t>(N, total - r0);
+        // diluted sources r0 .. r0+n-1; a noise vector's classes may straddle batches
+        for (int64_t nv = r0 / K; nv <= (r0 + n - 1) / K; ++nv) {
+            const int64_t lo = std::max<int64_t>(r0, nv * K), hi = std::min<int64_t>(r0 + n, (nv + 1) * K);
+            a.noise_first = first + nv;
+            a.k_first = (int)(lo - nv * K);
+            a.k_count = (int)(hi - lo);
+            Launch l = make_launch(c, (long)a.k_count * c->V, 256, 0, 16);
+            z2_source_kernel<<<l.grid, l.block, 0, c->stream>>>(a, c->d_canon + (size_t)(lo - r0) * field);
+            c->kernel_launches++;
+        }
+        CK(cudaGetLastError());
+        TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, 0, (int)c->Vh));
+        TRY(solve_batch(c, n, N, P, os));
+        for (int j = 0; j < n; ++j) {
+            const int st = status_of(os[j], P.tol, P.fixed_iters > 0);
+            if (st != DL_OK && *worst == DL_OK) *worst = st;
+        }
+        int tl = 0, th = T;
+        if ((dil & DL_DIL_TIME) && t0 >= 0) { tl = t0; th = t0 + 1; }
+        // eta: re-convert sources over the contracted range (b64 was consumed by the solver)
+        TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, tl * c->g.V3h, th * c->g.V3h));
+        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, tl, th, n_sinks));
+        fold_noise_kernel<<<std::max(1, (n_sinks * per + 255) / 256), 256, 0, c->stream>>>(c->d_loops, n, N, per,
+                                                                                           n_sinks, K, r0, out, 0);
+        c->kernel_launches++;
+        CK(cudaGetLastError());
+    }
+    return DL_OK;
+}
+
+extern "C" int dl_tsm_estimate(dl_ctx *c, uint64_t seed, int n_lp, int n_hp, unsigned dil, int t0,
+                               const dl_solve_params *lp, const dl_solve_params *hp, int sink, const dl_smear *sm,
+                               double *mean_out, double *var_out, double *per_noise_out) {
+    TRY(ready(c));
+    if (n_lp < 1 || n_hp < 1) return fail(DL_EINVAL, "need at least one LP and one HP noise vector");
+    if (dil & ~31u) return fail(DL_EINVAL, "unknown dilution bits");
+    if (!(sink & (DL_SINK_LOCAL | DL_SINK_SMEARED)) || (sink & ~3)) return fail(DL_EINVAL, "bad sink mask");
+    if ((sink & DL_SINK_SMEARED) && !sm) return fail(DL_EINVAL, "smeared sink needs smearing parameters");
+    if (!mean_out || !var_out) return fail(DL_EINVAL, "null output");
+    if ((dil & DL_DIL_TIME) && t0 >= c->dims[3]) return fail(DL_EINVAL, "t0 outside the lattice");
+    SolveCfg Plp, Php;
+    TRY(read_params(lp, &Plp));
+    TRY(read_params(hp, &Php));
+    if (Plp.batch != Php.batch) return fail(DL_EINVAL, "LP and HP batch sizes must agree");
+    const int T = c->dims[3];
+    const int per = 16 * T;
+    const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
+    const int N = Plp.batch;
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    const size_t per_noise = (size_t)n_sinks * per;
+    const size_t need = per_noise * ((size_t)n_lp + 2 * (size_t)n_hp) + 2 * per_noise;
+    if (c->noise_cap < need) {
+        TRY(sync(c));
+        if (c->d_noise) cudaFree(c->d_noise);
+        c->d_noise = nullptr;
+        if (cudaMalloc((void **)&c->d_noise, need * sizeof(double2)) != cudaSuccess)
+            return fail(DL_ENOMEM, "TSM buffers");
+        c->noise_cap = need;
+    }
+    double2 *d_lp = c->d_noise, *d_hp = d_lp + per_noise * n_lp, *d_lph = d_hp + per_noise * n_hp;
+    double2 *d_mean = d_lph + per_noise * n_hp, *d_var = d_mean + per_noise;
+    c->cur = c->stream;
+    const int cnt = (int)(per_noise * ((size_t)n_lp + 2 * (size_t)n_hp));
+    zero_kernel<<<std::max(1, std::min(4096, (cnt + 255) / 256)), 256, 0, c->stream>>>(c->d_noise, cnt);
+    int worst = DL_OK;
+    TRY(tsm_pass(c, seed, 0, n_lp, dil, t0, Plp, sink, sm, n_sinks, d_lp, &worst));
+    TRY(tsm_pass(c, seed, n_lp, n_hp, dil, t0, Php, sink, sm, n_sinks, d_hp, &worst));
+    TRY(tsm_pass(c, seed, n_lp, n_hp, dil, t0, Plp, sink, sm, n_sinks, d_lph, &worst));
+    tsm_combine_kernel<<<std::max(1, (int)((per_noise + 127) / 128)), 128, 0, c->stream>>>(
+        d_lp, n_lp, d_hp, d_lph, n_hp, n_sinks, T, (dil & DL_DIL_TIME) ? 1 : 0, t0, d_mean, d_var);
+    c->kernel_launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(mean_out, d_mean, per_noise * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(var_out, d_var, per_noise * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    if (per_noise_out)
+        CK(cudaMemcpyAsync(per_noise_out, c->d_noise, (size_t)cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync(c));
+    if (worst != DL_OK) fail(worst, "some TSM solves did not converge");
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
+// measurement
+// ---------------------------------------------------------------------------
+extern "C" int dl_bench_hop(dl_ctx *c, int precision, int n_rhs, int fused, int reps, double *ms, double *bytes) {
+    TRY(ready(c));
+    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64 || reps < 1 || !ms || !bytes)
+        return fail(DL_EINVAL, "bad arguments");
+    const int N = pow2_at_least(n_rhs);
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    c->cur = c->stream;
+    const size_t ne = half_elems(c, N);
+    for (int k = 0; k < 8; ++k) CK(launch_fill(precision, c->lo[k], ne, 1234u + k, c->stream));
+    const int Vh = (int)c->Vh;
+    auto once = [&]() -> int {
+        if (fused)
+            return do_hop(c, precision, MODE_XPAY, RED_R0DOT, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr,
+                          lo_ptr(c, LRH), 0, N, -0.02, 0, Vh, c->d_partials, nullptr);
+        return do_hop(c, precision, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, nullptr, 1,
+                      N, 1.0, 0, Vh, nullptr, nullptr);
+    };
+    const bool was = c->timing;
+    c->timing = false;
+    for (int k = 0; k < 3; ++k) TRY(once());
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, c->stream);
+    for (int k = 0; k < reps; ++k) TRY(once());
+    cudaEventRecord(e1, c->stream);
+    c->timing = was;
+    CK(cudaStreamSynchronize(c->stream));
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *ms = t / reps;
+    const double S = 24.0 * storage_bytes(precision), L = 18.0 * storage_bytes(precision);
+    *bytes = (double)Vh * (8.0 * L + (double)N * (fused ? 4 : 2) * S);
+    return DL_OK;
+}

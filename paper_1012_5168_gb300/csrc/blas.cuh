@@ -1,0 +1,424 @@
+// BiCGStab vector updates, scalar recurrences and the FP64 defect-correction
+// steps, for N right-hand sides in the even-odd tile layout (see common.cuh).
+//
+// The Krylov solver is BiCGStab (van der Vorst 1992; Sec. 2 of the paper uses
+// QUDA's mixed-precision CG/BiCGStab) on the even-site Schur complement
+// Mhat = 1 - kappa^2 D_eo D_oe.  One iteration, per right-hand side:
+//
+//   v = Mhat p                 (two hops; <rhat, v> fused in the second)
+//   alpha = rho / <rhat, v>
+//   s = r - alpha v
+//   t = Mhat s                 (two hops; <t,s>, <t,t>, <rhat,s>, <rhat,t>, <s,s> fused)
+//   omega = <t,s> / <t,t>
+//   rho'  = <rhat, s - omega t> = <rhat,s> - omega <rhat,t>
+//   beta  = (rho'/rho) (alpha/omega)
+//   |r'|^2 = <s,s> - |<t,s>|^2/<t,t>      (r' = s - omega t)
+//   x += alpha p + omega s ;  r = s - omega t ;  p = r + beta (p - omega v)
+//
+// Knowing rho' and beta before the vector update lets one kernel do all three
+// updates (5 reads, 3 writes per element).  Per-right-hand-side scalars live in
+// device memory (RhsState) so whole iterations can be captured in CUDA graphs;
+// every right-hand side carries its own active flag and stops independently.
+#pragma once
+
+#include "common.cuh"
+
+namespace dl {
+
+enum { ST_OK = 0, ST_BREAKDOWN = 5, ST_NAN = 6 };
+
+struct RhsState {
+    double2 rho, alpha, omega, beta;
+    double r2;       // recursive residual norm^2 of the inner iteration
+    double r2_0;     // at the start of the inner cycle
+    double target2;  // stop the inner cycle when r2 <= target2
+    int active;      // takes part in the current iteration
+    int next_active; // takes part in the next iteration
+    int iters;       // inner iterations in this cycle
+    int status;      // ST_OK / ST_BREAKDOWN / ST_NAN (inner cycle)
+    int max_iters;   // cap on iterations in this cycle
+    int fixed;       // 1: run exactly max_iters iterations
+};
+
+struct OuterState {
+    double b2;        // |bhat|^2 (even-site Schur system)
+    double r2;        // |bhat - Mhat x|^2 (FP64 true residual of the Schur system)
+    double full_b2;   // |b|^2 (full lattice)
+    double full_r2;   // |b - M x|^2 (full lattice)
+    double tol2;      // tol^2
+    int active;       // not yet converged
+    int status;
+    int outer;        // defect-correction cycles done
+    int iters;        // inner iterations summed over cycles
+};
+
+__device__ __forceinline__ bool finite2(double2 z) { return isfinite(z.x) && isfinite(z.y); }
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// Sum partials[b][rhs][k] over blocks b for one right-hand side (one warp).
+__device__ __forceinline__ double2 warp_sum_partials(const double2 *partials, int nblocks, int N, int NV,
+                                                     int rhs, int k) {
+    double re = 0.0, im = 0.0;
+    for (int b = threadIdx.x & 31; b < nblocks; b += 32) {
+        const double2 v = partials[((size_t)b * N + rhs) * NV + k];
+        re += v.x;
+        im += v.y;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, off);
+        im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    return make_double2(re, im);
+}
+
+// ---------------------------------------------------------------------------
+// scalar kernels: grid = N blocks of 32 threads (one warp per right-hand side)
+// ---------------------------------------------------------------------------
+
+// Start an inner cycle: rho = r2 = |r_l|^2 (from partials), target and caps.
+// max_iters caps this cycle; max_total caps the iterations summed over cycles.
+static __global__ void inner_start_kernel(RhsState *st, const OuterState *os, const double2 *partials,
+                                   int nblocks, int N, double delta, int max_iters, int max_total, int fixed) {
+    const int r = blockIdx.x;
+    const double2 n2 = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    RhsState s;
+    s.rho = make_double2(n2.x, 0.0);
+    s.alpha = make_double2(1.0, 0.0);
+    s.omega = make_double2(1.0, 0.0);
+    s.beta = make_double2(0.0, 0.0);
+    s.r2 = n2.x;
+    s.r2_0 = n2.x;
+    s.target2 = delta * delta * n2.x;
+    s.iters = 0;
+    s.status = ST_OK;
+    const int left = max_total - os[r].iters;
+    s.max_iters = fixed ? max_iters : (max_iters < left ? max_iters : left);
+    s.fixed = fixed;
+    const bool on = os[r].active && n2.x > 0.0 && isfinite(n2.x) && s.max_iters > 0;
+    s.active = on;
+    s.next_active = on;
+    st[r] = s;
+}
+
+// After v = Mhat p: alpha = rho / <rhat, v>.
+static __global__ void scalar_alpha_kernel(RhsState *st, const double2 *partials, int nblocks, int N) {
+    const int r = blockIdx.x;
+    const double2 d = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    RhsState &s = st[r];
+    s.active = s.next_active;
+    if (!s.active) return;
+    const double2 a = cdiv(s.rho, d);
+    if (!(d.x * d.x + d.y * d.y > 0.0) || !finite2(a)) {
+        s.status = finite2(d) ? ST_BREAKDOWN : ST_NAN;
+        s.active = 0;
+        s.next_active = 0;
+        return;
+    }
+    s.alpha = a;
+}
+
+// After t = Mhat s: omega, rho', beta, |r'|^2 and the stopping test.
+static __global__ void scalar_omega_kernel(RhsState *st, const double2 *partials, int nblocks, int N) {
+    const int r = blockIdx.x;
+    double2 v[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) v[k] = warp_sum_partials(partials, nblocks, N, 5, r, k);
+    if (threadIdx.x != 0) return;
+    RhsState &s = st[r];
+    if (!s.active) return;
+    const double2 ts = v[0];
+    const double tt = v[1].x;
+    const double2 r0s = v[2], r0t = v[3];
+    const double ss = v[4].x;
+    s.iters += 1;
+    bool stop = false;
+    if (!(isfinite(tt) && isfinite(ss) && finite2(ts) && finite2(r0s) && finite2(r0t))) {
+        s.status = ST_NAN;
+        s.omega = make_double2(0.0, 0.0);
+        s.active = 0;  // the vector update is skipped
+        s.next_active = 0;
+        return;
+    }
+    if (!(tt > 0.0)) {
+        // t = 0: s is already the solution's residual (zero) or the iteration broke down
+        s.omega = make_double2(0.0, 0.0);
+        s.r2 = ss;
+        s.beta = make_double2(0.0, 0.0);
+        if (ss > s.target2) s.status = ST_BREAKDOWN;
+        stop = true;
+    } else {
+        const double2 om = make_double2(ts.x / tt, ts.y / tt);
+        const double2 rho_new = make_double2(r0s.x - (om.x * r0t.x - om.y * r0t.y),
+                                             r0s.y - (om.x * r0t.y + om.y * r0t.x));
+        double r2 = ss - (ts.x * ts.x + ts.y * ts.y) / tt;
+        if (r2 < 0.0) r2 = 0.0;
+        s.omega = om;
+        s.r2 = r2;
+        const double2 beta = cmul2(cdiv(rho_new, s.rho), cdiv(s.alpha, om));
+        if (!finite2(beta) || !(rho_new.x * rho_new.x + rho_new.y * rho_new.y > 0.0)) {
+            s.beta = make_double2(0.0, 0.0);
+            if (r2 > s.target2) s.status = ST_BREAKDOWN;
+            stop = true;
+        } else {
+            s.beta = beta;
+        }
+        s.rho = rho_new;
+    }
+    const bool done = s.fixed ? (s.iters >= s.max_iters)
+                              : (s.r2 <= s.target2 || s.iters >= s.max_iters);
+    s.next_active = !(stop || done);
+}
+
+static __global__ void count_active_kernel(const RhsState *st, int N, int *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int n = 0;
+        for (int r = 0; r < N; ++r) n += st[r].next_active;
+        *out = n;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels (even half field, [Vh][12][N]; thread = (element, RHS group))
+// ---------------------------------------------------------------------------
+struct VecArgs {
+    int n_elem;   // Vh * 12
+    int N;        // right-hand sides in the layout
+};
+
+// s = r - alpha v
+template <typename S, int R>
+static __global__ void __launch_bounds__(256) axpy_s_kernel(VecArgs a, const RhsState *st, const S *r_, const S *v_, S *s_) {
+    typedef typename Real<S>::type T;
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        bool any = false;
+        cx<T> al[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const RhsState &q = st[r0 + k];
+            any |= (q.active != 0);
+            al[k] = mk((T)q.alpha.x, (T)q.alpha.y);
+        }
+        if (!any) continue;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<T> rv[R], vv[R], sv[R];
+        ld_pack<S, R, true>(r_ + off, rv);
+        ld_pack<S, R, true>(v_ + off, vv);
+#pragma unroll
+        for (int k = 0; k < R; ++k) sv[k] = rv[k] - al[k] * vv[k];
+        st_pack<S, R>(s_ + off, sv);
+    }
+}
+
+// x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
+template <typename S, int R>
+static __global__ void __launch_bounds__(256) update_kernel(VecArgs a, const RhsState *st, S *x_, S *r_, S *p_,
+                                                    const S *s_, const S *t_, const S *v_) {
+    typedef typename Real<S>::type T;
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        bool any = false;
+        bool on[R];
+        cx<T> al[R], om[R], be[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const RhsState &q = st[r0 + k];
+            on[k] = q.active != 0;
+            any |= on[k];
+            al[k] = mk((T)q.alpha.x, (T)q.alpha.y);
+            om[k] = mk((T)q.omega.x, (T)q.omega.y);
+            be[k] = mk((T)q.beta.x, (T)q.beta.y);
+        }
+        if (!any) continue;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<T> xv[R], pv[R], sv[R], tv[R], vv[R], rv[R];
+        ld_pack<S, R, false>(x_ + off, xv);
+        ld_pack<S, R, false>(p_ + off, pv);
+        ld_pack<S, R, true>(s_ + off, sv);
+        ld_pack<S, R, true>(t_ + off, tv);
+        ld_pack<S, R, true>(v_ + off, vv);
+        ld_pack<S, R, false>(r_ + off, rv);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (!on[k]) continue;
+            xv[k] = xv[k] + al[k] * pv[k] + om[k] * sv[k];
+            rv[k] = sv[k] - om[k] * tv[k];
+            pv[k] = rv[k] + be[k] * (pv[k] - om[k] * vv[k]);
+        }
+        st_pack<S, R>(x_ + off, xv);
+        st_pack<S, R>(r_ + off, rv);
+        st_pack<S, R>(p_ + off, pv);
+    }
+}
+
+// Inner-cycle set-up: r_l = r64 / |r64| rounded to S; rhat = p = r_l; x_l = 0;
+// partials of |r_l|^2 (of the rounded values).  Right-hand sides that are no
+// longer active in the outer loop get zero vectors.
+template <typename S, int R>
+static __global__ void __launch_bounds__(256) inner_init_kernel(VecArgs a, const OuterState *os, const double *r64,
+                                                        S *x_, S *r_, S *rhat_, S *p_, double2 *partials) {
+    typedef typename Real<S>::type T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    cx<T> red[R][1];
+#pragma unroll
+    for (int k = 0; k < R; ++k) red[k][0] = zero<T>();
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<double> src[R];
+        ld_pack<double, R, true>(r64 + off, src);
+        cx<T> lo[R], zr[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const OuterState &o = os[r0 + k];
+            const double sc = (o.active && o.r2 > 0.0) ? 1.0 / sqrt(o.r2) : 0.0;
+            lo[k] = mk((T)(src[k].re * sc), (T)(src[k].im * sc));
+            zr[k] = zero<T>();
+        }
+        st_pack<S, R>(r_ + off, lo);
+        // re-read the rounded value for a consistent rho
+        ld_pack<S, R, false>(r_ + off, lo);
+        st_pack<S, R>(rhat_ + off, lo);
+        st_pack<S, R>(p_ + off, lo);
+        st_pack<S, R>(x_ + off, zr);
+#pragma unroll
+        for (int k = 0; k < R; ++k) cjmac(red[k][0], lo[k], lo[k]);
+    }
+    block_reduce<R, 1, T>(red, G, a.N, partials, smem);
+}
+
+// x64 += |r64| * x_l for right-hand sides active in the outer loop.
+template <typename S, int R>
+static __global__ void __launch_bounds__(256) accumulate_kernel(VecArgs a, const OuterState *os, const S *x_, double *x64) {
+    typedef typename Real<S>::type T;
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<T> xl[R];
+        ld_pack<S, R, true>(x_ + off, xl);
+        cx<double> acc[R];
+        ld_pack<double, R, false>(x64 + off, acc);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const OuterState &o = os[r0 + k];
+            if (o.active) {
+                const double sc = sqrt(o.r2);
+                acc[k].re += sc * (double)xl[k].re;
+                acc[k].im += sc * (double)xl[k].im;
+            }
+        }
+        st_pack<double, R>(x64 + off, acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// outer (FP64) bookkeeping: grid = N blocks of 32 threads
+// ---------------------------------------------------------------------------
+// mode 0: initialise (b2 = |bhat|^2 from partials, r2 = b2, active = b2 > 0)
+// mode 1: after r = bhat - Mhat x: r2 from partials, convergence test, cycle count
+static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, const double2 *partials, int nblocks,
+                                    int N, int mode, double tol, int max_outer, int max_iter) {
+    const int r = blockIdx.x;
+    const double2 n2 = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    OuterState &o = os[r];
+    if (mode == 0) {
+        o.b2 = n2.x;
+        o.r2 = n2.x;
+        o.tol2 = tol * tol;
+        o.outer = 0;
+        o.iters = 0;
+        o.status = ST_OK;
+        o.active = (n2.x > 0.0) ? 1 : 0;
+        if (!isfinite(n2.x)) { o.status = ST_NAN; o.active = 0; }
+        return;
+    }
+    if (!o.active) return;
+    o.outer += 1;
+    o.iters += st[r].iters;
+    if (st[r].status == ST_NAN) o.status = ST_NAN;
+    o.r2 = n2.x;
+    if (!isfinite(n2.x)) {
+        o.status = ST_NAN;
+        o.active = 0;
+    } else if (n2.x <= 0.25 * o.tol2 * fmin(o.b2, o.full_b2)) {
+        // half the tolerance on the Schur system, measured against the smaller of
+        // |bhat| and |b|, so that the full-lattice residual |b - M x|/|b| meets tol
+        o.active = 0;
+    } else if (o.outer >= max_outer || o.iters >= max_iter) {
+        o.active = 0;  // reported as not converged by the host
+    }
+}
+
+static __global__ void outer_count_kernel(const OuterState *os, int N, int *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int n = 0;
+        for (int r = 0; r < N; ++r) n += os[r].active;
+        *out = n;
+    }
+}
+
+// full-system norms: mode 0 -> full_b2 (sum of two partial sets), mode 1 -> full_r2
+static __global__ void full_norm_kernel(OuterState *os, const double2 *pa, int na, const double2 *pb, int nb, int N,
+                                 int mode) {
+    const int r = blockIdx.x;
+    const double2 a = warp_sum_partials(pa, na, N, 1, r, 0);
+    const double2 b = warp_sum_partials(pb, nb, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    if (mode == 0) os[r].full_b2 = a.x + b.x;
+    else os[r].full_r2 = a.x + b.x;
+}
+
+}  // namespace dl
+
+namespace dl {
+// |v|^2 per right-hand side of a half field -> partials
+template <typename S, int R>
+static __global__ void __launch_bounds__(256) norm2_kernel(VecArgs a, const S *v_, double2 *partials) {
+    typedef typename Real<S>::type T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    cx<T> red[R][1];
+#pragma unroll
+    for (int k = 0; k < R; ++k) red[k][0] = zero<T>();
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        cx<T> v[R];
+        ld_pack<S, R, true>(v_ + ((size_t)e * a.N + r0) * 2, v);
+#pragma unroll
+        for (int k = 0; k < R; ++k) cjmac(red[k][0], v[k], v[k]);
+    }
+    block_reduce<R, 1, T>(red, G, a.N, partials, smem);
+}
+
+// deterministic pseudo-random fill (for timing runs only)
+template <typename S>
+static __global__ void fill_kernel(S *v, size_t n_complex, uint32_t seed) {
+    typedef typename Real<S>::type T;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_complex; i += (size_t)gridDim.x * blockDim.x) {
+        uint32_t h = (uint32_t)i * 2654435761u ^ seed;
+        h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+        cx<T> z[1];
+        z[0] = mk((T)((h & 0xffff) / 65536.0 - 0.5), (T)((h >> 16) / 65536.0 - 0.5));
+        st_pack<S, 1>(v + 2 * i, z);
+    }
+}
+}  // namespace dl

@@ -1,0 +1,286 @@
+// Device-side building blocks shared by every kernel of the library:
+// complex arithmetic, packed loads/stores of the even-odd spinor layout in
+// FP64 / FP32 / BF16 storage, lattice geometry and block reductions.
+//
+// Internal field layout ("EO tile"): a half-lattice field of parity p holds
+// complex values at [cb][c][r] with cb the checkerboard site index
+// (lexicographic index >> 1), c = 3*spin + colour (12 components) and r the
+// right-hand side (N of them, contiguous).  Threads of one site read the N
+// right-hand sides of a component as one contiguous run, so every load of a
+// warp is a handful of full 128-byte lines.
+//
+// Gauge layout: [parity][cb][mu][9 complex] (row-major 3x3 U_mu(x)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace dl {
+
+typedef __nv_bfloat16 bf16;
+
+// ----------------------------------------------------------------------------
+// complex numbers
+// ----------------------------------------------------------------------------
+template <typename T>
+struct cx {
+    T re, im;
+};
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T r, T i) { cx<T> z; z.re = r; z.im = i; return z; }
+template <typename T>
+__device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return mk(a.re + b.re, a.im + b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return mk(a.re - b.re, a.im - b.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator-(cx<T> a) { return mk(-a.re, -a.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return mk(s * a.re, s * a.im); }
+template <typename T>
+__device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// i*a and -i*a
+template <typename T>
+__device__ __forceinline__ cx<T> ti(cx<T> a) { return mk(-a.im, a.re); }
+template <typename T>
+__device__ __forceinline__ cx<T> tmi(cx<T> a) { return mk(a.im, -a.re); }
+template <typename T>
+__device__ __forceinline__ cx<T> cj(cx<T> a) { return mk(a.re, -a.im); }
+// acc += a*b ; acc += conj(a)*b
+template <typename T>
+__device__ __forceinline__ void cmac(cx<T> &acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename T>
+__device__ __forceinline__ void cjmac(cx<T> &acc, cx<T> a, cx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename T>
+__device__ __forceinline__ cx<T> zero() { return mk<T>(T(0), T(0)); }
+
+// ----------------------------------------------------------------------------
+// storage traits: S is the element type in memory (re and im interleaved);
+// arithmetic happens in Real<S> (double for FP64 storage, float otherwise).
+// ----------------------------------------------------------------------------
+template <typename S> struct Real;
+template <> struct Real<double> { typedef double type; };
+template <> struct Real<float> { typedef float type; };
+template <> struct Real<bf16> { typedef float type; };
+
+template <typename S>
+__host__ __device__ constexpr int cbytes() { return 2 * (int)sizeof(S); }
+
+// raw loads of NB bytes (NB in 4, 8, 16, 32, 64), read-only path (NC) or plain.
+template <int NB, bool NC>
+struct RawLd;
+template <bool NC> struct RawLd<4, NC> {
+    __device__ __forceinline__ static void ld(const void *p, uint32_t *w) {
+        w[0] = NC ? __ldg((const unsigned int *)p) : *(const unsigned int *)p;
+    }
+};
+template <bool NC> struct RawLd<8, NC> {
+    __device__ __forceinline__ static void ld(const void *p, uint32_t *w) {
+        uint2 v = NC ? __ldg((const uint2 *)p) : *(const uint2 *)p;
+        w[0] = v.x; w[1] = v.y;
+    }
+};
+template <bool NC> struct RawLd<16, NC> {
+    __device__ __forceinline__ static void ld(const void *p, uint32_t *w) {
+        uint4 v = NC ? __ldg((const uint4 *)p) : *(const uint4 *)p;
+        w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+    }
+};
+template <bool NC> struct RawLd<32, NC> {
+    __device__ __forceinline__ static void ld(const void *p, uint32_t *w) {
+        RawLd<16, NC>::ld(p, w);
+        RawLd<16, NC>::ld((const char *)p + 16, w + 4);
+    }
+};
+template <bool NC> struct RawLd<64, NC> {
+    __device__ __forceinline__ static void ld(const void *p, uint32_t *w) {
+        RawLd<32, NC>::ld(p, w);
+        RawLd<32, NC>::ld((const char *)p + 32, w + 8);
+    }
+};
+
+template <int NB>
+struct RawSt;
+template <> struct RawSt<4> {
+    __device__ __forceinline__ static void st(void *p, const uint32_t *w) { *(unsigned int *)p = w[0]; }
+};
+template <> struct RawSt<8> {
+    __device__ __forceinline__ static void st(void *p, const uint32_t *w) { *(uint2 *)p = make_uint2(w[0], w[1]); }
+};
+template <> struct RawSt<16> {
+    __device__ __forceinline__ static void st(void *p, const uint32_t *w) {
+        *(uint4 *)p = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+};
+template <> struct RawSt<32> {
+    __device__ __forceinline__ static void st(void *p, const uint32_t *w) {
+        RawSt<16>::st(p, w);
+        RawSt<16>::st((char *)p + 16, w + 4);
+    }
+};
+template <> struct RawSt<64> {
+    __device__ __forceinline__ static void st(void *p, const uint32_t *w) {
+        RawSt<32>::st(p, w);
+        RawSt<32>::st((char *)p + 32, w + 8);
+    }
+};
+
+// word <-> complex conversion
+template <typename S> struct Conv;
+template <> struct Conv<double> {
+    static constexpr int W = 4;  // 32-bit words per complex
+    __device__ __forceinline__ static cx<double> get(const uint32_t *w) {
+        double r = __hiloint2double((int)w[1], (int)w[0]);
+        double i = __hiloint2double((int)w[3], (int)w[2]);
+        return mk(r, i);
+    }
+    __device__ __forceinline__ static void put(cx<double> z, uint32_t *w) {
+        w[0] = (uint32_t)__double2loint(z.re); w[1] = (uint32_t)__double2hiint(z.re);
+        w[2] = (uint32_t)__double2loint(z.im); w[3] = (uint32_t)__double2hiint(z.im);
+    }
+};
+template <> struct Conv<float> {
+    static constexpr int W = 2;
+    __device__ __forceinline__ static cx<float> get(const uint32_t *w) {
+        return mk(__uint_as_float(w[0]), __uint_as_float(w[1]));
+    }
+    __device__ __forceinline__ static void put(cx<float> z, uint32_t *w) {
+        w[0] = __float_as_uint(z.re); w[1] = __float_as_uint(z.im);
+    }
+};
+template <> struct Conv<bf16> {
+    static constexpr int W = 1;
+    __device__ __forceinline__ static cx<float> get(const uint32_t *w) {
+        __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(w);
+        float2 f = __bfloat1622float2(b);
+        return mk(f.x, f.y);
+    }
+    __device__ __forceinline__ static void put(cx<float> z, uint32_t *w) {
+        __nv_bfloat162 b = __floats2bfloat162_rn(z.re, z.im);
+        *reinterpret_cast<__nv_bfloat162 *>(w) = b;
+    }
+};
+
+// Load / store R consecutive complex values of storage type S.
+template <typename S, int R, bool NC>
+__device__ __forceinline__ void ld_pack(const S *p, cx<typename Real<S>::type> (&v)[R]) {
+    constexpr int NB = R * cbytes<S>();
+    uint32_t w[NB / 4];
+    RawLd<NB, NC>::ld(p, w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = Conv<S>::get(w + r * Conv<S>::W);
+}
+template <typename S, int R>
+__device__ __forceinline__ void st_pack(S *p, const cx<typename Real<S>::type> (&v)[R]) {
+    constexpr int NB = R * cbytes<S>();
+    uint32_t w[NB / 4];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Conv<S>::put(v[r], w + r * Conv<S>::W);
+    RawSt<NB>::st(p, w);
+}
+
+// One complex of a link (read-only path).
+template <typename S>
+__device__ __forceinline__ cx<typename Real<S>::type> ld_link(const S *p) {
+    uint32_t w[cbytes<S>() / 4];
+    RawLd<cbytes<S>(), true>::ld(p, w);
+    return Conv<S>::get(w);
+}
+
+// ----------------------------------------------------------------------------
+// geometry
+// ----------------------------------------------------------------------------
+struct Geom {
+    int L[4];       // Lx, Ly, Lz, T
+    int stride[4];  // 1, Lx, Lx*Ly, Lx*Ly*Lz
+    int Vh;         // sites per parity
+    int V3h;        // sites per parity per timeslice
+    int t_bc;       // +1 or -1
+};
+
+struct Site {
+    int c[4];
+    int i;  // lexicographic index
+};
+
+__device__ __forceinline__ Site decode(uint32_t packed, const Geom &g) {
+    Site s;
+    s.c[0] = packed & 0xff;
+    s.c[1] = (packed >> 8) & 0xff;
+    s.c[2] = (packed >> 16) & 0xff;
+    s.c[3] = (packed >> 24) & 0xff;
+    s.i = s.c[0] + g.stride[1] * s.c[1] + g.stride[2] * s.c[2] + g.stride[3] * s.c[3];
+    return s;
+}
+
+// checkerboard index of the neighbour x + mu (fwd) or x - mu
+__device__ __forceinline__ int nbr_fwd(const Site &s, const Geom &g, int mu) {
+    int i = s.i + g.stride[mu];
+    if (s.c[mu] == g.L[mu] - 1) i -= g.L[mu] * g.stride[mu];
+    return i >> 1;
+}
+__device__ __forceinline__ int nbr_bwd(const Site &s, const Geom &g, int mu) {
+    int i = s.i - g.stride[mu];
+    if (s.c[mu] == 0) i += g.L[mu] * g.stride[mu];
+    return i >> 1;
+}
+
+// ----------------------------------------------------------------------------
+// block reduction of per-thread values v[R][NV] over threads with the same
+// right-hand-side group g (= global thread index mod G, G | 32).  Writes
+// partials[blockIdx.x][g*R + rr][v] as double2.  Deterministic order.
+// smem must hold (blockDim.x/32) * G * R * NV cx<T>.
+// ----------------------------------------------------------------------------
+template <int R, int NV, typename T>
+__device__ __forceinline__ void block_reduce(cx<T> (&v)[R][NV], int G, int N, double2 *partials, void *smem_raw) {
+    cx<T> *sm = reinterpret_cast<cx<T> *>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        if (off < G) break;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                v[r][k].re += __shfl_xor_sync(0xffffffffu, v[r][k].re, off);
+                v[r][k].im += __shfl_xor_sync(0xffffffffu, v[r][k].im, off);
+            }
+    }
+    if (lane < G) {
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) sm[((warp * G + lane) * R + r) * NV + k] = v[r][k];
+    }
+    __syncthreads();
+    const int nout = G * R * NV;  // == N * NV
+    for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+        const int k = o % NV;
+        const int rr = (o / NV) % R;
+        const int gg = o / (NV * R);
+        double re = 0.0, im = 0.0;
+        for (int w = 0; w < nwarp; ++w) {
+            cx<T> z = sm[((w * G + gg) * R + rr) * NV + k];
+            re += (double)z.re;
+            im += (double)z.im;
+        }
+        partials[((size_t)blockIdx.x * N + gg * R + rr) * NV + k] = make_double2(re, im);
+    }
+}
+
+}  // namespace dl

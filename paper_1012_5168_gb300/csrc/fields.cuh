@@ -1,0 +1,434 @@
+// Field-level kernels around the solver: layout conversion, gauge reordering,
+// complex Z2 / point sources, Gaussian smearing, loop contraction and the
+// per-timeslice Gamma-weighted spin matrices of the loop gradients.
+#pragma once
+
+#include "common.cuh"
+
+namespace dl {
+
+// ---------------------------------------------------------------------------
+// canonical [rhs][V][12] complex128  <->  EO tile [2][Vh][12][N] complex128
+// thread = (parity, cb, j); cb restricted to [cb0, cb1) in both parities.
+// ---------------------------------------------------------------------------
+struct ConvArgs {
+    const uint32_t *coords;
+    Geom g;
+    int cb0, cb1;
+    int n;       // right-hand sides converted (j < n)
+    int N;       // layout width
+    int gamma5;  // negate spins 2, 3
+};
+
+static __global__ void canon_to_eo_kernel(ConvArgs a, const double *canon, double *eo) {
+    const int nsite = a.cb1 - a.cb0;
+    const long total = 2L * nsite * a.N;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % a.N);
+        const long sp = idx / a.N;
+        const int p = (int)(sp / nsite);
+        const int cb = a.cb0 + (int)(sp % nsite);
+        const Site st = decode(a.coords[(size_t)p * a.g.Vh + cb], a.g);
+        double *dst = eo + ((size_t)p * a.g.Vh + cb) * 12 * a.N * 2 + (size_t)j * 2;
+        if (j >= a.n) {
+            for (int c = 0; c < 12; ++c) *(double2 *)(dst + (size_t)c * a.N * 2) = make_double2(0.0, 0.0);
+            continue;
+        }
+        const double2 *src = (const double2 *)(canon + ((size_t)j * 2 * a.g.Vh + st.i) * 24);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 v = src[c];
+            if (a.gamma5 && c >= 6) { v.x = -v.x; v.y = -v.y; }
+            *(double2 *)(dst + (size_t)c * a.N * 2) = v;
+        }
+    }
+}
+
+static __global__ void eo_to_canon_kernel(ConvArgs a, const double *eo, double *canon) {
+    const int nsite = a.cb1 - a.cb0;
+    const long total = 2L * nsite * a.n;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % a.n);
+        const long sp = idx / a.n;
+        const int p = (int)(sp / nsite);
+        const int cb = a.cb0 + (int)(sp % nsite);
+        const Site st = decode(a.coords[(size_t)p * a.g.Vh + cb], a.g);
+        const double *src = eo + ((size_t)p * a.g.Vh + cb) * 12 * a.N * 2 + (size_t)j * 2;
+        double2 *dst = (double2 *)(canon + ((size_t)j * 2 * a.g.Vh + st.i) * 24);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 v = *(const double2 *)(src + (size_t)c * a.N * 2);
+            if (a.gamma5 && c >= 6) { v.x = -v.x; v.y = -v.y; }
+            dst[c] = v;
+        }
+    }
+}
+
+// gauge: canonical [V][4][3][3] complex128 -> EO [2][Vh][4][9] complex in S
+template <typename S>
+static __global__ void gauge_reorder_kernel(const uint32_t *coords, Geom g, const double *canon, S *eo) {
+    typedef typename Real<S>::type T;
+    const int total = 2 * g.Vh;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const Site st = decode(coords[idx], g);
+        const double2 *src = (const double2 *)(canon + (size_t)st.i * 72);
+        S *dst = eo + (size_t)idx * 72;
+        for (int k = 0; k < 36; ++k) {
+            const double2 v = src[k];
+            cx<T> z[1];
+            z[0] = mk((T)v.x, (T)v.y);
+            st_pack<S, 1>(dst + 2 * k, z);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11) and complex Z2 sources
+// ---------------------------------------------------------------------------
+struct PhiloxOut {
+    uint64_t v[4];
+};
+
+__device__ __forceinline__ PhiloxOut philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0,
+                                                   uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += W0;
+            k1 += W1;
+        }
+        const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+        const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+        const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    PhiloxOut o;
+    o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+    return o;
+}
+
+struct SourceArgs {
+    const uint32_t *coords;
+    Geom g;
+    uint64_t seed;
+    int64_t noise_first;
+    int n_noise;
+    int dil_spin, dil_colour, dil_eo, dil_cubic, dil_time;  // class counts (1 if absent); time flag
+    int t0;
+    int k_first, k_count;  // classes k_first .. k_first+k_count-1 of each noise vector are written
+};
+
+// thread = (rhs, p, cb): one site of one diluted source, canonical output
+static __global__ void z2_source_kernel(SourceArgs a, double *out) {
+    const long nsite = 2L * a.g.Vh;
+    const long total = (long)a.n_noise * a.k_count * nsite;
+    const double s2 = sqrt(0.5);  // 1/sqrt(2), rounded once
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const long rhs = idx / nsite;
+        const int sp = (int)(idx % nsite);
+        const int j = (int)(rhs / a.k_count);
+        const int k = a.k_first + (int)(rhs % a.k_count);
+        const int64_t n = a.noise_first + j;
+        const Site st = decode(a.coords[sp], a.g);
+        const PhiloxOut b = philox4x64_10((uint64_t)(st.i >> 2), (uint64_t)n, 0, 0, a.seed, 0);
+        const uint64_t w = b.v[st.i & 3];
+        // class index digits, k = ((ks*C + kc)*E + ke)*Q + kq
+        const int kq = k % a.dil_cubic;
+        const int ke = (k / a.dil_cubic) % a.dil_eo;
+        const int kc = (k / (a.dil_cubic * a.dil_eo)) % a.dil_colour;
+        const int ks = k / (a.dil_cubic * a.dil_eo * a.dil_colour);
+        bool site_on = true;
+        if (a.dil_eo > 1) site_on &= (((st.c[0] + st.c[1] + st.c[2] + st.c[3]) & 1) == ke);
+        if (a.dil_cubic > 1) site_on &= (((st.c[0] & 1) + 2 * (st.c[1] & 1) + 4 * (st.c[2] & 1)) == kq);
+        if (a.dil_time) {
+            const int tn = a.t0 >= 0 ? a.t0 : (int)(n % a.g.L[3]);
+            site_on &= (st.c[3] == tn);
+        }
+        double2 *dst = (double2 *)(out + ((size_t)rhs * 2 * a.g.Vh + st.i) * 24);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const int alpha = c / 3, col = c % 3;
+            const bool on = site_on && (a.dil_spin == 1 || alpha == ks) && (a.dil_colour == 1 || col == kc);
+            double2 v = make_double2(0.0, 0.0);
+            if (on) {
+                v.x = ((w >> (2 * c)) & 1) ? -s2 : s2;
+                v.y = ((w >> (2 * c + 1)) & 1) ? -s2 : s2;
+            }
+            dst[c] = v;
+        }
+    }
+}
+
+// point sources e_s, s = first + j, s = 12 i + c: canonical output, n fields
+static __global__ void point_source_kernel(int64_t first, int n, long V, double *out) {
+    const long total = (long)n * V * 12;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const long j = idx / (V * 12);
+        const long e = idx % (V * 12);
+        ((double2 *)out)[idx] = make_double2(e == first + j ? 1.0 : 0.0, 0.0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian smearing step on EO tile fields, both parities in one launch:
+//   out_p = a * in_p + c * H_{p,1-p} in_{1-p},
+//   (H psi)(x) = sum_{j=x,y,z} [U_j(x) psi(x+j) + U_j(x-j)^dag psi(x-j)]
+// thread = (p, cb, rhs) with cb in [cb0, cb1).
+// ---------------------------------------------------------------------------
+struct SmearArgs {
+    const double *in;   // [2][Vh][12][N]
+    double *out;
+    const double *gauge;  // [2][Vh][4][9] complex128
+    const uint32_t *coords;
+    Geom g;
+    int cb0, cb1, N;
+    double a, c;
+};
+
+static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
+    const int nsite = A.cb1 - A.cb0;
+    const int total = 2 * nsite * A.N;
+    const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int j = idx % A.N;
+        const int sp = idx / A.N;
+        const int p = sp / nsite;
+        const int cb = A.cb0 + sp % nsite;
+        const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
+        const double *inn = A.in + (size_t)(1 - p) * half;
+        cx<double> acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = zero<double>();
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+            for (int dir = 0; dir < 2; ++dir) {
+                const int nb = dir == 0 ? nbr_fwd(st, A.g, mu) : nbr_bwd(st, A.g, mu);
+                const double *up = dir == 0 ? A.gauge + (((size_t)p * A.g.Vh + cb) * 4 + mu) * 18
+                                            : A.gauge + (((size_t)(1 - p) * A.g.Vh + nb) * 4 + mu) * 18;
+                cx<double> u[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) u[k] = ld_link<double>(up + 2 * k);
+                const double *src = inn + (size_t)nb * 12 * A.N * 2 + (size_t)j * 2;
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    cx<double> v[3];
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) {
+                        const double2 q = __ldg((const double2 *)(src + (size_t)(3 * s + b) * A.N * 2));
+                        v[b] = mk(q.x, q.y);
+                    }
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            if (dir == 0) cmac(acc[3 * s + aa], u[aa * 3 + b], v[b]);
+                            else cjmac(acc[3 * s + aa], u[b * 3 + aa], v[b]);
+                        }
+                }
+            }
+        }
+        const double *y = A.in + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
+        double *o = A.out + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const double2 q = __ldg((const double2 *)(y + (size_t)k * A.N * 2));
+            *(double2 *)(o + (size_t)k * A.N * 2) =
+                make_double2(A.a * q.x + A.c * acc[k].re, A.a * q.y + A.c * acc[k].im);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// loop contraction: per timeslice t and right-hand side j,
+//   S(t)_{beta alpha} = sum_{x in t} sum_a phi_{beta a}(x) conj(eta_{alpha a}(x)),
+// grid = (bx, timeslice offset, parity); partials [(tt*2 + p)*nbx + bx][N][16]
+// ---------------------------------------------------------------------------
+struct ContractArgs {
+    const double *eta;  // EO tile [2][Vh][12][N]
+    const double *phi;
+    Geom g;
+    int t_lo;
+    int N;
+    double2 *partials;
+};
+
+template <int R>
+static __global__ void __launch_bounds__(128) contract_kernel(ContractArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int p = blockIdx.z;
+    const int t = A.t_lo + blockIdx.y;
+    const int G = A.N / R;
+    const int lgG = __ffs(G) - 1;
+    const int cb0 = t * A.g.V3h;
+    const int total = A.g.V3h << lgG;
+    const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
+    cx<double> acc[R][16];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[r][k] = zero<double>();
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int cb = cb0 + (idx >> lgG);
+        const int r0 = (idx & (G - 1)) * R;
+        const size_t base = (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)r0 * 2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<double> e[R][4], f[R][4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                cx<double> ev[R], fv[R];
+                ld_pack<double, R, true>(A.eta + base + (size_t)(3 * s + a) * A.N * 2, ev);
+                ld_pack<double, R, true>(A.phi + base + (size_t)(3 * s + a) * A.N * 2, fv);
+#pragma unroll
+                for (int r = 0; r < R; ++r) { e[r][s] = ev[r]; f[r][s] = fv[r]; }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int be = 0; be < 4; ++be)
+#pragma unroll
+                    for (int al = 0; al < 4; ++al) cjmac(acc[r][be * 4 + al], e[r][al], f[r][be]);
+        }
+    }
+    double2 *part = A.partials + ((size_t)(blockIdx.y * 2 + p) * gridDim.x) * A.N * 16;
+    // block_reduce writes partials[blockIdx.x][N][16] relative to `part`
+    block_reduce<R, 16, double>(acc, G, A.N, part, smem);
+}
+
+// final: sum partials over (parity, bx) in fixed order, then L_Gamma(t) =
+// sum_{alpha beta} Gamma_{alpha beta} S_{beta alpha}.  out[j][16][T] double2.
+// grid = (n_t, n), block = 32.
+static __global__ void contract_final_kernel(const double2 *partials, int nbx, int N, int t_lo, int T,
+                                      const double2 *gammas /* [16][4][4] */, double2 *out) {
+    const int tt = blockIdx.x;
+    const int j = blockIdx.y;
+    __shared__ double2 S[16];
+    const int lane = threadIdx.x;
+    if (lane < 16) {
+        double re = 0.0, im = 0.0;
+        for (int p = 0; p < 2; ++p)
+            for (int b = 0; b < nbx; ++b) {
+                const double2 v = partials[(((size_t)(tt * 2 + p) * nbx + b) * N + j) * 16 + lane];
+                re += v.x;
+                im += v.y;
+            }
+        S[lane] = make_double2(re, im);  // S[beta*4 + alpha]
+    }
+    __syncthreads();
+    if (lane < 16) {
+        double re = 0.0, im = 0.0;
+        for (int al = 0; al < 4; ++al)
+            for (int be = 0; be < 4; ++be) {
+                const double2 gm = gammas[(lane * 4 + al) * 4 + be];
+                const double2 s = S[be * 4 + al];
+                re += gm.x * s.x - gm.y * s.y;
+                im += gm.x * s.y + gm.y * s.x;
+            }
+        out[((size_t)j * 16 + lane) * T + (t_lo + tt)] = make_double2(re, im);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gamma-weighted spin matrices for the loop gradients
+//   mode 0: W_{j,t} = sum_G w[j][G][t] G^dag ;  mode 1: W_{j,t} = sum_G conj(w[j][G][t]) G
+// then out(x) (+)= W_{j,t(x)} in(x) on canonical fields.
+// ---------------------------------------------------------------------------
+static __global__ void gamma_weights_kernel(const double2 *w, int n, int T, int mode, const double2 *gammas,
+                                     double2 *W /* [n][T][4][4] */) {
+    const int total = n * T * 16;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx % 16;  // row*4 + col of W
+        const int t = (idx / 16) % T;
+        const int j = idx / (16 * T);
+        const int row = e / 4, col = e % 4;
+        double re = 0.0, im = 0.0;
+        for (int G = 0; G < 16; ++G) {
+            const double2 c = w[((size_t)j * 16 + G) * T + t];
+            double2 m;
+            if (mode == 0) {  // (G^dag)_{row col} = conj(G_{col row})
+                const double2 g = gammas[(G * 4 + col) * 4 + row];
+                m = make_double2(g.x, -g.y);
+                re += c.x * m.x - c.y * m.y;
+                im += c.x * m.y + c.y * m.x;
+            } else {          // conj(c) G_{row col}
+                m = gammas[(G * 4 + row) * 4 + col];
+                re += c.x * m.x + c.y * m.y;
+                im += c.x * m.y - c.y * m.x;
+            }
+        }
+        W[idx] = make_double2(re, im);
+    }
+}
+
+static __global__ void apply_spin_matrix_kernel(const double *in, double *out, const double2 *W, int n, long V, int V3,
+                                         int T, int accumulate) {
+    const long total = (long)n * V * 3;  // thread = (j, site, colour)
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int a = (int)(idx % 3);
+        const long js = idx / 3;
+        const long i = js % V;
+        const long j = js / V;
+        const int t = (int)(i / V3);
+        const double2 *src = (const double2 *)in + js * 12;
+        double2 *dst = (double2 *)out + js * 12;
+        const double2 *m = W + ((size_t)j * T + t) * 16;
+        double2 v[4];
+        for (int s = 0; s < 4; ++s) v[s] = src[3 * s + a];
+        for (int r = 0; r < 4; ++r) {
+            double re = 0.0, im = 0.0;
+            for (int s = 0; s < 4; ++s) {
+                const double2 g = m[r * 4 + s];
+                re += g.x * v[s].x - g.y * v[s].y;
+                im += g.x * v[s].y + g.y * v[s].x;
+            }
+            if (accumulate) {
+                const double2 o = dst[3 * r + a];
+                re += o.x;
+                im += o.y;
+            }
+            dst[3 * r + a] = make_double2(re, im);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exact loops from point-source solutions (EO tile layout): for right-hand
+// side j solving e_s (s = first + j = 12 i + 3 alpha + a), add phi_{beta a}(i)
+// to S(t_i)_{beta alpha}.  One thread, fixed order (deterministic).
+// acc: [T][4][4] double2 (beta*4 + alpha)
+// ---------------------------------------------------------------------------
+static __global__ void point_diag_kernel(const double *phi_eo, const uint32_t *coords, Geom g, int64_t first, int n, int N,
+                                  double2 *acc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    (void)coords;
+    const int V3 = 2 * g.V3h;
+    for (int j = 0; j < n; ++j) {
+        const int64_t s = first + j;
+        const int i = (int)(s / 12);
+        const int c = (int)(s % 12);
+        const int alpha = c / 3, a = c % 3;
+        // parity and cb of lexicographic site i
+        int rem = i;
+        const int x = rem % g.L[0]; rem /= g.L[0];
+        const int y = rem % g.L[1]; rem /= g.L[1];
+        const int z = rem % g.L[2]; rem /= g.L[2];
+        const int t = rem;
+        const int p = (x + y + z + t) & 1;
+        const int cb = i >> 1;
+        const double *site = phi_eo + ((size_t)p * g.Vh + cb) * 12 * N * 2 + (size_t)j * 2;
+        for (int beta = 0; beta < 4; ++beta) {
+            const double2 v = *(const double2 *)(site + (size_t)(3 * beta + a) * N * 2);
+            double2 &o = acc[((size_t)t * 4 + beta) * 4 + alpha];
+            o.x += v.x;
+            o.y += v.y;
+        }
+        (void)V3;
+    }
+}
+
+}  // namespace dl

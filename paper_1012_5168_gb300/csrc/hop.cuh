@@ -1,0 +1,266 @@
+// Even-odd Wilson hopping term for N right-hand sides.
+//
+//   (D_{p,1-p} psi)(x) = sum_mu [ (1 - g_mu) U_mu(x) psi(x + mu)
+//                               + (1 + g_mu) U_mu(x - mu)^dag psi(x - mu) ]
+//
+// for x of parity p (Sec. 2: the N_f = 2 Wilson matrix M = 1 - kappa D; the
+// even-odd split of D is the Schur-complement preconditioning of the solver).
+//
+// Spin structure.  In the chiral (DeGrand-Rossi) basis every g_mu has the block
+// form [[0, X_mu], [X_mu^dag, 0]] with X_1 = i sigma_x, X_2 = -i sigma_y,
+// X_3 = i sigma_z, X_4 = 1 (all unitary).  Hence for sign s = -1 (forward,
+// 1 - g_mu) or s = +1 (backward, 1 + g_mu):
+//
+//   (1 + s g_mu) psi = [ h ; s X_mu^dag h ],   h = psi_up + s X_mu psi_down,
+//
+// so one hop needs the two-spinor h (6 complex), two SU(3) products (U or
+// U^dag on h) and a reconstruction of the lower two spins with entries of X
+// that are 0, +-1, +-i.  This halves the colour work of a naive 4x4 spin
+// product.  Each thread handles one site and R right-hand sides, loading each
+// link once and reusing it for its R right-hand sides; the N right-hand sides
+// of a site are spread over N/R neighbouring threads, so the link load of a
+// warp is a broadcast.
+//
+// Epilogues (MODE): out = c*D in (PLAIN), out = y + c*D in (XPAY),
+// out = z - y - c*D in (RESID).  Reductions (RED), per right-hand side, in the
+// arithmetic precision and then FP64 across warps and blocks:
+//   R0DOT: <rhat, out>;  BICG: <out, y>, <out, out>, <rhat, y>, <rhat, out>, <y, y>;
+//   NORM: <out, out>   (<a, b> = sum conj(a) b).
+#pragma once
+
+#include "common.cuh"
+
+namespace dl {
+
+enum { MODE_PLAIN = 0, MODE_XPAY = 1, MODE_RESID = 2 };
+enum { RED_NONE = 0, RED_R0DOT = 1, RED_BICG = 2, RED_NORM = 3 };
+
+template <int RED> struct RedCount { static constexpr int n = 0; };
+template <> struct RedCount<RED_R0DOT> { static constexpr int n = 1; };
+template <> struct RedCount<RED_BICG> { static constexpr int n = 5; };
+template <> struct RedCount<RED_NORM> { static constexpr int n = 1; };
+
+struct HopArgs {
+    void *out;              // parity p half field  [Vh][12][N]
+    const void *in;         // parity 1-p half field
+    const void *y;          // parity p (XPAY / RESID)
+    const void *z;          // parity p (RESID)
+    const void *rhat;       // parity p (R0DOT / BICG)
+    const void *gauge;      // [2][Vh][4][9] complex
+    const uint32_t *coords; // [2][Vh] packed x | y<<8 | z<<16 | t<<24
+    double2 *partials;      // [gridDim.x][N][NV]
+    int p;                  // output parity
+    int N;                  // right-hand sides in the layout
+    int cb_begin, cb_end;   // output sites processed
+    double c;               // coefficient of D
+    Geom g;
+};
+
+// Load the 12 components of R right-hand sides at one neighbour site and
+// project them to the two-spinor h = psi_up + s X_mu psi_down (s = SG).
+template <typename S, int R, int MU, int SG>
+__device__ __forceinline__ void load_project(const S *src, size_t N, cx<typename Real<S>::type> (&h)[R][6]) {
+    typedef typename Real<S>::type T;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<T> q0[R], q1[R], q2[R], q3[R];
+        ld_pack<S, R, true>(src + (size_t)a * N * 2, q0);
+        ld_pack<S, R, true>(src + (size_t)(3 + a) * N * 2, q1);
+        ld_pack<S, R, true>(src + (size_t)(6 + a) * N * 2, q2);
+        ld_pack<S, R, true>(src + (size_t)(9 + a) * N * 2, q3);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const cx<T> p0 = q0[r], p1 = q1[r], p2 = q2[r], p3 = q3[r];
+            if (MU == 0) {        // X = i sigma_x : X psi_d = (i p3, i p2)
+                h[r][a] = SG > 0 ? p0 + ti(p3) : p0 - ti(p3);
+                h[r][3 + a] = SG > 0 ? p1 + ti(p2) : p1 - ti(p2);
+            } else if (MU == 1) { // X = -i sigma_y = [[0,-1],[1,0]] : X psi_d = (-p3, p2)
+                h[r][a] = SG > 0 ? p0 - p3 : p0 + p3;
+                h[r][3 + a] = SG > 0 ? p1 + p2 : p1 - p2;
+            } else if (MU == 2) { // X = i sigma_z : X psi_d = (i p2, -i p3)
+                h[r][a] = SG > 0 ? p0 + ti(p2) : p0 - ti(p2);
+                h[r][3 + a] = SG > 0 ? p1 - ti(p3) : p1 + ti(p3);
+            } else {              // X = 1
+                h[r][a] = SG > 0 ? p0 + p2 : p0 - p2;
+                h[r][3 + a] = SG > 0 ? p1 + p3 : p1 - p3;
+            }
+        }
+    }
+}
+
+// acc += [ w ; s X_mu^dag w ] (the reconstructed lower spins), s = S.
+template <typename T, int MU, int S>
+__device__ __forceinline__ void reconstruct(const cx<T> (&w)[6], cx<T> (&acc)[12]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const cx<T> w0 = w[a], w1 = w[3 + a];
+        acc[a] = acc[a] + w0;
+        acc[3 + a] = acc[3 + a] + w1;
+        // lower = s X^dag w
+        if (MU == 0) {        // X^dag w = (-i w1, -i w0)
+            acc[6 + a] = S > 0 ? acc[6 + a] + tmi(w1) : acc[6 + a] - tmi(w1);
+            acc[9 + a] = S > 0 ? acc[9 + a] + tmi(w0) : acc[9 + a] - tmi(w0);
+        } else if (MU == 1) { // X^dag w = (w1, -w0)
+            acc[6 + a] = S > 0 ? acc[6 + a] + w1 : acc[6 + a] - w1;
+            acc[9 + a] = S > 0 ? acc[9 + a] - w0 : acc[9 + a] + w0;
+        } else if (MU == 2) { // X^dag w = (-i w0, i w1)
+            acc[6 + a] = S > 0 ? acc[6 + a] + tmi(w0) : acc[6 + a] - tmi(w0);
+            acc[9 + a] = S > 0 ? acc[9 + a] + ti(w1) : acc[9 + a] - ti(w1);
+        } else {              // X^dag w = (w0, w1)
+            acc[6 + a] = S > 0 ? acc[6 + a] + w0 : acc[6 + a] - w0;
+            acc[9 + a] = S > 0 ? acc[9 + a] + w1 : acc[9 + a] - w1;
+        }
+    }
+}
+
+// w = U h (DAG = false) or U^dag h (DAG = true) on both spin components of h.
+template <typename T, bool DAG>
+__device__ __forceinline__ void su3_mul(const cx<T> (&u)[9], const cx<T> (&h)[6], cx<T> (&w)[6]) {
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            cx<T> acc = zero<T>();
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (DAG) cjmac(acc, u[b * 3 + a], h[3 * s + b]);
+                else cmac(acc, u[a * 3 + b], h[3 * s + b]);
+            }
+            w[3 * s + a] = acc;
+        }
+}
+
+template <typename S, int R, int MU>
+__device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb, int r0,
+                                        cx<typename Real<S>::type> (&acc)[R][12]) {
+    typedef typename Real<S>::type T;
+    const S *in = reinterpret_cast<const S *>(A.in);
+    const S *gauge = reinterpret_cast<const S *>(A.gauge);
+    const size_t N = (size_t)A.N;
+    // ---- forward: (1 - g_mu) U_mu(x) psi(x + mu)
+    {
+        const int nb = nbr_fwd(st, A.g, MU);
+        const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == A.g.L[3] - 1);
+        cx<T> u[9];
+        const S *up = gauge + (((size_t)A.p * A.g.Vh + cb) * 4 + MU) * 18;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k] = ld_link<S>(up + 2 * k);
+        const S *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;
+        cx<T> hh[R][6];
+        load_project<S, R, MU, -1>(src, N, hh);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cx<T> w[6];
+            cx<T> (&h)[6] = hh[r];
+            if (flip) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) h[k] = -h[k];
+            }
+            su3_mul<T, false>(u, h, w);
+            reconstruct<T, MU, -1>(w, acc[r]);
+        }
+    }
+    // ---- backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
+    {
+        const int nb = nbr_bwd(st, A.g, MU);
+        const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == 0);
+        cx<T> u[9];
+        const S *up = gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) u[k] = ld_link<S>(up + 2 * k);
+        const S *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;
+        cx<T> hh[R][6];
+        load_project<S, R, MU, +1>(src, N, hh);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cx<T> w[6];
+            cx<T> (&h)[6] = hh[r];
+            if (flip) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) h[k] = -h[k];
+            }
+            su3_mul<T, true>(u, h, w);
+            reconstruct<T, MU, +1>(w, acc[r]);
+        }
+    }
+}
+
+template <typename S, int R, int MODE, int RED>
+__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
+    typedef typename Real<S>::type T;
+    constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = A.N / R;  // a power of two dividing 32 (checked by the host)
+    const int lgG = __ffs(G) - 1;
+    const size_t N = (size_t)A.N;
+    const int total = (A.cb_end - A.cb_begin) << lgG;  // < 2^31 (checked by the host)
+    const T cD = (T)A.c;
+    cx<T> red[R][NV];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[r][k] = zero<T>();
+
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int cb = A.cb_begin + (idx >> lgG);
+        const int r0 = (idx & (G - 1)) * R;
+        const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
+        cx<T> acc[R][12];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[r][c] = zero<T>();
+        hop_dir<S, R, 0>(A, st, cb, r0, acc);
+        hop_dir<S, R, 1>(A, st, cb, r0, acc);
+        hop_dir<S, R, 2>(A, st, cb, r0, acc);
+        hop_dir<S, R, 3>(A, st, cb, r0, acc);
+
+        const size_t base = (size_t)cb * 12 * N * 2 + (size_t)r0 * 2;
+        S *out = reinterpret_cast<S *>(A.out);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t off = base + (size_t)c * N * 2;
+            cx<T> o[R];
+            if (MODE == MODE_PLAIN) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[r] = cD * acc[r][c];
+            }
+            cx<T> yv[R];
+            if (MODE == MODE_XPAY || MODE == MODE_RESID || RED == RED_BICG) {
+                ld_pack<S, R, true>(reinterpret_cast<const S *>(A.y) + off, yv);
+            }
+            if (MODE == MODE_XPAY) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[r] = yv[r] + cD * acc[r][c];
+            } else if (MODE == MODE_RESID) {
+                cx<T> zv[R];
+                ld_pack<S, R, true>(reinterpret_cast<const S *>(A.z) + off, zv);
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[r] = zv[r] - yv[r] - cD * acc[r][c];
+            }
+            st_pack<S, R>(out + off, o);
+            if (RED == RED_R0DOT || RED == RED_BICG) {
+                cx<T> rh[R];
+                ld_pack<S, R, true>(reinterpret_cast<const S *>(A.rhat) + off, rh);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (RED == RED_R0DOT) {
+                        cjmac(red[r][0], rh[r], o[r]);
+                    } else {
+                        cjmac(red[r][0], o[r], yv[r]);   // <t, s>
+                        cjmac(red[r][1], o[r], o[r]);    // <t, t>
+                        cjmac(red[r][2], rh[r], yv[r]);  // <rhat, s>
+                        cjmac(red[r][3], rh[r], o[r]);   // <rhat, t>
+                        cjmac(red[r][4], yv[r], yv[r]);  // <s, s>
+                    }
+                }
+            } else if (RED == RED_NORM) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) cjmac(red[r][0], o[r], o[r]);
+            }
+        }
+    }
+    if (RED != RED_NONE) block_reduce<R, NV, T>(red, G, A.N, A.partials, smem);
+}
+
+}  // namespace dl

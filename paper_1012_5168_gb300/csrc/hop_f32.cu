@@ -1,0 +1,28 @@
+// Wilson-hop instantiations for float storage.
+#include "launch.h"
+
+namespace dl {
+
+template <int R, int MODE, int RED>
+static cudaError_t go(const HopArgs &a, const Launch &l) {
+    hop_kernel<float, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hop_f32(int R, int mode, int red, const HopArgs &a, const Launch &l) {
+#define DL_CASE(r, m, rd) \
+    if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l);
+    DL_CASE(1, MODE_PLAIN, RED_NONE)
+    DL_CASE(1, MODE_XPAY, RED_R0DOT)
+    DL_CASE(1, MODE_XPAY, RED_BICG)
+    DL_CASE(2, MODE_PLAIN, RED_NONE)
+    DL_CASE(2, MODE_XPAY, RED_R0DOT)
+    DL_CASE(2, MODE_XPAY, RED_BICG)
+    DL_CASE(4, MODE_PLAIN, RED_NONE)
+    DL_CASE(4, MODE_XPAY, RED_R0DOT)
+    DL_CASE(4, MODE_XPAY, RED_BICG)
+#undef DL_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dl

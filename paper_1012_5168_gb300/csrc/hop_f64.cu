@@ -1,0 +1,25 @@
+// Wilson-hop instantiations for double storage.
+#include "launch.h"
+
+namespace dl {
+
+template <int R, int MODE, int RED>
+static cudaError_t go(const HopArgs &a, const Launch &l) {
+    hop_kernel<double, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, const Launch &l) {
+#define DL_CASE(r, m, rd) \
+    if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l);
+    DL_CASE(1, MODE_PLAIN, RED_NONE)
+    DL_CASE(1, MODE_XPAY, RED_NONE)
+    DL_CASE(1, MODE_XPAY, RED_R0DOT)
+    DL_CASE(1, MODE_XPAY, RED_BICG)
+    DL_CASE(1, MODE_XPAY, RED_NORM)
+    DL_CASE(1, MODE_RESID, RED_NORM)
+#undef DL_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dl

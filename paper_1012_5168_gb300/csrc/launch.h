@@ -1,0 +1,46 @@
+// Host-side launchers for the kernel templates.  Each precision's Wilson-hop
+// and vector kernels are instantiated in their own translation unit
+// (hop_f64.cu, hop_f32.cu, hop_bf16.cu) so the build compiles them in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "hop.cuh"
+#include "blas.cuh"
+
+namespace dl {
+
+enum { P_F64 = 0, P_F32 = 1, P_BF16 = 2 };
+
+struct Launch {
+    int grid;
+    int block;
+    size_t smem;
+    cudaStream_t stream;
+};
+
+// Wilson hop; R = right-hand sides per thread (1, 2 or 4).
+// Returns cudaErrorInvalidValue for a combination that is not instantiated.
+cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, const Launch &l);
+cudaError_t launch_hop_f32(int R, int mode, int red, const HopArgs &a, const Launch &l);
+cudaError_t launch_hop_bf16(int R, int mode, int red, const HopArgs &a, const Launch &l);
+
+// Vector kernels of the inner iteration, per storage precision.
+struct VecLaunch {
+    int prec;  // P_*
+    int R;
+    VecArgs a;
+    Launch l;
+};
+cudaError_t launch_axpy_s(const VecLaunch &v, const RhsState *st, const void *r, const void *vv, void *s);
+cudaError_t launch_update(const VecLaunch &v, const RhsState *st, void *x, void *r, void *p, const void *s,
+                          const void *t, const void *vv);
+cudaError_t launch_inner_init(const VecLaunch &v, const OuterState *os, const double *r64, void *x, void *r,
+                              void *rhat, void *p, double2 *partials);
+cudaError_t launch_accumulate(const VecLaunch &v, const OuterState *os, const void *x, double *x64);
+cudaError_t launch_norm2(const VecLaunch &v, const void *x, double2 *partials);
+cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s);
+
+}  // namespace dl

@@ -1,0 +1,122 @@
+"""Loop contraction, exact loops and the truncated solver method vs the oracle (GPU).
+
+Loops: relative error ||L_gpu - L_oracle|| / ||L_oracle|| per Gamma over the
+timeslices, with Gammas whose loop is below 1e-6 of ||L_1|| judged against that
+floor; the target is 1e-9 at a final residual of 1e-12.
+"""
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import loops, noise, smear, wilson
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def to_gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def loop_error(got, ref):
+    """max over Gamma of ||got_G - ref_G|| / max(||ref_G||, 1e-6 ||ref_1||)."""
+    floor = 1e-6 * np.linalg.norm(ref[0])
+    num = np.linalg.norm(got - ref, axis=-1)
+    den = np.maximum(np.linalg.norm(ref, axis=-1), floor)
+    return float((num / den).max())
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 2, 4, 8)])
+def test_trace_loops_local_and_smeared(lib, dims):
+    U = synthetic.gauge_field(dims, eps=0.45, seed=2)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(0.12)
+    eta = synthetic.random_spinor(dims, seed=1, n=5)
+    phi = synthetic.random_spinor(dims, seed=2, n=5)
+    got = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(4.0, 6))
+    ref_l = loops.stochastic_loops(eta, phi)
+    ref_s = loops.smeared_loops(U, eta, phi, 4.0, 6)
+    assert np.abs(got[:, 0] - ref_l).max() < 1e-12 * np.abs(ref_l).max()
+    assert np.abs(got[:, 1] - ref_s).max() < 1e-12 * np.abs(ref_s).max()
+    summed = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL, sum_rhs=True)
+    assert np.abs(summed[0, 0] - ref_l.sum(0)).max() < 1e-12 * np.abs(ref_l).max()
+    part = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL, t_range=(1, 3))
+    assert np.all(part[:, 0, :, 0] == 0) and np.abs(part[:, 0, :, 1:3] - ref_l[:, :, 1:3]).max() < 1e-12 * np.abs(ref_l).max()
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_exact_loops_4x4x4x4(lib, prec):
+    """All 12V point sources on 4^4, kappa = 0.10, eps = 0.3: Tr[Gamma M^-1(x,x)] per timeslice."""
+    w = synthetic.WORKLOADS["exact_4x4x4x4"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    c = lib.Context(w["dims"])
+    c.load_gauge(U)
+    c.set_kappa(w["kappa"])
+    got, st = c.exact_loops(0, 12 * 256, lib.Params(tol=w["tol"], precision=prec, batch=64), lib.SINK_LOCAL)
+    ref = loops.exact_loops_dense(U, w["kappa"], -1.0)
+    assert st["status"] == 0 and st["true_residual"] <= w["tol"]
+    assert loop_error(got[0], ref) < 1e-9
+    c.close()
+
+
+def test_exact_smeared_loops_small(lib):
+    dims, kappa = (2, 2, 2, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.5, seed=4)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    got, st = c.exact_loops(0, 12 * 32, lib.Params(tol=1e-12, precision=0, batch=32),
+                            lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(2.0, 3))
+    assert loop_error(got[0], loops.exact_loops_dense(U, kappa, -1.0)) < 1e-9
+    assert loop_error(got[1], loops.exact_smeared_loops_dense(U, kappa, 2.0, 3, -1.0)) < 1e-9
+    c.close()
+
+
+def test_stochastic_loops_end_to_end(lib):
+    """Sources -> F32 mixed solve to 1e-12 -> local + smeared loops vs the oracle chain."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=6)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    dil = noise.SPIN | noise.COLOUR | noise.TIME
+    eta = c.make_sources(seed=3, noise_first=2, n_noise=1, dilution=dil, t0=-1)
+    phi, st = c.solve(eta, lib.Params(tol=1e-12, precision=1, batch=16))
+    got = c.trace_loops(eta, phi, lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(4.0, 50))
+    eta_r = noise.make_sources(dims, 3, 2, 1, dil, t0=-1)
+    phi_r = np.stack([wilson.solve(U, e, kappa, -1.0, tol=1e-13)[0] for e in eta_r])
+    ref_l = loops.stochastic_loops(eta_r, phi_r).sum(0)
+    ref_s = loops.smeared_loops(U, eta_r, phi_r, 4.0, 50).sum(0)
+    assert loop_error(got[:, 0].sum(0), ref_l) < 1e-9
+    assert loop_error(got[:, 1].sum(0), ref_s) < 1e-9
+    c.close()
+
+
+def test_tsm_deterministic_and_combination(lib):
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=7)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    lp = lib.Params(precision=2, fixed_iters=6, batch=8)
+    hp = lib.Params(tol=1e-11, precision=1, batch=8)
+    dil = noise.SPIN | noise.TIME
+    a = c.tsm_estimate(11, 6, 3, dil, -1, lp, hp, lib.SINK_LOCAL, per_noise=True)
+    b = c.tsm_estimate(11, 6, 3, dil, -1, lp, hp, lib.SINK_LOCAL, per_noise=True)
+    assert np.array_equal(a[2], b[2]) and np.array_equal(a[0], b[0])
+    pn = a[2][:, 0]
+    T = dims[3]
+    cover = lambda first, n: np.array([[(first + i) % T == t for t in range(T)] for i in range(n)])  # noqa: E731
+    mean, var = loops.tsm_estimate(pn[:6], pn[6:9], pn[9:12], lp_cover=cover(0, 6), hp_cover=cover(6, 3))
+    assert np.allclose(a[0][0], mean, rtol=1e-12, atol=1e-12)
+    assert np.allclose(a[1][0].real + a[1][0].imag, var, rtol=1e-10, atol=1e-12)
+    # the HP loops are the exact stochastic loops of those noise vectors
+    eta = noise.make_sources(dims, 11, 6, 3, dil, t0=-1)
+    phi = np.stack([wilson.solve(U, e, kappa, -1.0, tol=1e-13)[0] for e in eta])
+    ref = loops.stochastic_loops(eta, phi).reshape(3, 4, 16, T).sum(1)
+    assert loop_error(pn[6:9].reshape(-1, T), ref.reshape(-1, T)) < 1e-8
+    c.close()

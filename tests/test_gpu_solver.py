@@ -1,0 +1,134 @@
+"""CUDA even-odd BiCGStab (FP64, FP32- and BF16-inner defect correction) vs the oracle (GPU).
+
+A solve is correct when the oracle's own FP64 M reproduces b from the
+solution: ||b - M x|| / ||b|| <= tol, evaluated on the CPU.  Solutions are also
+compared with the oracle's full-lattice BiCGStab.
+"""
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import wilson
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def to_gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def residual(U, x, b, kappa):
+    r = b - wilson.apply_m(U, x, kappa, -1.0)
+    return np.linalg.norm(r.reshape(len(b), -1), axis=1) / np.linalg.norm(b.reshape(len(b), -1), axis=1)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("graph", [1, 0])
+def test_solve_small(lib, prec, graph):
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=3)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=9, n=5)  # 5 right-hand sides, batch 4: a ragged batch
+    tol = 1e-11
+    x, st = c.solve(to_gpu(b), lib.Params(tol=tol, precision=prec, batch=4, use_graph=graph, chunk=3))
+    x = x.cpu().numpy()
+    assert all(s["status"] == 0 for s in st), st
+    res = residual(U, x, b, kappa)
+    assert np.all(res <= tol), res
+    assert all(abs(s["true_residual"] - r) < 0.05 * tol + 1e-3 * r for s, r in zip(st, res))
+    ref = np.stack([wilson.solve(U, bb, kappa, -1.0, tol=1e-13)[0] for bb in b[:2]])
+    assert np.abs(x[:2] - ref).max() / np.abs(ref).max() < 1e-9
+    c.close()
+
+
+def test_graph_and_eager_agree_bitwise(lib):
+    """The inner iteration is deterministic: graph replay == direct launches, run twice."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=1)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = to_gpu(synthetic.random_spinor(dims, seed=2, n=4))
+    outs = []
+    for graph in (1, 0, 1):
+        x, _ = c.solve(b, lib.Params(precision=2, fixed_iters=13, batch=4, use_graph=graph, chunk=5))
+        outs.append(x.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    c.close()
+
+
+def test_adjoint_solve(lib):
+    dims, kappa = (4, 4, 2, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=4)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=5, n=2)
+    x, st = c.solve_adjoint(to_gpu(b), lib.Params(tol=1e-11, precision=1))
+    x = x.cpu().numpy()
+    r = b - wilson.apply_mdag(U, x, kappa, -1.0)
+    assert np.linalg.norm(r) / np.linalg.norm(b) < 1e-11
+    c.close()
+
+
+def test_edge_cases(lib):
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=4)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    # zero source -> zero solution, converged
+    z = torch.zeros((2, 4, 4, 4, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    x, st = c.solve(z)
+    assert torch.count_nonzero(x).item() == 0 and all(s["status"] == 0 for s in st)
+    # no right-hand sides
+    e = torch.zeros((0, 4, 4, 4, 4, 4, 3), dtype=torch.complex128, device="cuda")
+    x, st = c.solve(e)
+    assert st == []
+    # iteration cap -> NOT_CONVERGED reported, no hang
+    b = to_gpu(synthetic.random_spinor(dims, seed=1, n=1))
+    with pytest.raises(lib.DlError) as err:
+        c.solve(b, lib.Params(tol=1e-12, precision=1, max_iter=3))
+    assert err.value.status == lib.NOT_CONVERGED
+    x, st = c.solve(b, lib.Params(tol=1e-12, precision=1, max_iter=3), allow_fail=True)
+    assert st[0]["status"] == lib.NOT_CONVERGED and st[0]["iters"] <= 3
+    c.close()
+
+
+def test_supercritical_kappa_stops_cleanly(lib):
+    """kappa = 0.157 on eps = 0.45 links is past the critical point: the solve gives up."""
+    w = synthetic.WORKLOADS["supercritical_8x8x8x16"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    c = lib.Context(w["dims"])
+    c.load_gauge(U)
+    c.set_kappa(w["kappa"])
+    b = to_gpu(synthetic.random_spinor(w["dims"], seed=1, n=2))
+    x, st = c.solve(b, lib.Params(tol=1e-10, precision=1, max_iter=600), allow_fail=True)
+    assert all(s["status"] in (lib.NOT_CONVERGED, lib.BREAKDOWN, lib.NAN) for s in st)
+    assert all(s["iters"] <= 600 for s in st)
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_full_size(lib, prec):
+    """The paper's lattice shape (16^3 x 32), batch 16: residual checked by the oracle on samples."""
+    w = synthetic.WORKLOADS["wilson_16x16x16x32"]
+    dims, kappa = w["dims"], w["kappa"]
+    U = synthetic.gauge_field(dims, w["eps"], w["seed"])
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    n = 16 if prec else 2
+    eta = c.make_sources(seed=1, noise_first=0, n_noise=n, dilution=0)
+    x, st = c.solve(eta, lib.Params(tol=1e-10, precision=prec, batch=16))
+    assert all(s["status"] == 0 for s in st), st
+    for j in (0, n - 1):
+        b = eta[j:j + 1].cpu().numpy()
+        res = residual(U, x[j:j + 1].cpu().numpy(), b, kappa)
+        assert res[0] <= 1e-10, res
+    c.close()
