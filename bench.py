@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the disconnected-loop hot path on GB300.
+
+One step is one pass of the whole path over one synthetic gauge configuration
+of the paper's lattice shape (16^3 x 32; Sec. 2): complex Z2 noise with
+spin x colour x even-odd dilution and time dilution by translation (64 noise
+vectors x 24 = 1536 right-hand sides per rank), the batched mixed-precision
+even-odd BiCGStab with FP64 defect correction to a true residual of 1e-10,
+and the loop contraction Tr[Gamma M^{-1}(x,x)] on each source timeslice for a
+local and a Gaussian-smeared sink (alpha = 4, 50 iterations).
+
+Printed (rank 0, one JSON line): solves/s of that step (right-hand sides
+solved to 1e-10 and contracted, summed over ranks), the end-to-end figure
+through host buffers (gauge field uploaded from the host and loops read back
+every step), the Wilson-hop roofline from CUDA events around every hop launch
+of the timed region, the plain single-right-hand-side FP64 solve rate for
+comparison, clocks, and the FP64 CPU oracle timed on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dslash HBM GB/s (% of peak); solves/s and loops/s at res 1e-10 vs plain FP64"
+WORKLOAD = dict(name="stochastic_loops_16x16x16x32", dims=(16, 16, 16, 32), kappa=0.140, eps=0.45, seed=1,
+                n_noise=64, dilution="spin*colour*evenodd*time", t0="n mod T", tol=1e-10,
+                smear_alpha=4.0, smear_iter=50)
+CHUNK_NOISE = 4  # noise vectors per solve call (96 right-hand sides)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        p = json.load(open(path))
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def read_traffic(kind: str):
+    """Per-launch DRAM bytes of the hop kernel from the committed ncu summary, if current."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "hop_traffic.md")
+    src = os.path.join(ROOT, "paper_1012_5168_gb300", "csrc", "hop.cuh")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("hop.cuh sha256") != sha:
+        return None
+    key = f"{kind} dram bytes per launch"
+    return float(vals[key]) if key in vals else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.out = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            txt, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            txt, _ = self.proc.communicate()
+        rows = [r.split(", ") for r in txt.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[4:8]):
+                if v.strip() == "Active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# oracle baseline (CPU)
+# ---------------------------------------------------------------------------
+def oracle_iters_needed() -> int:
+    path = os.path.join(ROOT, "tests", "golden", "oracle_bicgstab_iters_16x16x16x32.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            return int(line.split()[0])
+    raise RuntimeError("no iteration count in " + path)
+
+
+def oracle_sample(seconds: float = 20.0):
+    """Time the oracle's full-lattice BiCGStab on the workload for about `seconds`.
+
+    Returns (solves/s, description).  The oracle runs whole BiCGStab
+    iterations on one 16^3 x 32 Z2 source; solves/s = 1 / (seconds per iteration
+    x iterations the oracle needs for 1e-10 on this workload, from
+    tests/golden/oracle_bicgstab_iters_16x16x16x32.txt).
+    """
+    import numpy as np
+    import synthetic
+    from oracle import noise, wilson
+    w = WORKLOAD
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    b = noise.z2_noise(w["dims"], 1, 0)
+    n_it = 1
+    t_iter = None
+    while True:
+        t0 = time.perf_counter()
+        wilson.bicgstab(lambda v: wilson.apply_m(U, v, w["kappa"], -1.0), b, tol=1e-30, max_iter=n_it,
+                        max_restarts=0)
+        dt = time.perf_counter() - t0
+        # subtract the two extra matvecs of the true-residual checks (before and after)
+        t_iter = max(dt, 1e-9) / (n_it + 1.0)
+        if dt >= seconds / 4 or n_it >= 64:
+            break
+        n_it = min(64, max(n_it * 2, int(seconds / max(t_iter, 1e-3))))
+    need = oracle_iters_needed()
+    rate = 1.0 / (t_iter * need)
+    desc = (f"oracle full-lattice FP64 BiCGStab on one 16^3x32 Z2 source: {n_it} iterations timed "
+            f"({t_iter:.2f} s each), scaled by the {need} iterations it needs for 1e-10")
+    return rate, desc, np.__version__
+
+
+# ---------------------------------------------------------------------------
+# our path
+# ---------------------------------------------------------------------------
+def run_step(ctx, dl, seed, noise0, params, store_loops):
+    """One configuration's worth of the path: 64 noise vectors x 24 diluted sources."""
+    w = WORKLOAD
+    T = w["dims"][3]
+    dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_EVENODD | dl.DIL_TIME
+    K = 24
+    n_solved = 0
+    for c0 in range(0, w["n_noise"], CHUNK_NOISE):
+        nn = min(CHUNK_NOISE, w["n_noise"] - c0)
+        eta = ctx.make_sources(seed, noise0 + c0, nn, dil, t0=-1, out=store_loops["eta"][: nn * K])
+        phi, st = ctx.solve(eta, params, x=store_loops["phi"][: nn * K])
+        for k in range(nn):
+            n = noise0 + c0 + k
+            t0 = n % T
+            lo = ctx.trace_loops(eta[k * K:(k + 1) * K], phi[k * K:(k + 1) * K], dl.SINK_LOCAL | dl.SINK_SMEARED,
+                                 smear=(w["smear_alpha"], w["smear_iter"]), t_range=(t0, t0 + 1), sum_rhs=True)
+            store_loops["loops"].append(lo)
+        n_solved += nn * K
+    return n_solved
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1012_5168_gb300 as dl
+    import synthetic
+
+    w = WORKLOAD
+    prec = dl.PREC_F32 if args.precision == "f32" else dl.PREC_BF16
+    params = dl.Params(tol=w["tol"], precision=prec, batch=args.batch, use_graph=1)
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    ctx = dl.Context(w["dims"], t_bc=-1)
+    ctx.load_gauge(U)
+    ctx.set_kappa(w["kappa"])
+    K = 24
+    store = dict(eta=ctx.new_fields(CHUNK_NOISE * K), phi=ctx.new_fields(CHUNK_NOISE * K), loops=[])
+    noise0 = rank * w["n_noise"]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ---- warm-up (also captures the CUDA graphs and fills caches)
+    for s in range(args.warmup):
+        run_step(ctx, dl, 1000 + s, noise0, params, store)
+
+    # ---- timed: inputs resident in HBM
+    ctx.get_timing(reset=True)
+    ctx.set_timing(True)
+    store["loops"] = []
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solved = 0
+    for s in range(args.steps):
+        solved += run_step(ctx, dl, 1 + s, noise0, params, store)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    tim = ctx.get_timing(reset=True)
+    ctx.set_timing(False)
+    total_solved = solved * world
+    value = total_solved / (ms / 1e3)
+
+    # ---- end to end: gauge uploaded from host, loops read back, every step
+    U_host = np.ascontiguousarray(U)
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    store["loops"] = []
+    f0.record(stream)
+    e2e_solved = 0
+    for s in range(args.steps):
+        ctx.load_gauge(U_host, check_unitarity=False)
+        e2e_solved += run_step(ctx, dl, 1 + s, noise0, params, store)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = max_over_ranks(f0.elapsed_time(f1))
+    h2d = U_host.nbytes
+    d2h = sum(a.nbytes for a in store["loops"]) // max(args.steps, 1) + 24 * (w["n_noise"] * K)
+
+    # ---- plain single-right-hand-side FP64 solve rate (the comparison of the metric)
+    eta1 = ctx.make_sources(5, 0, 1, 0)
+    ctx.solve(eta1[:1], dl.Params(tol=w["tol"], precision=dl.PREC_F64, batch=1))
+    torch.cuda.synchronize()
+    n64 = 3
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eta3 = ctx.make_sources(6, 0, n64, 0)
+    g0.record(stream)
+    _, st64 = ctx.solve(eta3, dl.Params(tol=w["tol"], precision=dl.PREC_F64, batch=1))
+    g1.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = n64 / (g0.elapsed_time(g1) / 1e3)
+
+    # ---- roofline of the dominant hop kernel (low precision, events over the timed region)
+    peak, peak_src = read_peaks()
+    kinds = ["low_plain", "low_fused", "f64_plain", "f64_fused"]
+    dom = max(range(4), key=lambda k: tim["hop_ms"][k])
+    per_launch_ms = tim["hop_ms"][dom] / max(tim["hop_launches"][dom], 1)
+    per_launch_bytes = tim["hop_bytes"][dom] / max(tim["hop_launches"][dom], 1)
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = read_traffic(kinds[dom])
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": f"hop_kernel {kinds[dom]} ({args.precision} storage, batch {args.batch})",
+                "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": per_launch_bytes,
+                "launches": tim["hop_launches"][dom], "ms_per_launch": round(per_launch_ms, 5),
+                "hop_share_of_step": round(sum(tim["hop_ms"]) / ms, 3) if ms > 0 else None}
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms / args.steps, 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == dl.PREC_F32 else "bf16",
+        "data": "synthetic (seeded SU(3) links U=exp(i*0.45*H), plaquette ~0.57; complex Z2 noise)",
+        "config": {"workload": w["name"], "lattice": "16x16x16x32", "kappa": w["kappa"], "eps": w["eps"],
+                   "noise_vectors_per_gpu": w["n_noise"], "rhs_per_gpu": w["n_noise"] * K,
+                   "dilution": w["dilution"], "tol": w["tol"], "solver": "even-odd BiCGStab, "
+                   f"{args.precision} inner + FP64 defect correction, batch {args.batch}, CUDA graphs",
+                   "sinks": "local + smeared(alpha=4, n=50)", "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world} (disjoint noise ranges)"},
+        "loops_per_s": round(value / K, 3),
+        "fp64_plain_single_rhs": {"solves_per_s": round(fp64_rate, 3),
+                                  "iters": [s["iters"] for s in st64]},
+        "speedup_vs_fp64_plain": round(value / world / fp64_rate, 2),
+        "e2e": {"value": round(e2e_solved * world / (ms_e2e / 1e3), 2), "unit": "solves/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(tim["kernel_launches"]),
+        "roofline": roofline,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, desc, _ = oracle_sample(20.0)
+        line["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+def reference_arm(args, rank, world):
+    """The FP64 CPU oracle, as it stands, on the same workload and metric."""
+    if rank != 0:
+        return
+    steps = []
+    desc = ""
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, desc, _ = oracle_sample(8.0)
+        if s >= args.warmup:
+            steps.append((rate, time.perf_counter() - t0))
+    value = statistics.median(r for r, _ in steps)
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t for _, t in steps), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD["name"], "lattice": "16x16x16x32", "kappa": WORKLOAD["kappa"],
+                   "eps": WORKLOAD["eps"], "tol": WORKLOAD["tol"]},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,12 @@ class Params:
                            self.max_outer, self.batch, self.use_graph, self.chunk)
 
 
+def n_classes(dilution: int) -> int:
+    """Diluted sources per noise vector for a dilution bitmask."""
+    return ((4 if dilution & DIL_SPIN else 1) * (3 if dilution & DIL_COLOUR else 1)
+            * (2 if dilution & DIL_EVENODD else 1) * (8 if dilution & DIL_CUBIC else 1))
+
+
 def _stats(arr) -> list:
     return [dict(status=s.status, iters=s.iters, outer=s.outer, true_residual=s.true_residual) for s in arr]
 
@@ -211,9 +217,7 @@ class Context:
                     kernel_launches=int(t.kernel_launches))
 
     def make_sources(self, seed: int, noise_first: int, n_noise: int, dilution: int, t0: int = 0, out=None):
-        n = ctypes.c_int64()
-        _check(lib().dl_make_sources(self._h, seed, noise_first, 0, dilution, t0, None, ctypes.byref(n)))
-        n_rhs = n.value * n_noise
+        n_rhs = n_classes(dilution) * n_noise
         if out is None:
             out = self.new_fields(n_rhs)
         elif self._field(out, "out") < n_rhs:

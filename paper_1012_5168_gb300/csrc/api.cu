@@ -194,12 +194,11 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.g = c->g;
     int R = prec == P_F64 ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
-    while (N / R > 32) R *= 2;
     const int G = N / R;
-    const int block = 128;
+    const int block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G;
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
-    const size_t smem = NV ? (size_t)(block / 32) * G * R * NV * (prec == P_F64 ? 16 : 8) : 0;
+    const size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (prec == P_F64 ? 16 : 8) : 0;
     Launch l = make_launch(c, total, block, smem, prec == P_F64 ? 4 : 8);
     if (nblocks) *nblocks = l.grid;
     const bool timed = c->timing;
@@ -232,12 +231,12 @@ static VecLaunch vec_launch(dl_ctx *c, int prec, int N, size_t smem_per_val, int
     VecLaunch v;
     v.prec = prec;
     v.R = prec == P_F64 ? 1 : std::min(2, N);
-    while (N / v.R > 32) v.R *= 2;
     v.a.n_elem = (int)(c->Vh * 12);
     v.a.N = N;
-    const int block = 256;
+    const int block = 256;  // a multiple of G (N <= 64)
     const int G = N / v.R;
-    v.l = make_launch(c, (long)v.a.n_elem * G, block, (size_t)(block / 32) * G * v.R * smem_per_val, per_sm);
+    v.l = make_launch(c, (long)v.a.n_elem * G, block, (size_t)(block / 32) * std::min(G, 32) * v.R * smem_per_val,
+                      per_sm);
     return v;
 }
 
@@ -1065,7 +1064,7 @@ static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, i
     const int nt = t_hi - t_lo;
     const int R = N > 32 ? 2 : 1;
     const int G = N / R;
-    const int block = R == 2 ? 64 : 128;
+    const int block = R == 2 ? 64 : 128;  // a multiple of G
     int nbx = std::max(1, std::min((int)((c->g.V3h * (long)G + block - 1) / block), std::max(1, 4 * c->num_sms / (2 * nt))));
     TRY(ensure_partials(c, (size_t)nt * 2 * nbx * N * 16));
     ContractArgs A;
@@ -1076,7 +1075,7 @@ static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, i
     A.N = N;
     A.partials = c->d_partials;
     dim3 grid(nbx, nt, 2);
-    const size_t smem = (size_t)(block / 32) * G * R * 16 * sizeof(double2);
+    const size_t smem = (size_t)(block / 32) * std::min(G, 32) * R * 16 * sizeof(double2);
     if (R == 1) contract_kernel<1><<<grid, block, smem, c->cur>>>(A);
     else contract_kernel<2><<<grid, block, smem, c->cur>>>(A);
     const int cnt = n * 16 * T;

@@ -240,9 +240,12 @@ __device__ __forceinline__ int nbr_bwd(const Site &s, const Geom &g, int mu) {
 
 // ----------------------------------------------------------------------------
 // block reduction of per-thread values v[R][NV] over threads with the same
-// right-hand-side group g (= global thread index mod G, G | 32).  Writes
-// partials[blockIdx.x][g*R + rr][v] as double2.  Deterministic order.
-// smem must hold (blockDim.x/32) * G * R * NV cx<T>.
+// right-hand-side group g = (global thread index) mod G, G a power of two that
+// divides blockDim.x (so g = threadIdx.x mod G).  Writes
+// partials[blockIdx.x][g*R + rr][v] as double2, in a fixed order.
+// G <= 32: lanes l and l ^ off (off >= G) share g, reduce with shuffles first.
+// G  > 32: every lane of a warp has its own g; warps are combined in shared memory.
+// smem must hold (blockDim.x/32) * min(G, 32) * R * NV cx<T>.
 // ----------------------------------------------------------------------------
 template <int R, int NV, typename T>
 __device__ __forceinline__ void block_reduce(cx<T> (&v)[R][NV], int G, int N, double2 *partials, void *smem_raw) {
@@ -250,6 +253,7 @@ __device__ __forceinline__ void block_reduce(cx<T> (&v)[R][NV], int G, int N, do
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarp = blockDim.x >> 5;
+    const int GW = G < 32 ? G : 32;  // distinct groups per warp
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
         if (off < G) break;
@@ -261,11 +265,11 @@ __device__ __forceinline__ void block_reduce(cx<T> (&v)[R][NV], int G, int N, do
                 v[r][k].im += __shfl_xor_sync(0xffffffffu, v[r][k].im, off);
             }
     }
-    if (lane < G) {
+    if (lane < GW) {
 #pragma unroll
         for (int r = 0; r < R; ++r)
 #pragma unroll
-            for (int k = 0; k < NV; ++k) sm[((warp * G + lane) * R + r) * NV + k] = v[r][k];
+            for (int k = 0; k < NV; ++k) sm[((warp * GW + lane) * R + r) * NV + k] = v[r][k];
     }
     __syncthreads();
     const int nout = G * R * NV;  // == N * NV
@@ -273,9 +277,11 @@ __device__ __forceinline__ void block_reduce(cx<T> (&v)[R][NV], int G, int N, do
         const int k = o % NV;
         const int rr = (o / NV) % R;
         const int gg = o / (NV * R);
+        const int l = gg % GW;  // lane holding group gg
         double re = 0.0, im = 0.0;
         for (int w = 0; w < nwarp; ++w) {
-            cx<T> z = sm[((w * G + gg) * R + rr) * NV + k];
+            if (((w * 32) % G) != gg - l) continue;  // warp w's lanes hold groups (32w .. 32w+31) mod G
+            cx<T> z = sm[((w * GW + l) * R + rr) * NV + k];
             re += (double)z.re;
             im += (double)z.im;
         }
