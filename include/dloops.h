@@ -235,6 +235,17 @@ int dl_tsm_estimate(dl_ctx *ctx, uint64_t seed, int n_lp, int n_hp, unsigned dil
 int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
                  double *ms, double *bytes);
 
+/* Autotuner for the Wilson-hop launch shape (right-hand sides per thread R in
+ * {1, 2, 4}, threads per block in {64, 128, 256}) at storage precision
+ * `precision` and batch width n_rhs: times an inner iteration's hops (two plain,
+ * two fused) for each candidate on random fields and keeps the fastest for this
+ * context.  force_R / force_block > 0 restrict the candidates.  Solves tune
+ * their (precision, batch) on first use.  *R_out, *block_out, *ms_out (may be
+ * NULL) receive the choice and its time for the four hops.  Overwrites the
+ * context's inner workspace: call between solves. */
+int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_block, int *R_out,
+                int *block_out, double *ms_out);
+
 #ifdef __cplusplus
 }
 #endif

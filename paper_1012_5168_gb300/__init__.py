@@ -39,7 +39,7 @@ SYMBOLS = (
     "dl_create", "dl_destroy", "dl_last_error", "dl_status_string", "dl_load_gauge", "dl_set_kappa",
     "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
-    "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop",
+    "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
 )
 
 
@@ -104,6 +104,7 @@ def lib() -> ctypes.CDLL:
         "dl_tsm_estimate": (i, [vp, u64, i, i, ctypes.c_uint, i, P(SolveParams), P(SolveParams), i, P(Smear),
                                 vp, vp, vp]),
         "dl_bench_hop": (i, [vp, i, i, i, i, P(d), P(d)]),
+        "dl_tune_hop": (i, [vp, i, i, i, i, P(i), P(i), P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -327,3 +328,10 @@ class Context:
         ms, by = ctypes.c_double(), ctypes.c_double()
         _check(lib().dl_bench_hop(self._h, precision, n_rhs, int(fused), reps, ctypes.byref(ms), ctypes.byref(by)))
         return ms.value, by.value
+
+    def tune_hop(self, precision: int, n_rhs: int, force_R: int = 0, force_block: int = 0):
+        """Autotune (or force) the hop launch shape; returns (R, block, ms for 2 plain + 2 fused hops)."""
+        R, B, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().dl_tune_hop(self._h, precision, n_rhs, force_R, force_block, ctypes.byref(R), ctypes.byref(B),
+                                 ctypes.byref(ms)))
+        return R.value, B.value, ms.value

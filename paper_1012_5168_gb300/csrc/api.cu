@@ -107,7 +107,10 @@ struct dl_ctx {
     std::vector<cudaEvent_t> event_pool;
     dl_timing tim;
     int64_t kernel_launches = 0;
-    int hop_R[3][8];  // tuned right-hand sides per thread, [prec][log2 N]
+    int hop_R[3][8];      // right-hand sides per thread, [prec][log2 N]
+    int hop_block[3][8];  // threads per block
+    bool hop_tuned[3][8];
+    bool autotune = true;
 };
 
 // ---------------------------------------------------------------------------
@@ -195,7 +198,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     int R = prec == P_F64 ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
-    const int block = 128;  // a multiple of G (N <= 64)
+    int block = c->hop_block[prec][ilog2(N)];
+    if (block % G) block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G;
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
     const size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (prec == P_F64 ? 16 : 8) : 0;
@@ -320,6 +324,95 @@ static int ensure_partials(dl_ctx *c, size_t elems) {
 }
 
 // ---------------------------------------------------------------------------
+// autotuner: right-hand sides per thread and block size of the Wilson hop
+// ---------------------------------------------------------------------------
+// Times one inner-iteration's worth of hops (two plain, two fused) for each
+// candidate launch shape on random fields of width N and keeps the fastest.
+// Uses the inner workspace, so it runs before a solve fills it.
+static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out) {
+    const int Vh = (int)c->Vh;
+    cudaEvent_t e0 = get_event(c), e1 = get_event(c);
+    const bool was = c->timing;
+    c->timing = false;
+    int rc = DL_OK;
+    for (int it = -1; it < reps && rc == DL_OK; ++it) {
+        if (it == 0) cudaEventRecord(e0, c->cur);
+        rc = do_hop(c, prec, MODE_PLAIN, RED_NONE, c->lo[7], c->lo[3], nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh,
+                    nullptr, nullptr);
+        if (rc == DL_OK)
+            rc = do_hop(c, prec, MODE_XPAY, RED_BICG, c->lo[6], c->lo[7], c->lo[5], nullptr, c->lo[2], 0, N, -0.02, 0,
+                        Vh, c->d_partials, nullptr);
+    }
+    cudaEventRecord(e1, c->cur);
+    c->timing = was;
+    float ms = 0.f;
+    if (rc == DL_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    c->event_pool.push_back(e0);
+    c->event_pool.push_back(e1);
+    *ms_out = ms / reps;
+    return rc;
+}
+
+static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block) {
+    const int l = ilog2(N);
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    c->cur = c->stream;
+    const size_t ne = half_elems(c, N);
+    for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
+    float best = 1e30f;
+    int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l];
+    const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
+    for (int ri = 0; ri < 3; ++ri) {
+        const int R = Rs[ri];
+        if (prec == P_F64 && R != 1) continue;
+        if (R > N || (force_R && R != force_R)) continue;
+        for (int bi = 0; bi < 3; ++bi) {
+            const int B = Bs[bi];
+            if (B % (N / R) || (force_block && B != force_block)) continue;
+            c->hop_R[prec][l] = R;
+            c->hop_block[prec][l] = B;
+            float ms = 0.f;
+            TRY(time_hops(c, prec, N, 5, &ms));
+            if (ms > 0.f && ms < best) {
+                best = ms;
+                bR = R;
+                bB = B;
+            }
+        }
+    }
+    c->hop_R[prec][l] = bR;
+    c->hop_block[prec][l] = bB;
+    c->hop_tuned[prec][l] = true;
+    invalidate_graphs(c);
+    return DL_OK;
+}
+
+extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int force_block, int *R_out,
+                           int *block_out, double *ms_out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
+    if (force_R < 0 || force_block < 0) return fail(DL_EINVAL, "bad forced shape");
+    const int N = pow2_at_least(n_rhs);
+    TRY(tune_hop(c, precision, N, force_R, force_block));
+    const int l = ilog2(N);
+    if (R_out) *R_out = c->hop_R[precision][l];
+    if (block_out) *block_out = c->hop_block[precision][l];
+    if (ms_out) {
+        float ms = 0.f;
+        TRY(time_hops(c, precision, N, 10, &ms));
+        *ms_out = ms;
+    }
+    return DL_OK;
+}
+
+static int maybe_tune(dl_ctx *c, int prec, int N) {
+    if (!c->autotune || c->hop_tuned[prec][ilog2(N)]) return DL_OK;
+    return tune_hop(c, prec, N, 0, 0);
+}
+
+// ---------------------------------------------------------------------------
 // gamma basis (chiral DeGrand-Rossi), host construction
 // ---------------------------------------------------------------------------
 typedef std::complex<double> zc;
@@ -414,7 +507,11 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     c->g.t_bc = t_bc;
     memset(&c->tim, 0, sizeof(c->tim));
     for (int p = 0; p < 3; ++p)
-        for (int l = 0; l < 8; ++l) c->hop_R[p][l] = 2;
+        for (int l = 0; l < 8; ++l) {
+            c->hop_R[p][l] = 2;
+            c->hop_block[p][l] = 128;
+            c->hop_tuned[p][l] = false;
+        }
     // coordinates table
     std::vector<uint32_t> coords(V);
     for (int t = 0; t < dims[3]; ++t)
@@ -812,6 +909,8 @@ static int solve_impl(dl_ctx *c, const void *b, void *x, int n_rhs, const dl_sol
     const int N = std::min(P.batch, pow2_at_least(n_rhs));
     TRY(ensure_ws(c, N));
     TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(maybe_tune(c, P.prec, N));
+    TRY(maybe_tune(c, P_F64, N));
     const size_t field = (size_t)c->V * 24;  // doubles per canonical field
     int worst = DL_OK;
     std::vector<OuterState> os;
@@ -1184,6 +1283,8 @@ extern "C" int dl_exact_loops(dl_ctx *c, int64_t src_first, int64_t n_src, const
     const int N = P.batch;
     TRY(ensure_ws(c, N));
     TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(maybe_tune(c, P.prec, N));
+    TRY(maybe_tune(c, P_F64, N));
     c->cur = c->stream;
     // accumulators: local spin matrices [T][16] at d_acc, smeared loops [16][T] at d_acc + per
     double2 *accS = c->d_acc, *accSm = c->d_acc + per;
@@ -1385,6 +1486,9 @@ extern "C" int dl_tsm_estimate(dl_ctx *c, uint64_t seed, int n_lp, int n_hp, uns
     const int N = Plp.batch;
     TRY(ensure_ws(c, N));
     TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(maybe_tune(c, Plp.prec, N));
+    TRY(maybe_tune(c, Php.prec, N));
+    TRY(maybe_tune(c, P_F64, N));
     const size_t per_noise = (size_t)n_sinks * per;
     const size_t need = per_noise * ((size_t)n_lp + 2 * (size_t)n_hp) + 2 * per_noise;
     if (c->noise_cap < need) {
