@@ -82,7 +82,7 @@ typedef struct dl_solve_params {
                             tolerance test (a deterministic low-precision map, as the
                             truncated solver method needs); 0: iterate to tol */
     double delta;        /* inner relative residual reduction per outer cycle (mixed
-                            precision); <= 0 picks 1e-5 (F32) or 3e-3 (BF16) */
+                            precision); <= 0 picks 3e-6 (F32) or 3e-3 (BF16) */
     int max_outer;       /* cap on defect-correction cycles; <= 0 picks 60 */
     int batch;           /* right-hand sides solved together per launch (1..64, a power
                             of two for F32/BF16 >= 2); <= 0 picks 16 */
@@ -235,16 +235,18 @@ int dl_tsm_estimate(dl_ctx *ctx, uint64_t seed, int n_lp, int n_hp, unsigned dil
 int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
                  double *ms, double *bytes);
 
-/* Autotuner for the Wilson-hop launch shape (right-hand sides per thread R in
- * {1, 2, 4}, threads per block in {64, 128, 256}) at storage precision
- * `precision` and batch width n_rhs: times an inner iteration's hops (two plain,
- * two fused) for each candidate on random fields and keeps the fastest for this
- * context.  force_R / force_block > 0 restrict the candidates.  Solves tune
- * their (precision, batch) on first use.  *R_out, *block_out, *ms_out (may be
- * NULL) receive the choice and its time for the four hops.  Overwrites the
- * context's inner workspace: call between solves. */
-int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_block, int *R_out,
-                int *block_out, double *ms_out);
+/* Autotuner for the Wilson-hop launch shape at storage precision `precision`
+ * and batch width n_rhs.  The candidates are: right-hand sides per thread R in
+ * {1, 2, 4}, threads per block in {64, 128, 256}, and for FP32/BF16 the direct
+ * or the cp.async-prefetching kernel.  Each candidate runs one plain and one
+ * fused hop on random fields; the fastest is kept for this context.
+ * force_R / force_block > 0 and force_pf >= 0 restrict the candidates.  Solves
+ * tune their (precision, batch) on first use.  *R_out, *block_out, *pf_out and
+ * *ms_out (may be NULL) receive the choice and its time for one plain plus one
+ * fused hop.  The call overwrites the context's inner workspace, so make it
+ * between solves. */
+int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_block, int force_pf,
+                int *R_out, int *block_out, int *pf_out, double *ms_out);
 
 #ifdef __cplusplus
 }

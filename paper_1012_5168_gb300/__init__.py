@@ -104,7 +104,7 @@ def lib() -> ctypes.CDLL:
         "dl_tsm_estimate": (i, [vp, u64, i, i, ctypes.c_uint, i, P(SolveParams), P(SolveParams), i, P(Smear),
                                 vp, vp, vp]),
         "dl_bench_hop": (i, [vp, i, i, i, i, P(d), P(d)]),
-        "dl_tune_hop": (i, [vp, i, i, i, i, P(i), P(i), P(d)]),
+        "dl_tune_hop": (i, [vp, i, i, i, i, i, P(i), P(i), P(i), P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -329,9 +329,9 @@ class Context:
         _check(lib().dl_bench_hop(self._h, precision, n_rhs, int(fused), reps, ctypes.byref(ms), ctypes.byref(by)))
         return ms.value, by.value
 
-    def tune_hop(self, precision: int, n_rhs: int, force_R: int = 0, force_block: int = 0):
-        """Autotune (or force) the hop launch shape; returns (R, block, ms for 2 plain + 2 fused hops)."""
-        R, B, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        _check(lib().dl_tune_hop(self._h, precision, n_rhs, force_R, force_block, ctypes.byref(R), ctypes.byref(B),
-                                 ctypes.byref(ms)))
-        return R.value, B.value, ms.value
+    def tune_hop(self, precision: int, n_rhs: int, force_R: int = 0, force_block: int = 0, force_pf: int = -1):
+        """Autotune (or force) the hop launch shape; returns (R, block, pf, ms of one plain + one fused hop)."""
+        R, B, pf, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().dl_tune_hop(self._h, precision, n_rhs, force_R, force_block, force_pf, ctypes.byref(R),
+                                 ctypes.byref(B), ctypes.byref(pf), ctypes.byref(ms)))
+        return R.value, B.value, pf.value, ms.value

@@ -109,6 +109,7 @@ struct dl_ctx {
     int64_t kernel_launches = 0;
     int hop_R[3][8];      // right-hand sides per thread, [prec][log2 N]
     int hop_block[3][8];  // threads per block
+    int hop_pf[3][8];     // 1: cp.async prefetching kernel
     bool hop_tuned[3][8];
     bool autotune = true;
 };
@@ -202,8 +203,10 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     if (block % G) block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G;
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
-    const size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (prec == P_F64 ? 16 : 8) : 0;
-    Launch l = make_launch(c, total, block, smem, prec == P_F64 ? 4 : 8);
+    const int pf = prec == P_F64 ? 0 : c->hop_pf[prec][ilog2(N)];
+    size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (prec == P_F64 ? 16 : 8) : 0;
+    if (pf) smem = std::max(smem, 2 * pf_stage_bytes(prec, R) * block);
+    Launch l = make_launch(c, total, block, smem, prec == P_F64 ? 4 : (pf ? 4 : 8));
     if (nblocks) *nblocks = l.grid;
     const bool timed = c->timing;
     TimedPair tp;
@@ -220,8 +223,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     }
     cudaError_t e;
     if (prec == P_F64) e = launch_hop_f64(R, mode, red, a, l);
-    else if (prec == P_F32) e = launch_hop_f32(R, mode, red, a, l);
-    else e = launch_hop_bf16(R, mode, red, a, l);
+    else if (prec == P_F32) e = launch_hop_f32(R, mode, red, pf, a, l);
+    else e = launch_hop_bf16(R, mode, red, pf, a, l);
     if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
     c->kernel_launches++;
     if (timed) {
@@ -353,7 +356,7 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out) {
     return rc;
 }
 
-static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block) {
+static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, int force_pf) {
     const int l = ilog2(N);
     TRY(ensure_ws(c, N));
     TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
@@ -361,44 +364,52 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block) {
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
     float best = 1e30f;
-    int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l];
+    int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_pf[prec][l];
     const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
-    for (int ri = 0; ri < 3; ++ri) {
-        const int R = Rs[ri];
-        if (prec == P_F64 && R != 1) continue;
-        if (R > N || (force_R && R != force_R)) continue;
-        for (int bi = 0; bi < 3; ++bi) {
-            const int B = Bs[bi];
-            if (B % (N / R) || (force_block && B != force_block)) continue;
-            c->hop_R[prec][l] = R;
-            c->hop_block[prec][l] = B;
-            float ms = 0.f;
-            TRY(time_hops(c, prec, N, 5, &ms));
-            if (ms > 0.f && ms < best) {
-                best = ms;
-                bR = R;
-                bB = B;
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 2); ++pf) {
+        if (force_pf >= 0 && pf != force_pf) continue;
+        for (int ri = 0; ri < 3; ++ri) {
+            const int R = Rs[ri];
+            if (prec == P_F64 && R != 1) continue;
+            if (R > N || (force_R && R != force_R)) continue;
+            for (int bi = 0; bi < 3; ++bi) {
+                const int B = Bs[bi];
+                if (B % (N / R) || (force_block && B != force_block)) continue;
+                if (pf && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
+                c->hop_R[prec][l] = R;
+                c->hop_block[prec][l] = B;
+                c->hop_pf[prec][l] = pf;
+                float ms = 0.f;
+                TRY(time_hops(c, prec, N, 5, &ms));
+                if (ms > 0.f && ms < best) {
+                    best = ms;
+                    bR = R;
+                    bB = B;
+                    bP = pf;
+                }
             }
         }
     }
     c->hop_R[prec][l] = bR;
     c->hop_block[prec][l] = bB;
+    c->hop_pf[prec][l] = bP;
     c->hop_tuned[prec][l] = true;
     invalidate_graphs(c);
     return DL_OK;
 }
 
-extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int force_block, int *R_out,
-                           int *block_out, double *ms_out) {
+extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int force_block, int force_pf,
+                           int *R_out, int *block_out, int *pf_out, double *ms_out) {
     if (!c) return fail(DL_EINVAL, "null context");
     if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
     if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
     if (force_R < 0 || force_block < 0) return fail(DL_EINVAL, "bad forced shape");
     const int N = pow2_at_least(n_rhs);
-    TRY(tune_hop(c, precision, N, force_R, force_block));
+    TRY(tune_hop(c, precision, N, force_R, force_block, force_pf));
     const int l = ilog2(N);
     if (R_out) *R_out = c->hop_R[precision][l];
     if (block_out) *block_out = c->hop_block[precision][l];
+    if (pf_out) *pf_out = c->hop_pf[precision][l];
     if (ms_out) {
         float ms = 0.f;
         TRY(time_hops(c, precision, N, 10, &ms));
@@ -409,7 +420,7 @@ extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int
 
 static int maybe_tune(dl_ctx *c, int prec, int N) {
     if (!c->autotune || c->hop_tuned[prec][ilog2(N)]) return DL_OK;
-    return tune_hop(c, prec, N, 0, 0);
+    return tune_hop(c, prec, N, 0, 0, -1);
 }
 
 // ---------------------------------------------------------------------------
@@ -510,6 +521,7 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
         for (int l = 0; l < 8; ++l) {
             c->hop_R[p][l] = 2;
             c->hop_block[p][l] = 128;
+            c->hop_pf[p][l] = 0;
             c->hop_tuned[p][l] = false;
         }
     // coordinates table
@@ -798,7 +810,7 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
     s->prec = p->precision;
     s->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
     s->fixed_iters = p->fixed_iters;
-    s->delta = p->delta > 0 ? p->delta : (p->precision == DL_PREC_BF16 ? 3e-3 : (p->precision == DL_PREC_F32 ? 1e-5 : 1e-3 * p->tol));
+    s->delta = p->delta > 0 ? p->delta : (p->precision == DL_PREC_BF16 ? 3e-3 : (p->precision == DL_PREC_F32 ? 3e-6 : 1e-3 * p->tol));
     if (p->precision == DL_PREC_F64 && !(p->delta > 0)) s->delta = std::max(1e-14, 0.5 * p->tol);
     s->max_outer = p->max_outer > 0 ? p->max_outer : 60;
     int b = p->batch > 0 ? p->batch : 16;

@@ -263,4 +263,240 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     if (RED != RED_NONE) block_reduce<R, NV, T>(red, G, A.N, A.partials, smem);
 }
 
+
+// ---------------------------------------------------------------------------
+// Prefetching variant.  Each thread streams its neighbour spinors and links
+// through a private two-stage shared-memory ring with cp.async: the data of
+// the next hop direction (or of the first direction of its next site) are in
+// flight while the current direction is computed, so the memory pipeline stays
+// full without holding the loads in registers.  Shared layout
+// [stage][item][thread] keeps every warp access conflict-free.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(uint32_t dst, const void *src) {
+    if (BYTES == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+    else if (BYTES == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N_PENDING>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N_PENDING)); }
+
+template <typename S, int R>
+struct PfLayout {
+    static constexpr int PB = R * cbytes<S>();            // bytes of one packed component
+    static constexpr int CH = PB > 16 ? 16 : PB;          // bytes per cp.async
+    static constexpr int NCH = PB / CH;                   // copies per component
+    static constexpr int LB = cbytes<S>();                // bytes of one link entry
+    static constexpr int STAGE = 12 * PB + 9 * LB;        // bytes per thread per stage
+};
+
+// Issue the copies of direction D (MU = D/2, forward if D even) of site `st`.
+template <typename S, int R, int D>
+__device__ __forceinline__ void pf_issue(const HopArgs &A, const Site &st, int cb, int r0, unsigned char *stage_base,
+                                         int nthreads) {
+    typedef PfLayout<S, R> L;
+    constexpr int MU = D / 2;
+    const S *in = reinterpret_cast<const S *>(A.in);
+    const S *gauge = reinterpret_cast<const S *>(A.gauge);
+    const int nb = (D % 2 == 0) ? nbr_fwd(st, A.g, MU) : nbr_bwd(st, A.g, MU);
+    const S *src = in + (size_t)nb * 12 * A.N * 2 + (size_t)r0 * 2;
+    const S *up = (D % 2 == 0) ? gauge + (((size_t)A.p * A.g.Vh + cb) * 4 + MU) * 18
+                               : gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
+    const uint32_t base = smem_addr(stage_base) + threadIdx.x * L::CH;
+#pragma unroll
+    for (int c = 0; c < 12; ++c)
+#pragma unroll
+        for (int h = 0; h < L::NCH; ++h)
+            cp_async<L::CH>(base + (uint32_t)((c * L::NCH + h) * nthreads * L::CH),
+                            reinterpret_cast<const unsigned char *>(src + (size_t)c * A.N * 2) + h * L::CH);
+    const uint32_t lbase = smem_addr(stage_base + 12 * L::PB * nthreads) + threadIdx.x * L::LB;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) cp_async<L::LB>(lbase + (uint32_t)(k * nthreads * L::LB), up + 2 * k);
+}
+
+// Compute direction D of the current site from a landed stage.
+template <typename S, int R, int D>
+__device__ __forceinline__ void pf_compute(const HopArgs &A, const Site &st, const unsigned char *stage_base,
+                                           int nthreads, cx<typename Real<S>::type> (&acc)[R][12]) {
+    typedef typename Real<S>::type T;
+    typedef PfLayout<S, R> L;
+    constexpr int MU = D / 2;
+    constexpr int SG = (D % 2 == 0) ? -1 : +1;
+    cx<T> hh[R][6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        cx<T> q[4][R];
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp) {
+            const int c = 3 * sp + a;
+            uint32_t w[L::PB / 4];
+#pragma unroll
+            for (int h = 0; h < L::NCH; ++h) {
+                const unsigned char *p = stage_base + ((c * L::NCH + h) * nthreads + threadIdx.x) * L::CH;
+#pragma unroll
+                for (int k = 0; k < L::CH / 4; ++k) w[h * (L::CH / 4) + k] = reinterpret_cast<const uint32_t *>(p)[k];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) q[sp][r] = Conv<S>::get(w + r * Conv<S>::W);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const cx<T> p0 = q[0][r], p1 = q[1][r], p2 = q[2][r], p3 = q[3][r];
+            if (MU == 0) {
+                hh[r][a] = SG > 0 ? p0 + ti(p3) : p0 - ti(p3);
+                hh[r][3 + a] = SG > 0 ? p1 + ti(p2) : p1 - ti(p2);
+            } else if (MU == 1) {
+                hh[r][a] = SG > 0 ? p0 - p3 : p0 + p3;
+                hh[r][3 + a] = SG > 0 ? p1 + p2 : p1 - p2;
+            } else if (MU == 2) {
+                hh[r][a] = SG > 0 ? p0 + ti(p2) : p0 - ti(p2);
+                hh[r][3 + a] = SG > 0 ? p1 - ti(p3) : p1 + ti(p3);
+            } else {
+                hh[r][a] = SG > 0 ? p0 + p2 : p0 - p2;
+                hh[r][3 + a] = SG > 0 ? p1 + p3 : p1 - p3;
+            }
+        }
+    }
+    cx<T> u[9];
+    const unsigned char *lb = stage_base + 12 * L::PB * nthreads;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        uint32_t w[L::LB / 4];
+#pragma unroll
+        for (int j = 0; j < L::LB / 4; ++j)
+            w[j] = reinterpret_cast<const uint32_t *>(lb + (k * nthreads + threadIdx.x) * L::LB)[j];
+        u[k] = Conv<S>::get(w);
+    }
+    const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == ((D % 2 == 0) ? A.g.L[3] - 1 : 0));
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        cx<T> w[6];
+        cx<T>(&h)[6] = hh[r];
+        if (flip) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[k] = -h[k];
+        }
+        su3_mul<T, (D % 2 == 1)>(u, h, w);
+        reconstruct<T, MU, SG>(w, acc[r]);
+    }
+}
+
+template <typename S, int R, int MODE, int RED>
+__global__ void __launch_bounds__(256) hop_kernel_pf(HopArgs A) {
+    typedef typename Real<S>::type T;
+    typedef PfLayout<S, R> L;
+    constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int nthreads = blockDim.x;
+    unsigned char *stage[2] = {smem, smem + (size_t)L::STAGE * nthreads};
+    const int G = A.N / R;
+    const int lgG = __ffs(G) - 1;
+    const size_t N = (size_t)A.N;
+    const int total = (A.cb_end - A.cb_begin) << lgG;
+    const int stride = gridDim.x * blockDim.x;
+    const T cD = (T)A.c;
+    cx<T> red[R][NV];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[r][k] = zero<T>();
+
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int cb = 0, r0 = 0;
+    Site st;
+    if (idx < total) {
+        cb = A.cb_begin + (idx >> lgG);
+        r0 = (idx & (G - 1)) * R;
+        st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
+        pf_issue<S, R, 0>(A, st, cb, r0, stage[0], nthreads);
+    }
+    cp_commit();
+    for (; idx < total; idx += stride) {
+        cx<T> acc[R][12];
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[r][c] = zero<T>();
+        // next site (for the prefetch issued during direction 7)
+        const int nidx = idx + stride;
+        int ncb = 0, nr0 = 0;
+        Site nst = st;
+        if (nidx < total) {
+            ncb = A.cb_begin + (nidx >> lgG);
+            nr0 = (nidx & (G - 1)) * R;
+            nst = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + ncb), A.g);
+        }
+#define DL_PF_STEP(D)                                                                  \
+        {                                                                              \
+            if (D < 7) pf_issue<S, R, (D + 1) % 8>(A, st, cb, r0, stage[(D + 1) & 1], nthreads); \
+            else if (nidx < total) pf_issue<S, R, 0>(A, nst, ncb, nr0, stage[0], nthreads);     \
+            cp_commit();                                                               \
+            cp_wait<1>();                                                              \
+            pf_compute<S, R, D>(A, st, stage[D & 1], nthreads, acc);                   \
+        }
+        DL_PF_STEP(0) DL_PF_STEP(1) DL_PF_STEP(2) DL_PF_STEP(3)
+        DL_PF_STEP(4) DL_PF_STEP(5) DL_PF_STEP(6) DL_PF_STEP(7)
+#undef DL_PF_STEP
+
+        const size_t base = (size_t)cb * 12 * N * 2 + (size_t)r0 * 2;
+        S *out = reinterpret_cast<S *>(A.out);
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const size_t off = base + (size_t)c * N * 2;
+            cx<T> o[R];
+            if (MODE == MODE_PLAIN) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[r] = cD * acc[r][c];
+            }
+            cx<T> yv[R];
+            if (MODE == MODE_XPAY || MODE == MODE_RESID || RED == RED_BICG) {
+                ld_pack<S, R, true>(reinterpret_cast<const S *>(A.y) + off, yv);
+            }
+            if (MODE == MODE_XPAY) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[r] = yv[r] + cD * acc[r][c];
+            } else if (MODE == MODE_RESID) {
+                cx<T> zv[R];
+                ld_pack<S, R, true>(reinterpret_cast<const S *>(A.z) + off, zv);
+#pragma unroll
+                for (int r = 0; r < R; ++r) o[r] = zv[r] - yv[r] - cD * acc[r][c];
+            }
+            st_pack<S, R>(out + off, o);
+            if (RED == RED_R0DOT || RED == RED_BICG) {
+                cx<T> rh[R];
+                ld_pack<S, R, true>(reinterpret_cast<const S *>(A.rhat) + off, rh);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (RED == RED_R0DOT) {
+                        cjmac(red[r][0], rh[r], o[r]);
+                    } else {
+                        cjmac(red[r][0], o[r], yv[r]);
+                        cjmac(red[r][1], o[r], o[r]);
+                        cjmac(red[r][2], rh[r], yv[r]);
+                        cjmac(red[r][3], rh[r], o[r]);
+                        cjmac(red[r][4], yv[r], yv[r]);
+                    }
+                }
+            } else if (RED == RED_NORM) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) cjmac(red[r][0], o[r], o[r]);
+            }
+        }
+        st = nst;
+        cb = ncb;
+        r0 = nr0;
+    }
+    cp_wait<0>();
+    if (RED != RED_NONE) {
+        __syncthreads();  // the reduction reuses the staging buffer
+        block_reduce<R, NV, T>(red, G, A.N, A.partials, smem);
+    }
+}
 }  // namespace dl

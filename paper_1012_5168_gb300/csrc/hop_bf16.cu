@@ -1,17 +1,28 @@
-// Wilson-hop instantiations for bf16 storage.
+// Wilson-hop instantiations for bf16 storage (direct and prefetching variants).
 #include "launch.h"
 
 namespace dl {
 
 template <int R, int MODE, int RED>
-static cudaError_t go(const HopArgs &a, const Launch &l) {
-    hop_kernel<bf16, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+static cudaError_t go(const HopArgs &a, const Launch &l, int pf) {
+    if (!pf) {
+        hop_kernel<bf16, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        return cudaGetLastError();
+    }
+    static size_t opted = 0;  // largest dynamic shared memory opted in so far
+    if (l.smem > 48 * 1024 && l.smem > opted) {
+        cudaError_t e = cudaFuncSetAttribute(hop_kernel_pf<bf16, R, MODE, RED>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem);
+        if (e != cudaSuccess) return e;
+        opted = l.smem;
+    }
+    hop_kernel_pf<bf16, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_hop_bf16(int R, int mode, int red, const HopArgs &a, const Launch &l) {
+cudaError_t launch_hop_bf16(int R, int mode, int red, int pf, const HopArgs &a, const Launch &l) {
 #define DL_CASE(r, m, rd) \
-    if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l);
+    if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l, pf);
     DL_CASE(1, MODE_PLAIN, RED_NONE)
     DL_CASE(1, MODE_XPAY, RED_R0DOT)
     DL_CASE(1, MODE_XPAY, RED_BICG)

@@ -24,8 +24,15 @@ struct Launch {
 // Wilson hop; R = right-hand sides per thread (1, 2 or 4).
 // Returns cudaErrorInvalidValue for a combination that is not instantiated.
 cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, const Launch &l);
-cudaError_t launch_hop_f32(int R, int mode, int red, const HopArgs &a, const Launch &l);
-cudaError_t launch_hop_bf16(int R, int mode, int red, const HopArgs &a, const Launch &l);
+// pf = 1 selects the cp.async prefetching kernel (low precision only); its
+// dynamic shared memory is pf_stage_bytes(prec, R) * 2 * block.
+cudaError_t launch_hop_f32(int R, int mode, int red, int pf, const HopArgs &a, const Launch &l);
+cudaError_t launch_hop_bf16(int R, int mode, int red, int pf, const HopArgs &a, const Launch &l);
+
+inline size_t pf_stage_bytes(int prec, int R) {
+    const int sb = prec == P_F32 ? 4 : (prec == P_BF16 ? 2 : 8);  // bytes of one real
+    return (size_t)12 * R * 2 * sb + (size_t)9 * 2 * sb;
+}
 
 // Vector kernels of the inner iteration, per storage precision.
 struct VecLaunch {
