@@ -226,6 +226,34 @@ int dl_tsm_estimate(dl_ctx *ctx, uint64_t seed, int n_lp, int n_hp, unsigned dil
                     int sink, const dl_smear *smear,
                     double *mean_out, double *var_out, double *per_noise_out);
 
+/* --- contraction without allocation --------------------------------------- */
+
+/* The paper has no counterpart to this call.  It exists for callers that
+ * cannot call cudaMalloc, so cannot create a dl_ctx: for example, code that
+ * runs while a stream is being captured into a CUDA graph, host programs that
+ * hand their whole device-memory budget to their own allocator, or plug-ins
+ * inside another application's CUDA context.  It computes the local loops
+ * L_Gamma(t) = sum_{x in t} eta_j(x)^dag Gamma phi_j(x), the same values as
+ * dl_trace_loops with DL_SINK_LOCAL, without any context and without
+ * allocating device or host memory.
+ *
+ * dev_eta, dev_phi: canonical complex128 fields, n_rhs of them, on the current
+ * device; dims: {Lx, Ly, Lz, T}, each in [1, 256]; timeslices [t_lo, t_hi).
+ * dev_out: device memory for double [n_rhs][16][T][2]; timeslices outside the
+ * range are set to zero.  Kernels run on cuda_stream (0 = legacy default
+ * stream); the call does not synchronise.
+ *
+ * Limit: n_rhs * (t_hi - t_lo) <= 16384.  Larger requests return DL_EINVAL with
+ * a message (split them into several calls).  Per-block partial sums live in a
+ * 4 MiB array of static device storage in the library, which every GPU that
+ * loads the library holds until the process exits.  The first call on each
+ * device looks up that array's device address and uploads a 4 KiB constant
+ * Gamma table.  Make that first call before any stream capture.  All calls
+ * share the array: calls whose kernels may overlap on the GPU (other streams,
+ * other host threads) race on it and must be serialised. */
+int dl_trace_loops_noalloc(const void *dev_eta, const void *dev_phi, int n_rhs, const int dims[4], int t_lo,
+                           int t_hi, void *dev_out, void *cuda_stream);
+
 /* --- low-level kernels exposed for measurement ---------------------------- */
 
 /* Apply the even-odd hop D_{p,1-p} (p = out_parity) to an internal batch of

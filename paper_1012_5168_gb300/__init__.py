@@ -40,6 +40,7 @@ SYMBOLS = (
     "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
     "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
+    "dl_trace_loops_noalloc",
 )
 
 
@@ -105,6 +106,7 @@ def lib() -> ctypes.CDLL:
                                 vp, vp, vp]),
         "dl_bench_hop": (i, [vp, i, i, i, i, P(d), P(d)]),
         "dl_tune_hop": (i, [vp, i, i, i, i, i, P(i), P(i), P(i), P(d)]),
+        "dl_trace_loops_noalloc": (i, [vp, vp, i, P(i), i, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -143,6 +145,30 @@ def n_classes(dilution: int) -> int:
     """Diluted sources per noise vector for a dilution bitmask."""
     return ((4 if dilution & DIL_SPIN else 1) * (3 if dilution & DIL_COLOUR else 1)
             * (2 if dilution & DIL_EVENODD else 1) * (8 if dilution & DIL_CUBIC else 1))
+
+
+def trace_loops_noalloc(eta, phi, dims, t_range=None, out=None, stream=None):
+    """Local loops without a context or any allocation inside the library.
+
+    eta, phi: complex128 CUDA tensors in the canonical layout; returns (or fills)
+    a complex128 CUDA tensor [n, 16, T].  For callers that cannot allocate
+    device memory: the library keeps its partial sums in fixed static storage
+    (n * (t_hi - t_lo) <= 16384); pass a preallocated `out`.
+    """
+    import torch
+    dims = tuple(int(d) for d in dims)
+    V = int(np.prod(dims))
+    n = eta.numel() // (12 * V)
+    T = dims[3]
+    lo, hi = t_range if t_range is not None else (0, T)
+    if out is None:
+        out = torch.empty((n, 16, T), dtype=torch.complex128, device=eta.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().dl_trace_loops_noalloc(ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()), n,
+                                        (ctypes.c_int * 4)(*dims), lo, hi, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(stream)))
+    return out
 
 
 def _stats(arr) -> list:

@@ -32,6 +32,8 @@ static int fail(int code, const std::string &msg) {
     return code;
 }
 
+__attribute__((visibility("hidden"))) int dl_record_error(int code, const char *msg) { return fail(code, msg); }
+
 #define CK(call)                                                                                        \
     do {                                                                                                \
         cudaError_t e_ = (call);                                                                        \
