@@ -48,6 +48,14 @@ def parse():
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="stochastic",
+                    choices=["stochastic", "exact_4x4x4x4", "single_rhs_16x16x16x32", "tsm_8x8x8x16",
+                             "autograd"],
+                    help="stochastic: the benchmark line (default); the others measure the remaining "
+                         "configurations and print one JSON line each")
+    ap.add_argument("--hop-profile", metavar="PREC:N[:KIND]", default=None,
+                    help="time the Wilson hop alone on the 16^3x32 workload (f32|bf16|f64, batch N, kernel kind "
+                         "0 direct / 1 prefetch / 2 staged; default autotuned) and exit")
     return ap.parse_args()
 
 
@@ -199,9 +207,180 @@ def run_step(ctx, dl, seed, noise0, params, store_loops):
     return n_solved
 
 
+def hop_profile(spec: str):
+    """Time the plain and the fused Wilson hop alone (used for ncu captures)."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    import synthetic
+    parts = spec.split(":")
+    prec = {"f64": dl.PREC_F64, "f32": dl.PREC_F32, "bf16": dl.PREC_BF16}[parts[0]]
+    n = int(parts[1])
+    kind = int(parts[2]) if len(parts) > 2 else -1
+    w = WORKLOAD
+    ctx = dl.Context(w["dims"], t_bc=-1)
+    ctx.load_gauge(synthetic.gauge_field(w["dims"], w["eps"], w["seed"]))
+    ctx.set_kappa(w["kappa"])
+    shape = ctx.tune_hop(prec, n, force_pf=kind)
+    out = {"precision": parts[0], "n_rhs": n, "R": shape[0], "block": shape[1], "kind": shape[2]}
+    for fused in (0, 1):
+        ms, by = ctx.bench_hop(prec, n, fused, reps=5)
+        out["fused" if fused else "plain"] = {"ms": round(ms, 5), "GB/s": round(by / ms / 1e6, 1)}
+    torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def _ctx(dl, name):
+    import synthetic
+    w = synthetic.WORKLOADS[name]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    ctx = dl.Context(w["dims"], t_bc=-1)
+    ctx.load_gauge(U)
+    ctx.set_kappa(w["kappa"])
+    return ctx, U, w
+
+
+def workload_exact():
+    """All 12V point sources on 4^4 (kappa 0.10, eps 0.3, tol 1e-12) vs the dense oracle inverse."""
+    import numpy as np
+    import torch
+    import paper_1012_5168_gb300 as dl
+    from oracle import loops
+    ctx, U, w = _ctx(dl, "exact_4x4x4x4")
+    V = int(np.prod(w["dims"]))
+    out = {"workload": "exact_4x4x4x4", "point_sources": 12 * V}
+    for name, prec in (("f64", dl.PREC_F64), ("f32", dl.PREC_F32)):
+        p = dl.Params(tol=w["tol"], precision=prec, batch=64)
+        ctx.exact_loops(0, 64, p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lo, st = ctx.exact_loops(0, 12 * V, p)
+        dt = time.perf_counter() - t0
+        out[name] = {"seconds": round(dt, 4), "solves_per_s": round(12 * V / dt, 1), "max_true_residual": st["true_residual"]}
+        if name == "f64":
+            got = lo[0]
+    t0 = time.perf_counter()
+    ref = loops.exact_loops_dense(U, w["kappa"], -1.0)
+    out["oracle_dense_seconds"] = round(time.perf_counter() - t0, 3)
+    floor = 1e-6 * np.linalg.norm(ref[0])
+    err = np.linalg.norm(got - ref, axis=-1) / np.maximum(np.linalg.norm(ref, axis=-1), floor)
+    out["max_rel_error_per_gamma"] = float(err.max())
+    print(json.dumps(out), flush=True)
+
+
+def workload_single_rhs():
+    """One Z2 source on 16^3 x 32 to 1e-10: plain FP64 vs FP32- and BF16-inner defect correction."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "wilson_16x16x16x32")
+    eta = ctx.make_sources(1, 0, 4, 0)
+    out = {"workload": "single_rhs_16x16x16x32", "tol": w["tol"]}
+    for name, prec in (("f64", dl.PREC_F64), ("f32", dl.PREC_F32), ("bf16", dl.PREC_BF16)):
+        p = dl.Params(tol=w["tol"], precision=prec, batch=1)
+        ctx.solve(eta[:1], p)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = ctx.solve(eta[1:4], p)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / 3
+        out[name] = {"ms_per_solve": round(dt * 1e3, 2), "solves_per_s": round(1 / dt, 2),
+                     "iters": [s["iters"] for s in st], "outer": [s["outer"] for s in st],
+                     "true_residual": max(s["true_residual"] for s in st)}
+    print(json.dumps(out), flush=True)
+
+
+def workload_tsm():
+    """TSM on 8^3 x 16 (500 LP: BF16, 30 fixed iterations; 50 HP: FP32-inner to 1e-10) vs the exact
+    loops from all 12V point sources; spin x colour dilution, time dilution t0 = n mod T."""
+    import numpy as np
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "tsm_8x8x8x16")
+    V = int(np.prod(w["dims"]))
+    T = w["dims"][3]
+    t0 = time.perf_counter()
+    exact, st = ctx.exact_loops(0, 12 * V, dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=64))
+    t_exact = time.perf_counter() - t0
+    exact = exact[0]  # [16][T]
+    dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_TIME
+    lp = dl.Params(precision=dl.PREC_BF16, fixed_iters=30, batch=64)
+    hp = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=64)
+    t0 = time.perf_counter()
+    mean, var, pn = ctx.tsm_estimate(1, 500, 50, dil, -1, lp, hp, dl.SINK_LOCAL, per_noise=True)
+    t_tsm = time.perf_counter() - t0
+    mean, var = mean[0], var[0]
+    sig = np.sqrt(np.maximum(var.real + var.imag, 1e-300))
+    z = np.abs(mean - exact) / sig  # per Gamma and timeslice
+    names = dl.GAMMA_NAMES
+    # per-Gamma spread of the single-noise estimators (LP ensemble) and bias of LP alone
+    lp_only = pn[:500, 0]
+    cover = np.array([[(i % T) == t for t in range(T)] for i in range(500)])
+    lp_mean = (lp_only * cover[:, None, :]).sum(0) / cover.sum(0)
+    out = {"workload": "tsm_8x8x8x16", "exact_point_solves": 12 * V, "exact_seconds": round(t_exact, 2),
+           "exact_max_true_residual": st["true_residual"], "tsm_seconds": round(t_tsm, 2),
+           "n_lp": 500, "n_hp": 50, "dilution": "spin*colour*time",
+           "z_median": float(np.median(z)), "z_max": float(z.max()),
+           "per_gamma": {names[g]: {"exact_sum_t": [float(exact[g].sum().real), float(exact[g].sum().imag)],
+                                    "tsm_sum_t": [float(mean[g].sum().real), float(mean[g].sum().imag)],
+                                    "stderr_per_t": float(np.median(sig[g])),
+                                    "lp_bias_per_t": float(np.median(np.abs(lp_mean[g] - exact[g])))}
+                         for g in range(16)}}
+    print(json.dumps(out), flush=True)
+
+
+def workload_autograd():
+    """d/dkappa Tr[g5 M^-1] and grad wrt the Z2 sources through LoopTrace, 32 right-hand sides,
+    on 8^3 x 16 and 16^3 x 32; FP64 central finite difference dkappa = 1e-5 as the check."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    from paper_1012_5168_gb300.autograd import loop_trace
+    res = {"workload": "autograd"}
+    for name in ("tsm_8x8x8x16", "wilson_16x16x16x32"):
+        ctx, U, w = _ctx(dl, name)
+        params = dl.Params(tol=1e-12, precision=dl.PREC_F32, batch=32)
+        eta = ctx.make_sources(seed=3, noise_first=0, n_noise=32, dilution=0).requires_grad_(True)
+        k = torch.tensor(w["kappa"], dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L = loop_trace(eta, k, ctx, params)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        loss = L[:, 5].real.sum()
+        t0 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t_bwd = time.perf_counter() - t0
+        dk = 1e-5
+        with torch.no_grad():
+            lp = loop_trace(eta.detach(), torch.tensor(w["kappa"] + dk, dtype=torch.float64), ctx, params)[:, 5].real.sum()
+            lm = loop_trace(eta.detach(), torch.tensor(w["kappa"] - dk, dtype=torch.float64), ctx, params)[:, 5].real.sum()
+        fd = (lp - lm).item() / (2 * dk)
+        # directional derivative along a random source perturbation
+        d = torch.randn_like(eta.detach())
+        h = 1e-6
+        with torch.no_grad():
+            fp = loop_trace(eta.detach() + h * d, k.detach(), ctx, params)[:, 5].real.sum()
+            fm = loop_trace(eta.detach() - h * d, k.detach(), ctx, params)[:, 5].real.sum()
+        fd_eta = (fp - fm).item() / (2 * h)
+        an_eta = torch.sum((eta.grad.conj() * d).real).item()  # PyTorch: grad = 2 df/dconj(eta)
+        res[name] = {"rhs": 32, "dloss_dkappa": k.grad.item(), "central_difference": fd,
+                     "rel_diff_kappa": abs(k.grad.item() - fd) / abs(fd),
+                     "directional_grad_eta": an_eta, "directional_fd_eta": fd_eta,
+                     "rel_diff_eta": abs(an_eta - fd_eta) / abs(fd_eta),
+                     "forward_s": round(t_fwd, 3), "backward_s": round(t_bwd, 3),
+                     "backward_over_forward": round(t_bwd / t_fwd, 2)}
+        ctx.close()
+    print(json.dumps(res), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.hop_profile:
+        return hop_profile(args.hop_profile)
+    if args.workload != "stochastic":
+        return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
+                "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd}[args.workload]()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 

@@ -79,6 +79,12 @@ struct dl_ctx {
     double *d_gauge64 = nullptr;
     float *d_gauge32 = nullptr;
     bf16 *d_gauge16 = nullptr;
+    float *d_gauge_ff = nullptr;   // float-float links (smearing)
+    bool smear_fp64 = false;       // smear in native FP64 instead of float-float
+    float *d_gauge8_32 = nullptr;  // site-major links (staged hop)
+    bf16 *d_gauge8_16 = nullptr;
+    int *h_err = nullptr;          // pinned, mapped: set by the staged hop on a wait timeout
+    int *d_err = nullptr;
     double2 *d_gammas = nullptr;  // [16][4][4]
 
     // batch workspace, width ws_N (power of two)
@@ -111,7 +117,7 @@ struct dl_ctx {
     int64_t kernel_launches = 0;
     int hop_R[3][8];      // right-hand sides per thread, [prec][log2 N]
     int hop_block[3][8];  // threads per block
-    int hop_pf[3][8];     // 1: cp.async prefetching kernel
+    int hop_kind[3][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged
     bool hop_tuned[3][8];
     bool autotune = true;
 };
@@ -171,6 +177,10 @@ static void harvest(dl_ctx *c, std::vector<TimedPair> &v, bool release) {
 static int sync(dl_ctx *c) {
     CK(cudaStreamSynchronize(c->stream));
     harvest(c, c->pending, true);
+    if (c->h_err && *(volatile int *)c->h_err) {
+        *(volatile int *)c->h_err = 0;
+        return fail(DL_ECUDA, "staged Wilson hop: a bounded wait for a bulk copy ran out");
+    }
     return DL_OK;
 }
 
@@ -198,6 +208,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.cb_end = cb1;
     a.c = coef;
     a.g = c->g;
+    a.gauge8 = prec == P_F32 ? (const void *)c->d_gauge8_32 : (prec == P_BF16 ? (const void *)c->d_gauge8_16 : nullptr);
+    a.err = c->d_err;
     int R = prec == P_F64 ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
@@ -205,10 +217,20 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     if (block % G) block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G;
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
-    const int pf = prec == P_F64 ? 0 : c->hop_pf[prec][ilog2(N)];
+    const int kind = prec == P_F64 ? 0 : c->hop_kind[prec][ilog2(N)];
     size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (prec == P_F64 ? 16 : 8) : 0;
-    if (pf) smem = std::max(smem, 2 * pf_stage_bytes(prec, R) * block);
-    Launch l = make_launch(c, total, block, smem, prec == P_F64 ? 4 : (pf ? 4 : 8));
+    int per_sm = prec == P_F64 ? 4 : 8;
+    long items = total;
+    if (kind == 1) {
+        smem = std::max(smem, 2 * pf_stage_bytes(prec, R) * block);
+        per_sm = 4;
+    } else if (kind == 2) {
+        const int sites = block / G;
+        smem = std::max(smem, tma_smem_bytes(prec, N, sites));
+        per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / smem));
+        items = (long)((cb1 - cb0 + sites - 1) / sites) * block;  // one chunk per block at a time
+    }
+    Launch l = make_launch(c, items, block, smem, per_sm);
     if (nblocks) *nblocks = l.grid;
     const bool timed = c->timing;
     TimedPair tp;
@@ -225,8 +247,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     }
     cudaError_t e;
     if (prec == P_F64) e = launch_hop_f64(R, mode, red, a, l);
-    else if (prec == P_F32) e = launch_hop_f32(R, mode, red, pf, a, l);
-    else e = launch_hop_bf16(R, mode, red, pf, a, l);
+    else if (prec == P_F32) e = launch_hop_f32(R, mode, red, kind, a, l);
+    else e = launch_hop_bf16(R, mode, red, kind, a, l);
     if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
     c->kernel_launches++;
     if (timed) {
@@ -366,9 +388,9 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
     float best = 1e30f;
-    int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_pf[prec][l];
+    int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_kind[prec][l];
     const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 2); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 3); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
@@ -377,10 +399,11 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
             for (int bi = 0; bi < 3; ++bi) {
                 const int B = Bs[bi];
                 if (B % (N / R) || (force_block && B != force_block)) continue;
-                if (pf && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
+                if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
+                if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
                 c->hop_R[prec][l] = R;
                 c->hop_block[prec][l] = B;
-                c->hop_pf[prec][l] = pf;
+                c->hop_kind[prec][l] = pf;
                 float ms = 0.f;
                 TRY(time_hops(c, prec, N, 5, &ms));
                 if (ms > 0.f && ms < best) {
@@ -394,7 +417,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     }
     c->hop_R[prec][l] = bR;
     c->hop_block[prec][l] = bB;
-    c->hop_pf[prec][l] = bP;
+    c->hop_kind[prec][l] = bP;
     c->hop_tuned[prec][l] = true;
     invalidate_graphs(c);
     return DL_OK;
@@ -411,7 +434,7 @@ extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int
     const int l = ilog2(N);
     if (R_out) *R_out = c->hop_R[precision][l];
     if (block_out) *block_out = c->hop_block[precision][l];
-    if (pf_out) *pf_out = c->hop_pf[precision][l];
+    if (pf_out) *pf_out = c->hop_kind[precision][l];
     if (ms_out) {
         float ms = 0.f;
         TRY(time_hops(c, precision, N, 10, &ms));
@@ -501,6 +524,10 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     memcpy(c->dims, dims, sizeof(c->dims));
     c->t_bc = t_bc;
     c->device = dev;
+    {
+        const char *e = getenv("DLOOPS_SMEAR_FP64");
+        c->smear_fp64 = e && e[0] == '1';
+    }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     c->stream = (cudaStream_t)cuda_stream;
     c->cur = c->stream;
@@ -523,7 +550,7 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
         for (int l = 0; l < 8; ++l) {
             c->hop_R[p][l] = 2;
             c->hop_block[p][l] = 128;
-            c->hop_pf[p][l] = 0;
+            c->hop_kind[p][l] = 0;
             c->hop_tuned[p][l] = false;
         }
     // coordinates table
@@ -544,11 +571,14 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4; ++j) gh[(n * 4 + i) * 4 + j] = make_double2(gam[n][i][j].real(), gam[n][i][j].imag());
     int rc = DL_OK;
+    if (c->h_err) *c->h_err = 0;
     if (cudaMalloc((void **)&c->d_coords, V * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_gammas, 256 * sizeof(double2)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_acc, 2 * 16 * dims[3] * sizeof(double2)) != cudaSuccess ||
         cudaHostAlloc((void **)&c->h_count, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
-        cudaHostGetDevicePointer((void **)&c->d_count, c->h_count, 0) != cudaSuccess)
+        cudaHostGetDevicePointer((void **)&c->d_count, c->h_count, 0) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&c->d_err, c->h_err, 0) != cudaSuccess)
         rc = fail(DL_ENOMEM, "context allocation failed");
     if (rc == DL_OK &&
         (cudaMemcpy(c->d_coords, coords.data(), V * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -571,11 +601,12 @@ extern "C" int dl_destroy(dl_ctx *c) {
         cudaEventDestroy(tp.a);
         cudaEventDestroy(tp.b);
     }
-    void *ptrs[] = {c->d_coords, c->d_gauge64, c->d_gauge32, c->d_gauge16, c->d_gammas, c->d_partials,
-                    c->d_acc,    c->d_noise,   c->d_w};
+    void *ptrs[] = {c->d_coords,   c->d_gauge64, c->d_gauge32,  c->d_gauge16, c->d_gauge8_32, c->d_gauge8_16,
+                    c->d_gauge_ff, c->d_gammas,  c->d_partials, c->d_acc,     c->d_noise,     c->d_w};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_count) cudaFreeHost(c->h_count);
+    if (c->h_err) cudaFreeHost(c->h_err);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
     return DL_OK;
@@ -605,7 +636,10 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
     if (!c->d_gauge64) {
         if (cudaMalloc((void **)&c->d_gauge64, n64 * sizeof(double)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge32, n64 * sizeof(float)) != cudaSuccess ||
-            cudaMalloc((void **)&c->d_gauge16, n64 * sizeof(bf16)) != cudaSuccess)
+            cudaMalloc((void **)&c->d_gauge16, n64 * sizeof(bf16)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge8_32, 2 * n64 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge8_16, 2 * n64 * sizeof(bf16)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge_ff, 2 * n64 * sizeof(float)) != cudaSuccess)
             return fail(DL_ENOMEM, "gauge allocation failed");
     }
     double *tmp = nullptr;
@@ -619,7 +653,10 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
         gauge_reorder_kernel<double><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge64);
         gauge_reorder_kernel<float><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge32);
         gauge_reorder_kernel<bf16><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge16);
-        c->kernel_launches += 3;
+        gauge8_kernel<float><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8_32);
+        gauge8_kernel<bf16><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8_16);
+        gauge_ff_kernel<<<grid, 256, 0, c->stream>>>(c->d_gauge64, c->d_gauge_ff, (long)n64 / 2);
+        c->kernel_launches += 6;
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
             rc = fail(DL_ECUDA, "gauge reorder failed");
     }
@@ -881,7 +918,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         CK(launch_accumulate(vec_launch(c, prec, N, 0), c->d_outer, lo_ptr(c, LX), xe));
         c->kernel_launches++;
         if (P.fixed_iters > 0) break;
-        // r = bhat - Mhat x  (FP64)
+        // r = bhat - Mhat x, recomputed in FP64 every cycle (true residual)
         TRY(do_hop(c, P_F64, MODE_PLAIN, RED_NONE, c->t64, xe, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh, nullptr,
                    nullptr));
         TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->r64, c->t64, xe, c->bh64, nullptr, 0, N, -k2, 0, Vh, pa, &nb));
@@ -1042,8 +1079,9 @@ extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return 
 
 // Smear the EO fields at *buf (full field, width N) over cb range; returns the
 // buffer holding the result (ping-pong with `spare`).
-static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, const dl_smear &s, int cb0, int cb1) {
+static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const dl_smear &s, int cb0, int cb1) {
     SmearArgs A;
+    A.n = n;
     A.gauge = c->d_gauge64;
     A.coords = c->d_coords;
     A.g = c->g;
@@ -1053,17 +1091,26 @@ static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, const dl_smea
     A.a = 1.0 / (1.0 + 6.0 * s.alpha);
     A.c = s.alpha / (1.0 + 6.0 * s.alpha);
     double *src = *buf, *dst = spare;
-    const size_t half = half_elems(c, N) * 2;
-    // the spare buffer must hold zeros outside the range only where it is read: the
-    // smearing step reads neighbours within the same timeslices, so clearing is not needed.
-    (void)half;
     Launch l = make_launch(c, 2L * (cb1 - cb0) * N, 128, 0, 8);
-    for (int it = 0; it < s.n_iter; ++it) {
-        A.in = src;
-        A.out = dst;
-        smear_kernel<<<l.grid, l.block, 0, c->cur>>>(A);
-        c->kernel_launches++;
-        std::swap(src, dst);
+    if (c->smear_fp64) {
+        for (int it = 0; it < s.n_iter; ++it) {
+            A.in = src;
+            A.out = dst;
+            smear_kernel<<<l.grid, l.block, 0, c->cur>>>(A);
+            c->kernel_launches++;
+            std::swap(src, dst);
+        }
+    } else {
+        Launch lc = make_launch(c, 2L * (cb1 - cb0) * 12 * n, 256, 0, 8);
+        ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 1);
+        for (int it = 0; it < s.n_iter; ++it) {
+            A.in = src;
+            A.out = dst;
+            smear_ff_kernel<<<l.grid, l.block, 0, c->cur>>>(A, c->d_gauge_ff);
+            std::swap(src, dst);
+        }
+        ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 0);
+        c->kernel_launches += s.n_iter + 2;
     }
     CK(cudaGetLastError());
     *buf = src;
@@ -1088,7 +1135,7 @@ extern "C" int dl_apply_smear(dl_ctx *c, const void *in, void *out, int n_rhs, c
         const int n = std::min(N, n_rhs - j0);
         TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, cb0, cb1));
         double *res = c->b64;
-        TRY(smear_eo(c, &res, c->s64a, N, *s, cb0, cb1));
+        TRY(smear_eo(c, &res, c->s64a, N, n, *s, cb0, cb1));
         TRY(eo_to_canon(c, res, (double *)out + j0 * field, n, N, 0, cb0, cb1));
     }
     return DL_OK;
@@ -1213,8 +1260,8 @@ static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, i
         if (!(sink & flag)) continue;
         double *e = eta_buf, *f = phi_buf;
         if (flag == DL_SINK_SMEARED) {
-            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, *sm, cb0, cb1));
-            TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, *sm, cb0, cb1));
+            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, n, *sm, cb0, cb1));
+            TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, n, *sm, cb0, cb1));
         }
         // contract into the slot `slot` region of d_loops viewed as [sink][n][16][T]
         TRY(contract_eo(c, e, f, n, N, t_lo, t_hi, c->d_loops + (size_t)slot * N * per));

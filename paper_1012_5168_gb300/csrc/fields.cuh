@@ -82,6 +82,33 @@ static __global__ void gauge_reorder_kernel(const uint32_t *coords, Geom g, cons
     }
 }
 
+// gauge, site-major with all eight links of a site in one row: for site x of
+// parity p, row d = 2 mu holds U_mu(x) and row d = 2 mu + 1 holds U_mu(x - mu)
+// (not conjugated).  Out: [2][Vh][8][9] complex in S.
+template <typename S>
+__global__ void gauge8_kernel(const uint32_t *coords, Geom g, const double *canon, S *out) {
+    typedef typename Real<S>::type T;
+    const int total = 2 * g.Vh;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const Site st = decode(coords[idx], g);
+        for (int d = 0; d < 8; ++d) {
+            const int mu = d >> 1;
+            int src = st.i;
+            if (d & 1) {
+                src = st.i - g.stride[mu];
+                if (st.c[mu] == 0) src += g.L[mu] * g.stride[mu];
+            }
+            const double2 *u = (const double2 *)(canon + ((size_t)src * 4 + mu) * 18);
+            S *dst = out + ((size_t)idx * 8 + d) * 18;
+            for (int k = 0; k < 9; ++k) {
+                cx<T> z[1];
+                z[0] = mk((T)u[k].x, (T)u[k].y);
+                st_pack<S, 1>(dst + 2 * k, z);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11) and complex Z2 sources
 // ---------------------------------------------------------------------------
@@ -187,6 +214,7 @@ struct SmearArgs {
     const uint32_t *coords;
     Geom g;
     int cb0, cb1, N;
+    int n;  // right-hand sides in use (columns j >= n are left untouched)
     double a, c;
 };
 
@@ -196,6 +224,7 @@ static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         const int j = idx % A.N;
+        if (j >= A.n) continue;
         const int sp = idx / A.N;
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite;
@@ -239,6 +268,163 @@ static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
             const double2 q = __ldg((const double2 *)(y + (size_t)k * A.N * 2));
             *(double2 *)(o + (size_t)k * A.N * 2) =
                 make_double2(A.a * q.x + A.c * acc[k].re, A.a * q.y + A.c * acc[k].im);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian smearing in float-float ("double-float") arithmetic.  A real is the
+// unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48
+// significant bits.  Sums use Knuth's error-free two-sum and products the
+// FMA-based exact product (Dekker), each followed by a renormalisation.  The
+// smearing runs on the FP32 pipes, which on GB300 issue about 60 times as fast
+// as FP64, while its rounding (~1e-14 relative per step) stays far below the
+// tolerance of the loops.  Fields in this format occupy the same 8 bytes per
+// real as FP64 and are converted in place before and after the iterations.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff ff_from(double x) {
+    ff r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+__device__ __forceinline__ double ff_to(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    ff r;
+    r.hi = s + e;
+    r.lo = e - (r.hi - s);
+    return r;
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    ff r;
+    r.hi = p + e;
+    r.lo = e - (r.hi - p);
+    return r;
+}
+__device__ __forceinline__ ff ff_neg(ff a) {
+    a.hi = -a.hi;
+    a.lo = -a.lo;
+    return a;
+}
+struct ffc {
+    ff re, im;
+};
+// acc += a * b  (DAG: acc += conj(a) * b)
+template <bool DAG>
+__device__ __forceinline__ void ffc_mac(ffc &acc, ffc a, ffc b) {
+    const ff ai = DAG ? ff_neg(a.im) : a.im;
+    acc.re = ff_add(acc.re, ff_add(ff_mul(a.re, b.re), ff_neg(ff_mul(ai, b.im))));
+    acc.im = ff_add(acc.im, ff_add(ff_mul(a.re, b.im), ff_mul(ai, b.re)));
+}
+__device__ __forceinline__ ffc ld_ffc(const double *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    ffc z;
+    z.re.hi = v.x;
+    z.re.lo = v.y;
+    z.im.hi = v.z;
+    z.im.lo = v.w;
+    return z;
+}
+
+// In-place conversion of an EO tile field (both parities, cb range, n of N
+// columns) between FP64 and float-float.  to_ff = 1: double -> ff; 0: back.
+static __global__ void ff_convert_kernel(double *f, int Vh, int cb0, int cb1, int N, int n, int to_ff) {
+    const long nsite = cb1 - cb0;
+    const long total = 2 * nsite * 12 * n;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % n);
+        const long q = idx / n;
+        const int c = (int)(q % 12);
+        const long sp = q / 12;
+        const int p = (int)(sp / nsite);
+        const int cb = cb0 + (int)(sp % nsite);
+        double *e = f + (((size_t)p * Vh + cb) * 12 * N + (size_t)c * N + j) * 2;
+        if (to_ff) {
+            const ff a = ff_from(e[0]), b = ff_from(e[1]);
+            *reinterpret_cast<float4 *>(e) = make_float4(a.hi, a.lo, b.hi, b.lo);
+        } else {
+            const float4 v = *reinterpret_cast<const float4 *>(e);
+            ff a, b;
+            a.hi = v.x; a.lo = v.y; b.hi = v.z; b.lo = v.w;
+            e[0] = ff_to(a);
+            e[1] = ff_to(b);
+        }
+    }
+}
+
+// Links in float-float: [2][Vh][4][9] complex as (re.hi, re.lo, im.hi, im.lo).
+static __global__ void gauge_ff_kernel(const double *g64, float *out, long n_complex) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_complex; i += (long)gridDim.x * blockDim.x) {
+        const ff a = ff_from(g64[2 * i]), b = ff_from(g64[2 * i + 1]);
+        reinterpret_cast<float4 *>(out)[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    }
+}
+
+// One smearing step in float-float; same contract as smear_kernel, fields and
+// links in float-float format.
+static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const float *gauge_ff) {
+    const int nsite = A.cb1 - A.cb0;
+    const int total = 2 * nsite * A.N;
+    const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
+    const ff fa = ff_from(A.a), fc = ff_from(A.c);
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int j = idx % A.N;
+        if (j >= A.n) continue;
+        const int sp = idx / A.N;
+        const int p = sp / nsite;
+        const int cb = A.cb0 + sp % nsite;
+        const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
+        const double *inn = A.in + (size_t)(1 - p) * half;
+        ffc acc[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k].re = acc[k].im = ff{0.f, 0.f};
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                const int nb = dir == 0 ? nbr_fwd(st, A.g, mu) : nbr_bwd(st, A.g, mu);
+                const double *up = reinterpret_cast<const double *>(
+                    gauge_ff + (dir == 0 ? (((size_t)p * A.g.Vh + cb) * 4 + mu) * 36
+                                         : (((size_t)(1 - p) * A.g.Vh + nb) * 4 + mu) * 36));
+                ffc u[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) u[k] = ld_ffc(up + 2 * k);
+                const double *src = inn + (size_t)nb * 12 * A.N * 2 + (size_t)j * 2;
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    ffc v[3];
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) v[b] = ld_ffc(src + (size_t)(3 * s + b) * A.N * 2);
+#pragma unroll
+                    for (int aa = 0; aa < 3; ++aa)
+#pragma unroll
+                        for (int b = 0; b < 3; ++b) {
+                            if (dir == 0) ffc_mac<false>(acc[3 * s + aa], u[aa * 3 + b], v[b]);
+                            else ffc_mac<true>(acc[3 * s + aa], u[b * 3 + aa], v[b]);
+                        }
+                }
+            }
+        }
+        const double *y = A.in + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
+        double *o = A.out + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+            const ffc q = ld_ffc(y + (size_t)k * A.N * 2);
+            ffc r;
+            r.re = ff_add(ff_mul(fa, q.re), ff_mul(fc, acc[k].re));
+            r.im = ff_add(ff_mul(fa, q.im), ff_mul(fc, acc[k].im));
+            *reinterpret_cast<float4 *>(o + (size_t)k * A.N * 2) = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
         }
     }
 }

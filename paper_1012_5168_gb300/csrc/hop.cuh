@@ -54,6 +54,8 @@ struct HopArgs {
     int cb_begin, cb_end;   // output sites processed
     double c;               // coefficient of D
     Geom g;
+    const void *gauge8;     // [2][Vh][8][9] complex, site-major links (staged kernel)
+    int *err;               // set to 1 by the staged kernel when a bounded wait runs out
 };
 
 // Load the 12 components of R right-hand sides at one neighbour site and
@@ -142,7 +144,9 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
         const int nb = nbr_fwd(st, A.g, MU);
         const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == A.g.L[3] - 1);
         cx<T> u[9];
-        const S *up = gauge + (((size_t)A.p * A.g.Vh + cb) * 4 + MU) * 18;
+        // site-major rows (all eight links of the output site together) when present
+        const S *up = A.gauge8 ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU) * 18
+                               : gauge + (((size_t)A.p * A.g.Vh + cb) * 4 + MU) * 18;
 #pragma unroll
         for (int k = 0; k < 9; ++k) u[k] = ld_link<S>(up + 2 * k);
         const S *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;
@@ -165,7 +169,9 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
         const int nb = nbr_bwd(st, A.g, MU);
         const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == 0);
         cx<T> u[9];
-        const S *up = gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
+        const S *up = A.gauge8
+                          ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU + 1) * 18
+                          : gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
 #pragma unroll
         for (int k = 0; k < 9; ++k) u[k] = ld_link<S>(up + 2 * k);
         const S *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;

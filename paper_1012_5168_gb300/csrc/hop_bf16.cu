@@ -1,10 +1,22 @@
 // Wilson-hop instantiations for bf16 storage (direct and prefetching variants).
 #include "launch.h"
+#include "hop_tma.cuh"
 
 namespace dl {
 
 template <int R, int MODE, int RED>
 static cudaError_t go(const HopArgs &a, const Launch &l, int pf) {
+    if (pf == 2) {
+        static size_t opted_tma = 0;
+        if (l.smem > 48 * 1024 && l.smem > opted_tma) {
+            cudaError_t e = cudaFuncSetAttribute(hop_kernel_tma<bf16, R, MODE, RED, TMA_STAGES>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)l.smem);
+            if (e != cudaSuccess) return e;
+            opted_tma = l.smem;
+        }
+        hop_kernel_tma<bf16, R, MODE, RED, TMA_STAGES><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        return cudaGetLastError();
+    }
     if (!pf) {
         hop_kernel<bf16, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
@@ -24,12 +36,15 @@ cudaError_t launch_hop_bf16(int R, int mode, int red, int pf, const HopArgs &a, 
 #define DL_CASE(r, m, rd) \
     if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l, pf);
     DL_CASE(1, MODE_PLAIN, RED_NONE)
+    DL_CASE(1, MODE_XPAY, RED_NONE)
     DL_CASE(1, MODE_XPAY, RED_R0DOT)
     DL_CASE(1, MODE_XPAY, RED_BICG)
     DL_CASE(2, MODE_PLAIN, RED_NONE)
+    DL_CASE(2, MODE_XPAY, RED_NONE)
     DL_CASE(2, MODE_XPAY, RED_R0DOT)
     DL_CASE(2, MODE_XPAY, RED_BICG)
     DL_CASE(4, MODE_PLAIN, RED_NONE)
+    DL_CASE(4, MODE_XPAY, RED_NONE)
     DL_CASE(4, MODE_XPAY, RED_R0DOT)
     DL_CASE(4, MODE_XPAY, RED_BICG)
 #undef DL_CASE

@@ -24,10 +24,19 @@ struct Launch {
 // Wilson hop; R = right-hand sides per thread (1, 2 or 4).
 // Returns cudaErrorInvalidValue for a combination that is not instantiated.
 cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, const Launch &l);
-// pf = 1 selects the cp.async prefetching kernel (low precision only); its
-// dynamic shared memory is pf_stage_bytes(prec, R) * 2 * block.
-cudaError_t launch_hop_f32(int R, int mode, int red, int pf, const HopArgs &a, const Launch &l);
-cudaError_t launch_hop_bf16(int R, int mode, int red, int pf, const HopArgs &a, const Launch &l);
+// kind (low precision only): 0 direct loads; 1 cp.async prefetching kernel,
+// dynamic shared memory pf_stage_bytes(prec, R) * 2 * block; 2 bulk-copy
+// staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R)).
+cudaError_t launch_hop_f32(int R, int mode, int red, int kind, const HopArgs &a, const Launch &l);
+cudaError_t launch_hop_bf16(int R, int mode, int red, int kind, const HopArgs &a, const Launch &l);
+
+// TMA_STAGES stages of `sites` neighbour blocks [12][N], two link rows and two
+// neighbour-table rows per site
+constexpr int TMA_STAGES = 4;
+inline size_t tma_smem_bytes(int prec, int N, int sites) {
+    const size_t cb = prec == P_F32 ? 8 : (prec == P_BF16 ? 4 : 16);  // bytes of one complex
+    return 128 + TMA_STAGES * (size_t)sites * 12 * N * cb + 2 * (size_t)sites * 72 * cb + 2 * (size_t)sites * 8 * 4;
+}
 
 inline size_t pf_stage_bytes(int prec, int R) {
     const int sb = prec == P_F32 ? 4 : (prec == P_BF16 ? 2 : 8);  // bytes of one real

@@ -132,3 +132,44 @@ def test_solve_full_size(lib, prec):
         res = residual(U, x[j:j + 1].cpu().numpy(), b, kappa)
         assert res[0] <= 1e-10, res
     c.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("batch", [1, 4, 16, 64])
+def test_hop_kernel_kinds(lib, prec, kind, batch):
+    """Direct, cp.async-prefetching and bulk-copy-staged hops all solve to tolerance."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=8)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    n = min(batch, 5) if batch > 1 else 2
+    b = synthetic.random_spinor(dims, seed=21, n=n)
+    N = 1 << (min(batch, 1 << (n - 1).bit_length()) - 1).bit_length()
+    R, B, k, _ = c.tune_hop(prec, N, force_pf=kind)
+    assert k == kind
+    x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=prec, batch=batch))
+    assert all(s["status"] == 0 for s in st), st
+    res = residual(U, x.cpu().numpy(), b, kappa)
+    assert np.all(res <= 1e-11), res
+    c.close()
+
+
+def test_hop_kernel_kinds_full_size(lib):
+    """The three hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides)."""
+    w = synthetic.WORKLOADS["wilson_16x16x16x32"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    c = lib.Context(w["dims"])
+    c.load_gauge(U)
+    c.set_kappa(w["kappa"])
+    eta = c.make_sources(seed=4, noise_first=0, n_noise=32, dilution=0)
+    sols = []
+    for kind in (0, 1, 2):
+        c.tune_hop(1, 32, force_pf=kind)
+        x, st = c.solve(eta, lib.Params(tol=1e-10, precision=1, batch=32))
+        assert all(s["status"] == 0 and s["true_residual"] <= 1e-10 for s in st)
+        sols.append(x)
+    for x in sols[1:]:
+        assert (torch.linalg.vector_norm(x - sols[0]) / torch.linalg.vector_norm(sols[0])).item() < 1e-9
+    c.close()
