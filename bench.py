@@ -53,9 +53,11 @@ def parse():
                              "autograd"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
-    ap.add_argument("--hop-profile", metavar="PREC:N[:KIND]", default=None,
+    ap.add_argument("--hop-profile", metavar="PREC:N[:KIND[:R:BLOCK]]", default=None,
                     help="time the Wilson hop alone on the 16^3x32 workload (f32|bf16|f64, batch N, kernel kind "
-                         "0 direct / 1 prefetch / 2 staged; default autotuned) and exit")
+                         "0 direct / 1 prefetch / 2 staged, right-hand sides per thread, block size; default "
+                         "autotuned) and exit.  With all five fields the hop launches are, in order: 12 of the "
+                         "forced tuning run, 22 timing the choice, 8 plain (3 warm-up), 8 fused (3 warm-up)")
     return ap.parse_args()
 
 
@@ -216,11 +218,13 @@ def hop_profile(spec: str):
     prec = {"f64": dl.PREC_F64, "f32": dl.PREC_F32, "bf16": dl.PREC_BF16}[parts[0]]
     n = int(parts[1])
     kind = int(parts[2]) if len(parts) > 2 else -1
+    force_r = int(parts[3]) if len(parts) > 3 else 0
+    force_b = int(parts[4]) if len(parts) > 4 else 0
     w = WORKLOAD
     ctx = dl.Context(w["dims"], t_bc=-1)
     ctx.load_gauge(synthetic.gauge_field(w["dims"], w["eps"], w["seed"]))
     ctx.set_kappa(w["kappa"])
-    shape = ctx.tune_hop(prec, n, force_pf=kind)
+    shape = ctx.tune_hop(prec, n, force_R=force_r, force_block=force_b, force_pf=kind)
     out = {"precision": parts[0], "n_rhs": n, "R": shape[0], "block": shape[1], "kind": shape[2]}
     for fused in (0, 1):
         ms, by = ctx.bench_hop(prec, n, fused, reps=5)
