@@ -199,12 +199,11 @@ def run_step(ctx, dl, seed, noise0, params, store_loops):
         nn = min(CHUNK_NOISE, w["n_noise"] - c0)
         eta = ctx.make_sources(seed, noise0 + c0, nn, dil, t0=-1, out=store_loops["eta"][: nn * K])
         phi, st = ctx.solve(eta, params, x=store_loops["phi"][: nn * K])
-        for k in range(nn):
-            n = noise0 + c0 + k
-            t0 = n % T
-            lo = ctx.trace_loops(eta[k * K:(k + 1) * K], phi[k * K:(k + 1) * K], dl.SINK_LOCAL | dl.SINK_SMEARED,
-                                 smear=(w["smear_alpha"], w["smear_iter"]), t_range=(t0, t0 + 1), sum_rhs=True)
-            store_loops["loops"].append(lo)
+        # each diluted source lives on the timeslice of its noise vector (n mod T)
+        t_of = [(noise0 + c0 + j // K) % T for j in range(nn * K)]
+        lo = ctx.trace_loops(eta, phi, dl.SINK_LOCAL | dl.SINK_SMEARED, smear=(w["smear_alpha"], w["smear_iter"]),
+                             t_of_rhs=t_of, group=K)  # [nn][2 sinks][16][T]: one loop per noise vector
+        store_loops["loops"].append(lo)
         n_solved += nn * K
     return n_solved
 
@@ -472,11 +471,21 @@ def main():
     n64 = 3
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     eta3 = ctx.make_sources(6, 0, n64, 0)
+    ctx.get_timing(reset=True)
     g0.record(stream)
     _, st64 = ctx.solve(eta3, dl.Params(tol=w["tol"], precision=dl.PREC_F64, batch=1))
     g1.record(stream)
     torch.cuda.synchronize()
     fp64_rate = n64 / (g0.elapsed_time(g1) / 1e3)
+    # the FP64 hop is bound by FP64 issue: compare its flop rate (1320 per site and RHS)
+    # with the FMA rate measured on this GPU
+    t64 = ctx.get_timing(reset=True)
+    vh = int(np.prod(w["dims"])) // 2
+    ms64 = t64["hop_ms"][2] + t64["hop_ms"][3]
+    n_hop64 = t64["hop_launches"][2] + t64["hop_launches"][3]
+    fma64, _ = dl.bench_fma(dl.PREC_F64)
+    fma32, _ = dl.bench_fma(dl.PREC_F32)
+    hop64_tflops = 1320.0 * vh * n_hop64 / (ms64 / 1e3) / 1e12 if ms64 > 0 else 0.0
 
     # ---- roofline of the dominant hop kernel (low precision, events over the timed region)
     peak, peak_src = read_peaks()
@@ -514,7 +523,12 @@ def main():
                    "parallelism": f"replicas x{world} (disjoint noise ranges)"},
         "loops_per_s": round(value / K, 3),
         "fp64_plain_single_rhs": {"solves_per_s": round(fp64_rate, 3),
-                                  "iters": [s["iters"] for s in st64]},
+                                  "iters": [s["iters"] for s in st64],
+                                  "hop_roofline": {"bound": "alu", "achieved": round(hop64_tflops, 4),
+                                                   "peak": round(fma64, 4), "unit": "TFLOP/s",
+                                                   "frac": round(hop64_tflops / fma64, 4) if fma64 else None,
+                                                   "peak_source": "measured FP64 FMA chains (dl_bench_fma)"}},
+        "fma_peak_tflops": {"f64": round(fma64, 3), "f32": round(fma32, 2)},
         "speedup_vs_fp64_plain": round(value / world / fp64_rate, 2),
         "e2e": {"value": round(e2e_solved * world / (ms_e2e / 1e3), 2), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},

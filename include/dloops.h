@@ -82,7 +82,7 @@ typedef struct dl_solve_params {
                             tolerance test (a deterministic low-precision map, as the
                             truncated solver method needs); 0: iterate to tol */
     double delta;        /* inner relative residual reduction per outer cycle (mixed
-                            precision); <= 0 picks 3e-6 (F32) or 3e-3 (BF16) */
+                            precision); <= 0 picks 3e-6 (F32) or 1e-3 (BF16) */
     int max_outer;       /* cap on defect-correction cycles; <= 0 picks 60 */
     int batch;           /* right-hand sides solved together per launch (1..64, a power
                             of two for F32/BF16 >= 2); <= 0 picks 16 */
@@ -194,12 +194,18 @@ int dl_apply_gamma_weights(dl_ctx *ctx, const void *dev_in, void *dev_out, int n
 /* --- loops (Sec. 3, Eq. 2) ------------------------------------------------ */
 
 /* Loop contraction L_Gamma(t) = sum_{x in t} eta(x)^dag Gamma phi(x) for each
- * pair (eta_j, phi_j), all 16 Gamma, timeslices [t_lo, t_hi) (others 0).
- * sink: DL_SINK_LOCAL and/or DL_SINK_SMEARED (then eta and phi are both
- * smeared by K first; smear must be non-NULL).  host_out: double
- * [n_rhs or 1 if sum_rhs][n_sinks][16][T][2] (local first), FP64 sums. */
-int dl_trace_loops(dl_ctx *ctx, const void *dev_eta, const void *dev_phi, int n_rhs,
-                   int sink, const dl_smear *smear, int t_lo, int t_hi, int sum_rhs,
+ * pair (eta_j, phi_j) and all 16 Gamma (Sec. 3, Eq. 2; FP64 sums).
+ * Timeslices: with t_of_rhs == NULL every pair is contracted on [t_lo, t_hi);
+ * otherwise (host array of n_rhs entries) pair j only on timeslice t_of_rhs[j]
+ * (time-diluted sources; t_lo, t_hi unused).  Other timeslices are zero.
+ * sink: DL_SINK_LOCAL and/or DL_SINK_SMEARED; for the smeared sink eta and phi
+ * are both smeared by K first (Sec. 2), on the same timeslices; smear must be
+ * non-NULL.  group >= 1 must divide n_rhs: the loops of each run of `group`
+ * consecutive pairs are summed (for instance the dilution classes of one noise
+ * vector; group = 1 gives per-pair loops, group = n_rhs the total).
+ * host_out: double [n_rhs/group][n_sinks][16][T][2] (local first). */
+int dl_trace_loops(dl_ctx *ctx, const void *dev_eta, const void *dev_phi, int n_rhs, int sink,
+                   const dl_smear *smear, int t_lo, int t_hi, const int *t_of_rhs, int group,
                    double *host_out);
 
 /* Exact loops (Sec. 1-2: the all-to-all diagonal): solve the point sources
@@ -265,9 +271,10 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
 
 /* Autotuner for the Wilson-hop launch shape at storage precision `precision`
  * and batch width n_rhs.  The candidates are: right-hand sides per thread R in
- * {1, 2, 4}, threads per block in {64, 128, 256}, and for FP32/BF16 the direct
- * or the cp.async-prefetching kernel.  Each candidate runs one plain and one
- * fused hop on random fields; the fastest is kept for this context.
+ * {1, 2, 4}, threads per block in {64, 128, 256}, and for FP32/BF16 the
+ * kernel kind: 0 direct, 1 cp.async-prefetching, 2 bulk-copy staged.  Each
+ * candidate runs one plain and one fused hop on random fields; the fastest is
+ * kept for this context.
  * force_R / force_block > 0 and force_pf >= 0 restrict the candidates.  Solves
  * tune their (precision, batch) on first use.  *R_out, *block_out, *pf_out and
  * *ms_out (may be NULL) receive the choice and its time for one plain plus one
@@ -275,6 +282,16 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
  * between solves. */
 int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_block, int force_pf,
                 int *R_out, int *block_out, int *pf_out, double *ms_out);
+
+/* Fused-multiply-add rate of the current device at `precision` (DL_PREC_F64 or
+ * DL_PREC_F32), in TFLOP/s (2 flops per FMA), from one launch of independent
+ * FMA chains over 8 blocks of 256 threads per SM on `cuda_stream` (NULL: the
+ * default stream).  *ms (may be NULL) receives the kernel time.  It is the
+ * arithmetic ceiling of the FP64 solve, which on this GPU class is bound by
+ * FP64 issue rate rather than by memory.  Allocates and frees a scratch
+ * buffer of 8 bytes per thread.  Errors: DL_EINVAL for another precision or a
+ * NULL tflops, DL_ENOMEM, DL_ECUDA. */
+int dl_bench_fma(int precision, void *cuda_stream, double *tflops, double *ms);
 
 #ifdef __cplusplus
 }

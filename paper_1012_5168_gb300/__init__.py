@@ -40,7 +40,7 @@ SYMBOLS = (
     "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
     "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
-    "dl_trace_loops_noalloc",
+    "dl_trace_loops_noalloc", "dl_bench_fma",
 )
 
 
@@ -100,13 +100,14 @@ def lib() -> ctypes.CDLL:
         "dl_apply_m": (i, [vp, vp, vp, i]),
         "dl_apply_smear": (i, [vp, vp, vp, i, P(Smear), i, i]),
         "dl_apply_gamma_weights": (i, [vp, vp, vp, i, vp, i, i]),
-        "dl_trace_loops": (i, [vp, vp, vp, i, i, P(Smear), i, i, i, vp]),
+        "dl_trace_loops": (i, [vp, vp, vp, i, i, P(Smear), i, i, P(i), i, vp]),
         "dl_exact_loops": (i, [vp, i64, i64, P(SolveParams), i, P(Smear), vp, P(SolveStats)]),
         "dl_tsm_estimate": (i, [vp, u64, i, i, ctypes.c_uint, i, P(SolveParams), P(SolveParams), i, P(Smear),
                                 vp, vp, vp]),
         "dl_bench_hop": (i, [vp, i, i, i, i, P(d), P(d)]),
         "dl_tune_hop": (i, [vp, i, i, i, i, i, P(i), P(i), P(i), P(d)]),
         "dl_trace_loops_noalloc": (i, [vp, vp, i, P(i), i, i, vp, vp]),
+        "dl_bench_fma": (i, [i, vp, P(d), P(d)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -169,6 +170,16 @@ def trace_loops_noalloc(eta, phi, dims, t_range=None, out=None, stream=None):
                                         (ctypes.c_int * 4)(*dims), lo, hi, ctypes.c_void_p(out.data_ptr()),
                                         ctypes.c_void_p(stream)))
     return out
+
+
+def bench_fma(precision: int, stream=None):
+    """Measured FMA rate of the current GPU at PREC_F64 or PREC_F32: (TFLOP/s, kernel ms)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().dl_bench_fma(precision, ctypes.c_void_p(stream), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def _stats(arr) -> list:
@@ -307,18 +318,28 @@ class Context:
                                             n, w.ctypes.data_as(ctypes.c_void_p), mode, int(accumulate)))
         return out
 
-    def trace_loops(self, eta, phi, sink: int = SINK_LOCAL, smear=None, t_range=None, sum_rhs: bool = False):
-        """Loops sum_{x in t} eta^dag Gamma phi: complex array [n or 1][n_sinks][16][T]."""
+    def trace_loops(self, eta, phi, sink: int = SINK_LOCAL, smear=None, t_range=None, sum_rhs: bool = False,
+                    t_of_rhs=None, group: int | None = None):
+        """Loops sum_{x in t} eta^dag Gamma phi: complex array [n/group][n_sinks][16][T].
+
+        t_of_rhs: optional per-pair timeslice (time-diluted sources); group: sum
+        each run of `group` consecutive pairs (default 1, or n with sum_rhs).
+        """
         n = self._field(eta, "eta")
         if self._field(phi, "phi") != n:
             raise ValueError("eta and phi hold different numbers of fields")
         T = self.dims[3]
         lo, hi = t_range if t_range is not None else (0, T)
+        if group is None:
+            group = max(n, 1) if sum_rhs else 1
         n_sinks = (1 if sink & SINK_LOCAL else 0) + (1 if sink & SINK_SMEARED else 0)
-        out = np.zeros(((1 if sum_rhs else n), n_sinks, 16, T), dtype=np.complex128)
+        out = np.zeros((max(n // group, 1) if sum_rhs else n // group, n_sinks, 16, T), dtype=np.complex128)
         sm = Smear(*smear) if smear is not None else None
+        tarr = None
+        if t_of_rhs is not None:
+            tarr = (ctypes.c_int * n)(*[int(t) for t in t_of_rhs])
         _check(lib().dl_trace_loops(self._h, ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()), n,
-                                    sink, ctypes.byref(sm) if sm is not None else None, lo, hi, int(sum_rhs),
+                                    sink, ctypes.byref(sm) if sm is not None else None, lo, hi, tarr, group,
                                     out.ctypes.data_as(ctypes.c_void_p)))
         return out
 

@@ -100,11 +100,13 @@ struct dl_ctx {
     size_t partials_cap = 0;  // double2 elements
     double2 *d_loops = nullptr;  // [N][2 sinks][16][T]
     double2 *d_acc = nullptr;    // [2 sinks][T][16] exact-loop accumulators
+    double2 *d_acc2 = nullptr;   // [64][2 sinks][16][T] grouped loops
     double *d_canon = nullptr;   // N canonical fields (internal sources)
     double2 *d_noise = nullptr;  // per-noise loops (TSM)
     size_t noise_cap = 0;
     double2 *d_w = nullptr;      // gamma weights / spin matrices
     size_t w_cap = 0;
+    int *d_tcol = nullptr;       // per-column timeslice of the current batch (64 ints)
 
     int *h_count = nullptr;  // pinned, mapped
     int *d_count = nullptr;
@@ -134,6 +136,7 @@ static int pow2_at_least(int n) { return 1 << ilog2(n < 1 ? 1 : n); }
 
 static Launch make_launch(dl_ctx *c, long items, int block, size_t smem, int per_sm) {
     Launch l;
+    l.num_sms = 0;
     long need = (items + block - 1) / block;
     long cap = (long)c->num_sms * per_sm;
     l.grid = (int)std::max(1L, std::min(need, cap));
@@ -230,8 +233,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
         per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / smem));
         items = (long)((cb1 - cb0 + sites - 1) / sites) * block;  // one chunk per block at a time
     }
-    Launch l = make_launch(c, items, block, smem, per_sm);
-    if (nblocks) *nblocks = l.grid;
+    Launch l = make_launch(c, items, block, smem, kind == 0 ? 16 : per_sm);
+    if (kind == 0) l.num_sms = c->num_sms;  // the direct kernel runs at full residency (up to 16 blocks/SM)
     const bool timed = c->timing;
     TimedPair tp;
     if (timed) {
@@ -250,6 +253,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     else if (prec == P_F32) e = launch_hop_f32(R, mode, red, kind, a, l);
     else e = launch_hop_bf16(R, mode, red, kind, a, l);
     if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
+    if (nblocks) *nblocks = l.grid;
     c->kernel_launches++;
     if (timed) {
         record(c, tp.b);
@@ -383,7 +387,7 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out) {
 static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, int force_pf) {
     const int l = ilog2(N);
     TRY(ensure_ws(c, N));
-    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     c->cur = c->stream;
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
@@ -575,6 +579,8 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     if (cudaMalloc((void **)&c->d_coords, V * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_gammas, 256 * sizeof(double2)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_acc, 2 * 16 * dims[3] * sizeof(double2)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_tcol, 64 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_acc2, (size_t)64 * 2 * 16 * dims[3] * sizeof(double2)) != cudaSuccess ||
         cudaHostAlloc((void **)&c->h_count, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void **)&c->d_count, c->h_count, 0) != cudaSuccess ||
         cudaHostAlloc((void **)&c->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
@@ -602,7 +608,8 @@ extern "C" int dl_destroy(dl_ctx *c) {
         cudaEventDestroy(tp.b);
     }
     void *ptrs[] = {c->d_coords,   c->d_gauge64, c->d_gauge32,  c->d_gauge16, c->d_gauge8_32, c->d_gauge8_16,
-                    c->d_gauge_ff, c->d_gammas,  c->d_partials, c->d_acc,     c->d_noise,     c->d_w};
+                    c->d_gauge_ff, c->d_gammas,  c->d_partials, c->d_acc,     c->d_noise,     c->d_w,
+                    c->d_tcol,     c->d_acc2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->h_count) cudaFreeHost(c->h_count);
@@ -696,8 +703,10 @@ extern "C" int dl_get_timing(dl_ctx *c, dl_timing *out, int reset) {
 // ---------------------------------------------------------------------------
 // layout conversion
 // ---------------------------------------------------------------------------
-static int canon_to_eo(dl_ctx *c, const double *canon, double *eo, int n, int N, int g5, int cb0, int cb1) {
+static int canon_to_eo(dl_ctx *c, const double *canon, double *eo, int n, int N, int g5, int cb0, int cb1,
+                       const int *tcol = nullptr) {
     ConvArgs a;
+    a.tcol = tcol;
     a.coords = c->d_coords;
     a.g = c->g;
     a.cb0 = cb0;
@@ -712,8 +721,10 @@ static int canon_to_eo(dl_ctx *c, const double *canon, double *eo, int n, int N,
     return DL_OK;
 }
 
-static int eo_to_canon(dl_ctx *c, const double *eo, double *canon, int n, int N, int g5, int cb0, int cb1) {
+static int eo_to_canon(dl_ctx *c, const double *eo, double *canon, int n, int N, int g5, int cb0, int cb1,
+                       const int *tcol = nullptr) {
     ConvArgs a;
+    a.tcol = tcol;
     a.coords = c->d_coords;
     a.g = c->g;
     a.cb0 = cb0;
@@ -823,6 +834,7 @@ static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int 
 }
 
 struct SolveCfg {
+    bool restart;  // restart BiCGStab every defect-correction cycle (default) instead of continuing it
     double tol;
     int prec;
     int max_iter;
@@ -849,7 +861,7 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
     s->prec = p->precision;
     s->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
     s->fixed_iters = p->fixed_iters;
-    s->delta = p->delta > 0 ? p->delta : (p->precision == DL_PREC_BF16 ? 3e-3 : (p->precision == DL_PREC_F32 ? 3e-6 : 1e-3 * p->tol));
+    s->delta = p->delta > 0 ? p->delta : (p->precision == DL_PREC_BF16 ? 1e-3 : (p->precision == DL_PREC_F32 ? 3e-6 : 1e-3 * p->tol));
     if (p->precision == DL_PREC_F64 && !(p->delta > 0)) s->delta = std::max(1e-14, 0.5 * p->tol);
     s->max_outer = p->max_outer > 0 ? p->max_outer : 60;
     int b = p->batch > 0 ? p->batch : 16;
@@ -857,6 +869,12 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
     s->batch = pow2_at_least(b);
     s->use_graph = p->use_graph != 0;
     s->chunk = p->chunk > 0 ? p->chunk : 8;
+    {
+        // Continuing p and rhat across cycles (a reliable update) measured slower than a
+        // restart on the 16^3 x 32 workload for both inner precisions; kept as an option.
+        const char *e = getenv("DLOOPS_CONTINUE_CYCLES");
+        s->restart = !(e && e[0] == '1');
+    }
     return DL_OK;
 }
 
@@ -900,8 +918,9 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         c->kernel_launches++;
         TRY(sync(c));
         if (*(volatile int *)c->h_count == 0) break;
-        VecLaunch v = vec_launch(c, prec, N, prec == P_F64 ? 16 : 8);
-        CK(launch_inner_init(v, c->d_outer, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH), lo_ptr(c, LP), pa));
+        VecLaunch v = vec_launch(c, prec, N, 2 * (prec == P_F64 ? 16 : 8));
+        CK(launch_inner_init(v, c->d_outer, c->d_rhs, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH),
+                             lo_ptr(c, LP), pa, (cycle == 0 || P.restart) ? 1 : 0));
         const int target = P.fixed_iters > 0 ? P.fixed_iters : P.max_iter;
         inner_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
                                                     P.max_iter, P.fixed_iters > 0 ? 1 : 0);
@@ -959,7 +978,7 @@ static int solve_impl(dl_ctx *c, const void *b, void *x, int n_rhs, const dl_sol
     TRY(read_params(params, &P));
     const int N = std::min(P.batch, pow2_at_least(n_rhs));
     TRY(ensure_ws(c, N));
-    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     TRY(maybe_tune(c, P.prec, N));
     TRY(maybe_tune(c, P_F64, N));
     const size_t field = (size_t)c->V * 24;  // doubles per canonical field
@@ -1056,7 +1075,7 @@ static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool 
     if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
     const int N = std::min(64, pow2_at_least(n_rhs));
     TRY(ensure_ws(c, N));
-    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     const size_t field = (size_t)c->V * 24, half = half_elems(c, N) * 2;
     const int Vh = (int)c->Vh;
     const int mode = with_m ? MODE_XPAY : MODE_PLAIN;
@@ -1079,9 +1098,11 @@ extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return 
 
 // Smear the EO fields at *buf (full field, width N) over cb range; returns the
 // buffer holding the result (ping-pong with `spare`).
-static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const dl_smear &s, int cb0, int cb1) {
+static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const dl_smear &s, int cb0, int cb1,
+                    const int *tcol = nullptr) {
     SmearArgs A;
     A.n = n;
+    A.tcol = tcol;
     A.gauge = c->d_gauge64;
     A.coords = c->d_coords;
     A.g = c->g;
@@ -1102,14 +1123,14 @@ static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const 
         }
     } else {
         Launch lc = make_launch(c, 2L * (cb1 - cb0) * 12 * n, 256, 0, 8);
-        ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 1);
+        ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 1, tcol, c->g.V3h);
         for (int it = 0; it < s.n_iter; ++it) {
             A.in = src;
             A.out = dst;
             smear_ff_kernel<<<l.grid, l.block, 0, c->cur>>>(A, c->d_gauge_ff);
             std::swap(src, dst);
         }
-        ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 0);
+        ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 0, tcol, c->g.V3h);
         c->kernel_launches += s.n_iter + 2;
     }
     CK(cudaGetLastError());
@@ -1219,10 +1240,14 @@ __global__ void spin_to_gamma_kernel(const double2 *S, int T, const double2 *gam
 // Contract EO fields eta (c->b64) and phi (c->x64), width N, n right-hand sides,
 // timeslices [t_lo, t_hi) into dst[j][16][T] (other timeslices zero).
 static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, int N, int t_lo, int t_hi,
-                       double2 *dst) {
+                       double2 *dst, const int *tcol = nullptr) {
     const int T = c->dims[3];
+    if (tcol) {  // one timeslice per column
+        t_lo = 0;
+        t_hi = 1;
+    }
     const int nt = t_hi - t_lo;
-    const int R = N > 32 ? 2 : 1;
+    const int R = (N > 32 && !tcol) ? 2 : 1;
     const int G = N / R;
     const int block = R == 2 ? 64 : 128;  // a multiple of G
     int nbx = std::max(1, std::min((int)((c->g.V3h * (long)G + block - 1) / block), std::max(1, 4 * c->num_sms / (2 * nt))));
@@ -1234,13 +1259,15 @@ static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, i
     A.t_lo = t_lo;
     A.N = N;
     A.partials = c->d_partials;
+    A.tcol = tcol;
+    A.n = n;
     dim3 grid(nbx, nt, 2);
     const size_t smem = (size_t)(block / 32) * std::min(G, 32) * R * 16 * sizeof(double2);
     if (R == 1) contract_kernel<1><<<grid, block, smem, c->cur>>>(A);
     else contract_kernel<2><<<grid, block, smem, c->cur>>>(A);
     const int cnt = n * 16 * T;
     zero_kernel<<<std::max(1, (cnt + 255) / 256), 256, 0, c->cur>>>(dst, cnt);
-    contract_final_kernel<<<dim3(nt, n), 32, 0, c->cur>>>(c->d_partials, nbx, N, t_lo, T, c->d_gammas, dst);
+    contract_final_kernel<<<dim3(nt, n), 32, 0, c->cur>>>(c->d_partials, nbx, N, t_lo, T, c->d_gammas, dst, tcol);
     c->kernel_launches += 3;
     CK(cudaGetLastError());
     return DL_OK;
@@ -1249,7 +1276,7 @@ static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, i
 // Loops of the EO pair (eta in *eta_buf, phi in *phi_buf) for the requested
 // sinks into c->d_loops[j][sink][16][T]; smearing overwrites the buffers.
 static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, int sink, const dl_smear *sm, int t_lo,
-                    int t_hi, int n_sinks) {
+                    int t_hi, int n_sinks, const int *tcol = nullptr) {
     const int T = c->dims[3];
     const int cb0 = t_lo * c->g.V3h, cb1 = t_hi * c->g.V3h;
     const int per = 16 * T;
@@ -1260,19 +1287,38 @@ static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, i
         if (!(sink & flag)) continue;
         double *e = eta_buf, *f = phi_buf;
         if (flag == DL_SINK_SMEARED) {
-            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, n, *sm, cb0, cb1));
-            TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, n, *sm, cb0, cb1));
+            const int s0 = tcol ? 0 : cb0, s1 = tcol ? c->g.V3h : cb1;
+            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, n, *sm, s0, s1, tcol));
+            TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, n, *sm, s0, s1, tcol));
         }
         // contract into the slot `slot` region of d_loops viewed as [sink][n][16][T]
-        TRY(contract_eo(c, e, f, n, N, t_lo, t_hi, c->d_loops + (size_t)slot * N * per));
+        TRY(contract_eo(c, e, f, n, N, t_lo, t_hi, c->d_loops + (size_t)slot * N * per, tcol));
         ++slot;
     }
     (void)n_sinks;
     return DL_OK;
 }
 
+// out[g][s][e] = sum over the right-hand sides of group g (consecutive, fixed order)
+__global__ void group_sum_kernel(const double2 *loops /* [sink][N][per] */, int n, int N, int group, int n_sinks,
+                                 int per, double2 *out /* [n/group][sink][per] */) {
+    const int count = (n / group) * n_sinks * per;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count; idx += gridDim.x * blockDim.x) {
+        const int e = idx % per;
+        const int s = (idx / per) % n_sinks;
+        const int g = idx / (per * n_sinks);
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < group; ++k) {
+            const double2 v = loops[((size_t)s * N + g * group + k) * per + e];
+            re += v.x;
+            im += v.y;
+        }
+        out[idx] = make_double2(re, im);
+    }
+}
+
 extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n_rhs, int sink, const dl_smear *sm,
-                              int t_lo, int t_hi, int sum_rhs, double *host_out) {
+                              int t_lo, int t_hi, const int *t_of_rhs, int group, double *host_out) {
     if (!c) return fail(DL_EINVAL, "null context");
     if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
     if (!(sink & (DL_SINK_LOCAL | DL_SINK_SMEARED)) || (sink & ~3)) return fail(DL_EINVAL, "bad sink mask");
@@ -1280,50 +1326,71 @@ extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n
     if ((sink & DL_SINK_SMEARED) && !c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
     if (sm && (sm->n_iter < 0 || !std::isfinite(sm->alpha))) return fail(DL_EINVAL, "bad smearing parameters");
     const int T = c->dims[3];
-    if (t_lo < 0 || t_hi > T || t_lo >= t_hi) return fail(DL_EINVAL, "bad timeslice range");
+    if (!t_of_rhs && (t_lo < 0 || t_hi > T || t_lo >= t_hi)) return fail(DL_EINVAL, "bad timeslice range");
     if (!host_out) return fail(DL_EINVAL, "null output");
+    if (group < 1 || (n_rhs > 0 && n_rhs % group)) return fail(DL_EINVAL, "group must divide n_rhs");
+    if (t_of_rhs)
+        for (int j = 0; j < n_rhs; ++j)
+            if (t_of_rhs[j] < 0 || t_of_rhs[j] >= T) return fail(DL_EINVAL, "t_of_rhs entry outside the lattice");
     const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
     const int per = 16 * T;
-    if (n_rhs == 0) {
-        if (sum_rhs) memset(host_out, 0, sizeof(double) * 2 * n_sinks * per);
-        return DL_OK;
-    }
+    if (n_rhs == 0) return DL_OK;
     if (!eta || !phi) return fail(DL_EINVAL, "null field pointer");
+    // A batch (layout width N) holds whole groups when a group fits in 64 right-hand
+    // sides; a larger group is covered by consecutive batches of a divisor of it.
     const int N = std::min(64, pow2_at_least(n_rhs));
+    int per_batch = (N / group) * group;
+    if (group > 64) {
+        per_batch = 1;
+        for (int d = 64; d >= 1; --d)
+            if (group % d == 0) {
+                per_batch = d;
+                break;
+            }
+    }
     TRY(ensure_ws(c, N));
     const size_t field = (size_t)c->V * 24;
-    const int cb0 = t_lo * c->g.V3h, cb1 = t_hi * c->g.V3h;
-    std::vector<double2> h((size_t)N * 2 * per);
-    std::vector<double> acc(sum_rhs ? (size_t)2 * n_sinks * per : 0, 0.0);
+    const int cb0 = t_of_rhs ? 0 : t_lo * c->g.V3h, cb1 = t_of_rhs ? c->g.V3h : t_hi * c->g.V3h;
+    std::vector<double2> h((size_t)N * n_sinks * per);
     c->cur = c->stream;
-    // the accumulated sum over right-hand sides lives on the device (fixed order)
-    double2 *dsum = c->d_acc;
-    if (sum_rhs) zero_kernel<<<std::max(1, (2 * per + 255) / 256), 256, 0, c->stream>>>(dsum, 2 * per);
-    for (int j0 = 0; j0 < n_rhs; j0 += N) {
-        const int n = std::min(N, n_rhs - j0);
-        TRY(canon_to_eo(c, (const double *)eta + j0 * field, c->b64, n, N, 0, cb0, cb1));
-        TRY(canon_to_eo(c, (const double *)phi + j0 * field, c->x64, n, N, 0, cb0, cb1));
-        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, t_lo, t_hi, n_sinks));
-        if (sum_rhs) {
+    double2 *dsum = c->d_acc;  // running sums of a group spanning batches (group > 64)
+    if (group > 64) zero_kernel<<<std::max(1, (2 * per + 255) / 256), 256, 0, c->stream>>>(dsum, 2 * per);
+    int g_done = 0;
+    for (int j0 = 0; j0 < n_rhs; j0 += per_batch) {
+        const int n = std::min(per_batch, n_rhs - j0);
+        const int *tcol = nullptr;
+        if (t_of_rhs) {
+            CK(cudaMemcpyAsync(c->d_tcol, t_of_rhs + j0, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            tcol = c->d_tcol;
+        }
+        TRY(canon_to_eo(c, (const double *)eta + j0 * field, c->b64, n, N, 0, cb0, cb1, tcol));
+        TRY(canon_to_eo(c, (const double *)phi + j0 * field, c->x64, n, N, 0, cb0, cb1, tcol));
+        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, t_lo, t_hi, n_sinks, tcol));
+        if (group <= 64) {
+            const int ng = n / group;
+            group_sum_kernel<<<std::max(1, (ng * n_sinks * per + 255) / 256), 256, 0, c->stream>>>(
+                c->d_loops, n, N, group, n_sinks, per, c->d_acc2);
+            c->kernel_launches++;
+            CK(cudaMemcpyAsync(h.data(), c->d_acc2, sizeof(double2) * (size_t)ng * n_sinks * per,
+                               cudaMemcpyDeviceToHost, c->stream));
+            TRY(sync(c));
+            memcpy(host_out + (size_t)g_done * n_sinks * per * 2, h.data(), sizeof(double2) * (size_t)ng * n_sinks * per);
+            g_done += ng;
+        } else {
             for (int s = 0; s < n_sinks; ++s) {
                 double2 *part = c->d_loops + (size_t)s * N * per;
-                // fold this batch's right-hand sides in order, then add to the running sum
                 sum_loops_kernel<<<std::max(1, (per + 255) / 256), 256, 0, c->stream>>>(part, n, per, part, per);
                 add_kernel<<<std::max(1, (per + 255) / 256), 256, 0, c->stream>>>(dsum + (size_t)s * per, part, per);
                 c->kernel_launches += 2;
             }
-        } else {
-            CK(cudaMemcpyAsync(h.data(), c->d_loops, sizeof(double2) * (size_t)n_sinks * N * per,
-                               cudaMemcpyDeviceToHost, c->stream));
-            TRY(sync(c));
-            for (int j = 0; j < n; ++j)
-                for (int s = 0; s < n_sinks; ++s)
-                    memcpy(host_out + ((size_t)(j0 + j) * n_sinks + s) * per * 2, &h[(size_t)s * N * per + (size_t)j * per],
-                           sizeof(double2) * per);
+            if ((j0 + n) % group == 0) {  // a group is complete
+                CK(cudaMemcpyAsync(host_out + (size_t)g_done * n_sinks * per * 2, dsum,
+                                   sizeof(double2) * n_sinks * per, cudaMemcpyDeviceToHost, c->stream));
+                TRY(sync(c));
+                zero_kernel<<<std::max(1, (2 * per + 255) / 256), 256, 0, c->stream>>>(dsum, 2 * per);
+                ++g_done;
+            }
         }
-    }
-    if (sum_rhs) {
-        CK(cudaMemcpyAsync(host_out, dsum, sizeof(double2) * n_sinks * per, cudaMemcpyDeviceToHost, c->stream));
     }
     TRY(sync(c));
     return DL_OK;
@@ -1343,7 +1410,7 @@ extern "C" int dl_exact_loops(dl_ctx *c, int64_t src_first, int64_t n_src, const
     const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
     const int N = P.batch;
     TRY(ensure_ws(c, N));
-    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     TRY(maybe_tune(c, P.prec, N));
     TRY(maybe_tune(c, P_F64, N));
     c->cur = c->stream;
@@ -1514,11 +1581,17 @@ static int tsm_pass(dl_ctx *c, uint64_t seed, int64_t first, int count, unsigned
             const int st = status_of(os[j], P.tol, P.fixed_iters > 0);
             if (st != DL_OK && *worst == DL_OK) *worst = st;
         }
-        int tl = 0, th = T;
-        if ((dil & DL_DIL_TIME) && t0 >= 0) { tl = t0; th = t0 + 1; }
-        // eta: re-convert sources over the contracted range (b64 was consumed by the solver)
-        TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, tl * c->g.V3h, th * c->g.V3h));
-        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, tl, th, n_sinks));
+        // eta: re-convert the sources (b64 was consumed by the solver).  Time-diluted
+        // sources are contracted (and smeared) on their own timeslice only.
+        const int *tcol = nullptr;
+        if (dil & DL_DIL_TIME) {
+            int ts[64];
+            for (int j = 0; j < n; ++j) ts[j] = t0 >= 0 ? t0 : (int)((first + (r0 + j) / K) % T);
+            CK(cudaMemcpyAsync(c->d_tcol, ts, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            tcol = c->d_tcol;
+        }
+        TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, 0, tcol ? c->g.V3h : (int)c->Vh, tcol));
+        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, 0, T, n_sinks, tcol));
         fold_noise_kernel<<<std::max(1, (n_sinks * per + 255) / 256), 256, 0, c->stream>>>(c->d_loops, n, N, per,
                                                                                            n_sinks, K, r0, out, 0);
         c->kernel_launches++;
@@ -1546,7 +1619,7 @@ extern "C" int dl_tsm_estimate(dl_ctx *c, uint64_t seed, int n_lp, int n_hp, uns
     const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
     const int N = Plp.batch;
     TRY(ensure_ws(c, N));
-    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     TRY(maybe_tune(c, Plp.prec, N));
     TRY(maybe_tune(c, Php.prec, N));
     TRY(maybe_tune(c, P_F64, N));
@@ -1591,7 +1664,7 @@ extern "C" int dl_bench_hop(dl_ctx *c, int precision, int n_rhs, int fused, int 
         return fail(DL_EINVAL, "bad arguments");
     const int N = pow2_at_least(n_rhs);
     TRY(ensure_ws(c, N));
-    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 8 * N * 16));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     c->cur = c->stream;
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(precision, c->lo[k], ne, 1234u + k, c->stream));

@@ -50,6 +50,7 @@ struct OuterState {
     int status;
     int outer;        // defect-correction cycles done
     int iters;        // inner iterations summed over cycles
+    double sigma;     // |r64| that scaled the current inner phase (0 before the first)
 };
 
 __device__ __forceinline__ bool finite2(double2 z) { return isfinite(z.x) && isfinite(z.y); }
@@ -82,15 +83,18 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2 *partials, in
 // scalar kernels: grid = N blocks of 32 threads (one warp per right-hand side)
 // ---------------------------------------------------------------------------
 
-// Start an inner cycle: rho = r2 = |r_l|^2 (from partials), target and caps.
-// max_iters caps this cycle; max_total caps the iterations summed over cycles.
-static __global__ void inner_start_kernel(RhsState *st, const OuterState *os, const double2 *partials,
+// Start an inner phase: rho = <rhat, r_l>, r2 = |r_l|^2 (from the partials of
+// inner_init_kernel), target and caps; records the scale sigma = |r64| of the
+// phase.  max_iters caps this phase; max_total the iterations over all phases.
+static __global__ void inner_start_kernel(RhsState *st, OuterState *os, const double2 *partials,
                                    int nblocks, int N, double delta, int max_iters, int max_total, int fixed) {
     const int r = blockIdx.x;
-    const double2 n2 = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    const double2 rho = warp_sum_partials(partials, nblocks, N, 2, r, 0);
+    const double2 n2 = warp_sum_partials(partials, nblocks, N, 2, r, 1);
     if (threadIdx.x != 0) return;
+    os[r].sigma = os[r].active ? sqrt(os[r].r2) : 0.0;
     RhsState s;
-    s.rho = make_double2(n2.x, 0.0);
+    s.rho = rho;
     s.alpha = make_double2(1.0, 0.0);
     s.omega = make_double2(1.0, 0.0);
     s.beta = make_double2(0.0, 0.0);
@@ -102,7 +106,8 @@ static __global__ void inner_start_kernel(RhsState *st, const OuterState *os, co
     const int left = max_total - os[r].iters;
     s.max_iters = fixed ? max_iters : (max_iters < left ? max_iters : left);
     s.fixed = fixed;
-    const bool on = os[r].active && n2.x > 0.0 && isfinite(n2.x) && s.max_iters > 0;
+    const bool on = os[r].active && n2.x > 0.0 && isfinite(n2.x) && (rho.x != 0.0 || rho.y != 0.0) &&
+                    s.max_iters > 0;
     s.active = on;
     s.next_active = on;
     st[r] = s;
@@ -269,12 +274,103 @@ static __global__ void __launch_bounds__(256) update_kernel(VecArgs a, const Rhs
     }
 }
 
-// Inner-cycle set-up: r_l = r64 / |r64| rounded to S; rhat = p = r_l; x_l = 0;
-// partials of |r_l|^2 (of the rounded values).  Right-hand sides that are no
-// longer active in the outer loop get zero vectors.
+// Inner-phase set-up from the FP64 residual r64 (one of two modes per
+// right-hand side):
+//  restart:   r_l = r64/|r64| rounded to S; rhat = p = r_l; x_l = 0.
+//  continue:  r_l = r64/|r64|; p *= sigma_prev/|r64| (the search direction of the
+//             previous phase, rescaled to the new unit); rhat kept; x_l = 0.
+//             This is a reliable update (Sleijpen & van der Vorst 1996): the
+//             Krylov recurrence carries on and only the residual is replaced by
+//             the true one.
+// A right-hand side restarts on the first phase, after a breakdown or NaN, or
+// when `restart` is set.  Partials: [0] <rhat, r_l> (rho), [1] |r_l|^2, both
+// of the rounded values.  Right-hand sides no longer active in the outer loop
+// get zero vectors.
 template <typename S, int R>
-static __global__ void __launch_bounds__(256) inner_init_kernel(VecArgs a, const OuterState *os, const double *r64,
-                                                        S *x_, S *r_, S *rhat_, S *p_, double2 *partials) {
+__global__ void __launch_bounds__(256) inner_init_kernel(VecArgs a, const OuterState *os, const RhsState *st,
+                                                        const double *r64, S *x_, S *r_, S *rhat_, S *p_,
+                                                        double2 *partials, int restart) {
+    typedef typename Real<S>::type T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    cx<T> red[R][2];
+#pragma unroll
+    for (int k = 0; k < R; ++k) red[k][0] = red[k][1] = zero<T>();
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<double> src[R];
+        ld_pack<double, R, true>(r64 + off, src);
+        cx<T> lo[R], zr[R], pv[R], rh[R];
+        bool cont[R];
+        bool any_cont = false;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const OuterState &o = os[r0 + k];
+            const bool on = o.active && o.r2 > 0.0;
+            const double sc = on ? 1.0 / sqrt(o.r2) : 0.0;
+            lo[k] = mk((T)(src[k].re * sc), (T)(src[k].im * sc));
+            zr[k] = zero<T>();
+            cont[k] = on && !restart && o.sigma > 0.0 && st[r0 + k].status == ST_OK;
+            any_cont |= cont[k];
+        }
+        st_pack<S, R>(r_ + off, lo);
+        ld_pack<S, R, false>(r_ + off, lo);  // the rounded value, for a consistent rho
+        if (any_cont) {
+            ld_pack<S, R, false>(p_ + off, pv);
+            ld_pack<S, R, false>(rhat_ + off, rh);
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (cont[k]) {
+                const OuterState &o = os[r0 + k];
+                const T f = (T)(o.sigma / sqrt(o.r2));
+                pv[k] = f * pv[k];
+            } else {
+                pv[k] = lo[k];
+                rh[k] = lo[k];
+            }
+        }
+        st_pack<S, R>(p_ + off, pv);
+        st_pack<S, R>(rhat_ + off, rh);
+        ld_pack<S, R, false>(rhat_ + off, rh);
+        st_pack<S, R>(x_ + off, zr);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            cjmac(red[k][0], rh[k], lo[k]);
+            cjmac(red[k][1], lo[k], lo[k]);
+        }
+    }
+    block_reduce<R, 2, T>(red, G, a.N, partials, smem);
+}
+
+// ---------------------------------------------------------------------------
+// CG on the normal equations (CGNR: Hestenes-Stiefel CG applied to
+// Mhat^dag Mhat e = Mhat^dag r_l), the single-precision solver Sec. 2 uses for
+// the low-precision inversions of the truncated solver method.  Mhat is
+// gamma5-hermitian (g5 Mhat g5 = Mhat^dag), so Mhat^dag costs the same two
+// hops as Mhat.  Per right-hand side and iteration:
+//
+//   w = Mhat p                       (two hops; |w|^2 fused in the second)
+//   alpha = |z|^2 / |w|^2
+//   x += alpha p ;  r -= alpha w     (r stored as g5 r; |r|^2 fused)
+//   u = Mhat (g5 r)                  (two hops; |u|^2 fused), z' = g5 u = Mhat^dag r
+//   beta = |z'|^2 / |z|^2 ;  p = g5 u + beta p
+//
+// r is the residual of Mhat e = r_l itself, so the inner stopping test
+// |r| <= delta |r_l| is the one BiCGStab uses.  RhsState.rho.x holds |z|^2.
+// ---------------------------------------------------------------------------
+
+// gamma5 = diag(1, 1, -1, -1) in spin: components 6..11 of a site are negated.
+__device__ __forceinline__ bool g5_negates(int e) { return (e % 12) >= 6; }
+
+// Phase set-up: g5 r_l with r_l = r64/|r64| rounded to S; x_l = 0.
+// Partials [0] = |r_l|^2 of the rounded value.  Right-hand sides no longer
+// active in the outer loop get zero vectors.
+template <typename S, int R>
+__global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, const OuterState *os, const double *r64, S *x_,
+                                                     S *r5_, double2 *partials) {
     typedef typename Real<S>::type T;
     extern __shared__ __align__(16) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
@@ -285,26 +381,183 @@ static __global__ void __launch_bounds__(256) inner_init_kernel(VecArgs a, const
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
         const size_t off = ((size_t)e * a.N + r0) * 2;
+        const double sg = g5_negates(e) ? -1.0 : 1.0;
         cx<double> src[R];
         ld_pack<double, R, true>(r64 + off, src);
         cx<T> lo[R], zr[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
             const OuterState &o = os[r0 + k];
-            const double sc = (o.active && o.r2 > 0.0) ? 1.0 / sqrt(o.r2) : 0.0;
+            const double sc = (o.active && o.r2 > 0.0) ? sg / sqrt(o.r2) : 0.0;
             lo[k] = mk((T)(src[k].re * sc), (T)(src[k].im * sc));
             zr[k] = zero<T>();
         }
-        st_pack<S, R>(r_ + off, lo);
-        // re-read the rounded value for a consistent rho
-        ld_pack<S, R, false>(r_ + off, lo);
-        st_pack<S, R>(rhat_ + off, lo);
-        st_pack<S, R>(p_ + off, lo);
+        st_pack<S, R>(r5_ + off, lo);
+        ld_pack<S, R, false>(r5_ + off, lo);  // the rounded value
         st_pack<S, R>(x_ + off, zr);
 #pragma unroll
         for (int k = 0; k < R; ++k) cjmac(red[k][0], lo[k], lo[k]);
     }
     block_reduce<R, 1, T>(red, G, a.N, partials, smem);
+}
+
+// x += alpha p ;  g5 r -= alpha g5 w  for active right-hand sides; partials [0] = |r|^2.
+template <typename S, int R>
+__global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a, const RhsState *st, S *x_, S *r5_, const S *p_,
+                                                       const S *w_, double2 *partials) {
+    typedef typename Real<S>::type T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    cx<T> red[R][1];
+#pragma unroll
+    for (int k = 0; k < R; ++k) red[k][0] = zero<T>();
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        bool on[R];
+        bool any = false;
+        T al[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const RhsState &q = st[r0 + k];
+            on[k] = q.active != 0;
+            any |= on[k];
+            al[k] = (T)q.alpha.x;
+        }
+        if (!any) continue;
+        const T sg = g5_negates(e) ? (T)-1 : (T)1;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<T> xv[R], rv[R], pv[R], wv[R];
+        ld_pack<S, R, false>(x_ + off, xv);
+        ld_pack<S, R, false>(r5_ + off, rv);
+        ld_pack<S, R, true>(p_ + off, pv);
+        ld_pack<S, R, true>(w_ + off, wv);
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (!on[k]) continue;
+            xv[k] = xv[k] + al[k] * pv[k];
+            rv[k] = rv[k] - (sg * al[k]) * wv[k];
+        }
+        st_pack<S, R>(x_ + off, xv);
+        st_pack<S, R>(r5_ + off, rv);
+        ld_pack<S, R, false>(r5_ + off, rv);  // the rounded value
+#pragma unroll
+        for (int k = 0; k < R; ++k) cjmac(red[k][0], rv[k], rv[k]);
+    }
+    block_reduce<R, 1, T>(red, G, a.N, partials, smem);
+}
+
+// p = g5 u + beta p for active right-hand sides, or p = g5 u everywhere (init).
+template <typename S, int R>
+__global__ void __launch_bounds__(256) cg_p_kernel(VecArgs a, const RhsState *st, const S *u_, S *p_, int init) {
+    typedef typename Real<S>::type T;
+    const int G = a.N / R, lgG = __ffs(G) - 1;
+    const int total = a.n_elem << lgG;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+        bool on[R];
+        bool any = false;
+        T be[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            const RhsState &q = st[r0 + k];
+            on[k] = init || q.active != 0;
+            any |= on[k];
+            be[k] = init ? (T)0 : (T)q.beta.x;
+        }
+        if (!any) continue;
+        const T sg = g5_negates(e) ? (T)-1 : (T)1;
+        const size_t off = ((size_t)e * a.N + r0) * 2;
+        cx<T> uv[R], pv[R];
+        ld_pack<S, R, true>(u_ + off, uv);
+        if (init) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) pv[k] = sg * uv[k];
+        } else {
+            ld_pack<S, R, false>(p_ + off, pv);
+#pragma unroll
+            for (int k = 0; k < R; ++k)
+                if (on[k]) pv[k] = sg * uv[k] + be[k] * pv[k];
+        }
+        st_pack<S, R>(p_ + off, pv);
+    }
+}
+
+// CG phase start: |r_l|^2 from cg_init_kernel's partials (pr), |z|^2 = |u|^2
+// from the second hop of u = Mhat g5 r_l (pu); target, caps and sigma as in
+// inner_start_kernel.
+static __global__ void cg_start_kernel(RhsState *st, OuterState *os, const double2 *pr, int nr, const double2 *pu,
+                                       int nu, int N, double delta, int max_iters, int max_total, int fixed) {
+    const int r = blockIdx.x;
+    const double2 n2 = warp_sum_partials(pr, nr, N, 1, r, 0);
+    const double2 zz = warp_sum_partials(pu, nu, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    os[r].sigma = os[r].active ? sqrt(os[r].r2) : 0.0;
+    RhsState s;
+    s.rho = make_double2(zz.x, 0.0);
+    s.alpha = make_double2(0.0, 0.0);
+    s.omega = make_double2(0.0, 0.0);
+    s.beta = make_double2(0.0, 0.0);
+    s.r2 = n2.x;
+    s.r2_0 = n2.x;
+    s.target2 = delta * delta * n2.x;
+    s.iters = 0;
+    s.status = ST_OK;
+    const int left = max_total - os[r].iters;
+    s.max_iters = fixed ? max_iters : (max_iters < left ? max_iters : left);
+    s.fixed = fixed;
+    const bool on = os[r].active && n2.x > 0.0 && isfinite(n2.x) && zz.x > 0.0 && isfinite(zz.x) &&
+                    s.max_iters > 0;
+    s.active = on;
+    s.next_active = on;
+    st[r] = s;
+}
+
+// After w = Mhat p: alpha = |z|^2 / |w|^2.
+static __global__ void cg_alpha_kernel(RhsState *st, const double2 *partials, int nblocks, int N) {
+    const int r = blockIdx.x;
+    const double2 ww = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    RhsState &s = st[r];
+    s.active = s.next_active;
+    if (!s.active) return;
+    const double a = s.rho.x / ww.x;
+    if (!(ww.x > 0.0) || !isfinite(a)) {
+        s.status = isfinite(ww.x) ? ST_BREAKDOWN : ST_NAN;
+        s.active = 0;
+        s.next_active = 0;
+        return;
+    }
+    s.alpha = make_double2(a, 0.0);
+}
+
+// After the update (pr: |r|^2) and u = Mhat g5 r (pu: |u|^2): beta, stopping test.
+static __global__ void cg_beta_kernel(RhsState *st, const double2 *pr, int nr, const double2 *pu, int nu, int N) {
+    const int r = blockIdx.x;
+    const double2 n2 = warp_sum_partials(pr, nr, N, 1, r, 0);
+    const double2 zz = warp_sum_partials(pu, nu, N, 1, r, 0);
+    if (threadIdx.x != 0) return;
+    RhsState &s = st[r];
+    if (!s.active) return;
+    s.iters += 1;
+    if (!isfinite(n2.x) || !isfinite(zz.x)) {
+        s.status = ST_NAN;
+        s.active = 0;  // the p update is skipped
+        s.next_active = 0;
+        return;
+    }
+    s.r2 = n2.x;
+    bool stop = false;
+    if (!(zz.x > 0.0)) {
+        s.beta = make_double2(0.0, 0.0);
+        if (n2.x > s.target2) s.status = ST_BREAKDOWN;
+        stop = true;
+    } else {
+        s.beta = make_double2(zz.x / s.rho.x, 0.0);
+        s.rho = make_double2(zz.x, 0.0);
+    }
+    const bool done = s.fixed ? (s.iters >= s.max_iters) : (s.r2 <= s.target2 || s.iters >= s.max_iters);
+    s.next_active = !(stop || done);
 }
 
 // x64 += |r64| * x_l for right-hand sides active in the outer loop.
@@ -350,6 +603,7 @@ static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, c
         o.tol2 = tol * tol;
         o.outer = 0;
         o.iters = 0;
+        o.sigma = 0.0;
         o.status = ST_OK;
         o.active = (n2.x > 0.0) ? 1 : 0;
         if (!isfinite(n2.x)) { o.status = ST_NAN; o.active = 0; }

@@ -18,7 +18,11 @@ struct ConvArgs {
     int n;       // right-hand sides converted (j < n)
     int N;       // layout width
     int gamma5;  // negate spins 2, 3
+    const int *tcol;  // if set: column j covers timeslice tcol[j] only (cb range [cb0, cb1) inside it)
 };
+__device__ __forceinline__ int col_offset(const int *tcol, int j, int n, const Geom &g) {
+    return (tcol && j < n) ? tcol[j] * g.V3h : 0;
+}
 
 static __global__ void canon_to_eo_kernel(ConvArgs a, const double *canon, double *eo) {
     const int nsite = a.cb1 - a.cb0;
@@ -27,7 +31,7 @@ static __global__ void canon_to_eo_kernel(ConvArgs a, const double *canon, doubl
         const int j = (int)(idx % a.N);
         const long sp = idx / a.N;
         const int p = (int)(sp / nsite);
-        const int cb = a.cb0 + (int)(sp % nsite);
+        const int cb = a.cb0 + (int)(sp % nsite) + col_offset(a.tcol, j, a.n, a.g);
         const Site st = decode(a.coords[(size_t)p * a.g.Vh + cb], a.g);
         double *dst = eo + ((size_t)p * a.g.Vh + cb) * 12 * a.N * 2 + (size_t)j * 2;
         if (j >= a.n) {
@@ -51,7 +55,7 @@ static __global__ void eo_to_canon_kernel(ConvArgs a, const double *eo, double *
         const int j = (int)(idx % a.n);
         const long sp = idx / a.n;
         const int p = (int)(sp / nsite);
-        const int cb = a.cb0 + (int)(sp % nsite);
+        const int cb = a.cb0 + (int)(sp % nsite) + col_offset(a.tcol, j, a.n, a.g);
         const Site st = decode(a.coords[(size_t)p * a.g.Vh + cb], a.g);
         const double *src = eo + ((size_t)p * a.g.Vh + cb) * 12 * a.N * 2 + (size_t)j * 2;
         double2 *dst = (double2 *)(canon + ((size_t)j * 2 * a.g.Vh + st.i) * 24);
@@ -216,6 +220,7 @@ struct SmearArgs {
     int cb0, cb1, N;
     int n;  // right-hand sides in use (columns j >= n are left untouched)
     double a, c;
+    const int *tcol;  // if set: column j is smeared on timeslice tcol[j] only
 };
 
 static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
@@ -227,7 +232,7 @@ static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
         if (j >= A.n) continue;
         const int sp = idx / A.N;
         const int p = sp / nsite;
-        const int cb = A.cb0 + sp % nsite;
+        const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
         const double *inn = A.in + (size_t)(1 - p) * half;
         cx<double> acc[12];
@@ -339,7 +344,8 @@ __device__ __forceinline__ ffc ld_ffc(const double *p) {
 
 // In-place conversion of an EO tile field (both parities, cb range, n of N
 // columns) between FP64 and float-float.  to_ff = 1: double -> ff; 0: back.
-static __global__ void ff_convert_kernel(double *f, int Vh, int cb0, int cb1, int N, int n, int to_ff) {
+static __global__ void ff_convert_kernel(double *f, int Vh, int cb0, int cb1, int N, int n, int to_ff,
+                                         const int *tcol, int V3h) {
     const long nsite = cb1 - cb0;
     const long total = 2 * nsite * 12 * n;
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
@@ -348,7 +354,7 @@ static __global__ void ff_convert_kernel(double *f, int Vh, int cb0, int cb1, in
         const int c = (int)(q % 12);
         const long sp = q / 12;
         const int p = (int)(sp / nsite);
-        const int cb = cb0 + (int)(sp % nsite);
+        const int cb = cb0 + (int)(sp % nsite) + (tcol ? tcol[j] * V3h : 0);
         double *e = f + (((size_t)p * Vh + cb) * 12 * N + (size_t)c * N + j) * 2;
         if (to_ff) {
             const ff a = ff_from(e[0]), b = ff_from(e[1]);
@@ -383,7 +389,7 @@ static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const
         if (j >= A.n) continue;
         const int sp = idx / A.N;
         const int p = sp / nsite;
-        const int cb = A.cb0 + sp % nsite;
+        const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
         const double *inn = A.in + (size_t)(1 - p) * half;
         ffc acc[12];
@@ -441,6 +447,8 @@ struct ContractArgs {
     int t_lo;
     int N;
     double2 *partials;
+    const int *tcol;  // if set (R = 1, one timeslice slot): column j is contracted on tcol[j]
+    int n;
 };
 
 template <int R>
@@ -459,8 +467,8 @@ static __global__ void __launch_bounds__(128) contract_kernel(ContractArgs A) {
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc[r][k] = zero<double>();
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int cb = cb0 + (idx >> lgG);
         const int r0 = (idx & (G - 1)) * R;
+        const int cb = cb0 + (idx >> lgG) + (A.tcol ? col_offset(A.tcol, r0, A.n, A.g) - t * A.g.V3h : 0);
         const size_t base = (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)r0 * 2;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
@@ -490,7 +498,7 @@ static __global__ void __launch_bounds__(128) contract_kernel(ContractArgs A) {
 // sum_{alpha beta} Gamma_{alpha beta} S_{beta alpha}.  out[j][16][T] double2.
 // grid = (n_t, n), block = 32.
 static __global__ void contract_final_kernel(const double2 *partials, int nbx, int N, int t_lo, int T,
-                                      const double2 *gammas /* [16][4][4] */, double2 *out) {
+                                      const double2 *gammas /* [16][4][4] */, double2 *out, const int *tcol) {
     const int tt = blockIdx.x;
     const int j = blockIdx.y;
     __shared__ double2 S[16];
@@ -515,7 +523,7 @@ static __global__ void contract_final_kernel(const double2 *partials, int nbx, i
                 re += gm.x * s.x - gm.y * s.y;
                 im += gm.x * s.y + gm.y * s.x;
             }
-        out[((size_t)j * 16 + lane) * T + (t_lo + tt)] = make_double2(re, im);
+        out[((size_t)j * 16 + lane) * T + (tcol ? tcol[j] : t_lo + tt)] = make_double2(re, im);
     }
 }
 

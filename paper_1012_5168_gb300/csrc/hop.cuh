@@ -136,6 +136,7 @@ template <typename S, int R, int MU>
 __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb, int r0,
                                         cx<typename Real<S>::type> (&acc)[R][12]) {
     typedef typename Real<S>::type T;
+    constexpr bool G8 = sizeof(S) < sizeof(double);  // FP32 / BF16 read the site-major link rows
     const S *in = reinterpret_cast<const S *>(A.in);
     const S *gauge = reinterpret_cast<const S *>(A.gauge);
     const size_t N = (size_t)A.N;
@@ -144,9 +145,9 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
         const int nb = nbr_fwd(st, A.g, MU);
         const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == A.g.L[3] - 1);
         cx<T> u[9];
-        // site-major rows (all eight links of the output site together) when present
-        const S *up = A.gauge8 ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU) * 18
-                               : gauge + (((size_t)A.p * A.g.Vh + cb) * 4 + MU) * 18;
+        // low precision: site-major rows (all eight links of the output site together)
+        const S *up = G8 ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU) * 18
+                         : gauge + (((size_t)A.p * A.g.Vh + cb) * 4 + MU) * 18;
 #pragma unroll
         for (int k = 0; k < 9; ++k) u[k] = ld_link<S>(up + 2 * k);
         const S *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;
@@ -169,9 +170,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
         const int nb = nbr_bwd(st, A.g, MU);
         const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == 0);
         cx<T> u[9];
-        const S *up = A.gauge8
-                          ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU + 1) * 18
-                          : gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
+        const S *up = G8 ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU + 1) * 18
+                         : gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
 #pragma unroll
         for (int k = 0; k < 9; ++k) u[k] = ld_link<S>(up + 2 * k);
         const S *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;

@@ -5,7 +5,7 @@
 namespace dl {
 
 template <int R, int MODE, int RED>
-static cudaError_t go(const HopArgs &a, const Launch &l, int pf) {
+static cudaError_t go(const HopArgs &a, Launch &l, int pf) {
     if (pf == 2) {
         static size_t opted_tma = 0;
         if (l.smem > 48 * 1024 && l.smem > opted_tma) {
@@ -18,6 +18,7 @@ static cudaError_t go(const HopArgs &a, const Launch &l, int pf) {
         return cudaGetLastError();
     }
     if (!pf) {
+        clamp_grid(l, resident_blocks(hop_kernel<bf16, R, MODE, RED>, l.block, l.smem));
         hop_kernel<bf16, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
     }
@@ -32,7 +33,7 @@ static cudaError_t go(const HopArgs &a, const Launch &l, int pf) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_hop_bf16(int R, int mode, int red, int pf, const HopArgs &a, const Launch &l) {
+cudaError_t launch_hop_bf16(int R, int mode, int red, int pf, const HopArgs &a, Launch &l) {
 #define DL_CASE(r, m, rd) \
     if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l, pf);
     DL_CASE(1, MODE_PLAIN, RED_NONE)

@@ -4,12 +4,13 @@
 namespace dl {
 
 template <int R, int MODE, int RED>
-static cudaError_t go(const HopArgs &a, const Launch &l) {
+static cudaError_t go(const HopArgs &a, Launch &l) {
+    clamp_grid(l, resident_blocks(hop_kernel<double, R, MODE, RED>, l.block, l.smem));
     hop_kernel<double, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, const Launch &l) {
+cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, Launch &l) {
 #define DL_CASE(r, m, rd) \
     if (R == r && mode == m && red == rd) return go<r, m, rd>(a, l);
     DL_CASE(1, MODE_PLAIN, RED_NONE)

@@ -19,16 +19,41 @@ struct Launch {
     int block;
     size_t smem;
     cudaStream_t stream;
+    int num_sms;  // > 0: the launcher clamps grid to num_sms x resident blocks of the kernel
 };
 
-// Wilson hop; R = right-hand sides per thread (1, 2 or 4).
+// Resident blocks per SM of `kernel` at this block size and dynamic shared
+// memory (cached per kernel, block and shared-memory size).
+template <typename K>
+inline int resident_blocks(K kernel, int block, size_t smem) {
+    static int cached[4][1024];
+    static size_t cached_smem[4][1024];
+    const int bi = block == 64 ? 0 : (block == 128 ? 1 : (block == 256 ? 2 : 3));
+    const int si = (int)((smem / 256) % 1024);
+    if (cached[bi][si] > 0 && cached_smem[bi][si] == smem) return cached[bi][si];
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess || n < 1) n = 1;
+    cached[bi][si] = n;
+    cached_smem[bi][si] = smem;
+    return n;
+}
+// Resident blocks, at most 16 per SM (the partial-sum buffers are sized for that).
+inline void clamp_grid(Launch &l, int resident) {
+    if (l.num_sms > 0) {
+        const int cap = l.num_sms * (resident < 16 ? resident : 16);
+        if (l.grid > cap) l.grid = cap;
+    }
+}
+
+// Wilson hop; R = right-hand sides per thread (1, 2 or 4).  l.grid may be
+// lowered to the kernel's residency (l.num_sms > 0); the launch used is left in l.
 // Returns cudaErrorInvalidValue for a combination that is not instantiated.
-cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, const Launch &l);
+cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, Launch &l);
 // kind (low precision only): 0 direct loads; 1 cp.async prefetching kernel,
 // dynamic shared memory pf_stage_bytes(prec, R) * 2 * block; 2 bulk-copy
 // staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R)).
-cudaError_t launch_hop_f32(int R, int mode, int red, int kind, const HopArgs &a, const Launch &l);
-cudaError_t launch_hop_bf16(int R, int mode, int red, int kind, const HopArgs &a, const Launch &l);
+cudaError_t launch_hop_f32(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
+cudaError_t launch_hop_bf16(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 
 // TMA_STAGES stages of `sites` neighbour blocks [12][N], two link rows and two
 // neighbour-table rows per site
@@ -53,8 +78,8 @@ struct VecLaunch {
 cudaError_t launch_axpy_s(const VecLaunch &v, const RhsState *st, const void *r, const void *vv, void *s);
 cudaError_t launch_update(const VecLaunch &v, const RhsState *st, void *x, void *r, void *p, const void *s,
                           const void *t, const void *vv);
-cudaError_t launch_inner_init(const VecLaunch &v, const OuterState *os, const double *r64, void *x, void *r,
-                              void *rhat, void *p, double2 *partials);
+cudaError_t launch_inner_init(const VecLaunch &v, const OuterState *os, const RhsState *st, const double *r64,
+                              void *x, void *r, void *rhat, void *p, double2 *partials, int restart);
 cudaError_t launch_accumulate(const VecLaunch &v, const OuterState *os, const void *x, double *x64);
 cudaError_t launch_norm2(const VecLaunch &v, const void *x, double2 *partials);
 cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s);

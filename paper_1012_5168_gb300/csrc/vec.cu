@@ -35,11 +35,11 @@ cudaError_t launch_update(const VecLaunch &v, const RhsState *st, void *x, void 
     return cudaGetLastError();
 }
 
-cudaError_t launch_inner_init(const VecLaunch &v, const OuterState *os, const double *r64, void *x, void *r,
-                              void *rhat, void *p, double2 *partials) {
-#define CALL(S, RR)                                                                                   \
-    inner_init_kernel<S, RR><<<v.l.grid, v.l.block, v.l.smem, v.l.stream>>>(v.a, os, r64, (S *)x, (S *)r, \
-                                                                            (S *)rhat, (S *)p, partials)
+cudaError_t launch_inner_init(const VecLaunch &v, const OuterState *os, const RhsState *st, const double *r64,
+                              void *x, void *r, void *rhat, void *p, double2 *partials, int restart) {
+#define CALL(S, RR)                                                                                       \
+    inner_init_kernel<S, RR><<<v.l.grid, v.l.block, v.l.smem, v.l.stream>>>(v.a, os, st, r64, (S *)x, (S *)r, \
+                                                                            (S *)rhat, (S *)p, partials, restart)
     DL_DISPATCH(v.prec, v.R, CALL);
 #undef CALL
     return cudaGetLastError();

@@ -120,3 +120,56 @@ def test_tsm_deterministic_and_combination(lib):
     ref = loops.stochastic_loops(eta, phi).reshape(3, 4, 16, T).sum(1)
     assert loop_error(pn[6:9].reshape(-1, T), ref.reshape(-1, T)) < 1e-8
     c.close()
+
+
+def test_trace_loops_per_rhs_timeslice_and_groups(lib):
+    """Time-diluted sources contracted on their own timeslice, summed per noise vector."""
+    dims, kappa = (4, 4, 2, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=9)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    dil = noise.SPIN | noise.COLOUR | noise.TIME
+    eta = c.make_sources(seed=5, noise_first=3, n_noise=6, dilution=dil, t0=-1)  # 72 sources, t0 = n mod 8
+    phi = torch.from_numpy(synthetic.random_spinor(dims, seed=4, n=72)).cuda()
+    t_of = [(3 + j // 12) % 8 for j in range(72)]
+    got = c.trace_loops(eta, phi, lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(3.0, 7), t_of_rhs=t_of, group=12)
+    assert got.shape == (6, 2, 16, 8)
+    e, f = eta.cpu().numpy(), phi.cpu().numpy()
+    ref_l = loops.stochastic_loops(e, f)
+    ref_s = loops.smeared_loops(U, e, f, 3.0, 7)
+    for g in range(6):
+        t0 = (3 + g) % 8
+        want_l = np.zeros((16, 8), complex)
+        want_s = np.zeros((16, 8), complex)
+        want_l[:, t0] = ref_l[12 * g:12 * g + 12, :, t0].sum(0)
+        want_s[:, t0] = ref_s[12 * g:12 * g + 12, :, t0].sum(0)
+        assert np.abs(got[g, 0] - want_l).max() < 1e-12 * np.abs(ref_l).max()
+        assert np.abs(got[g, 1] - want_s).max() < 1e-12 * np.abs(ref_s).max()
+    # groups of 36 (a batch holds one group) and of 72 (spans batches) agree with the sums
+    g36 = c.trace_loops(eta, phi, lib.SINK_LOCAL, t_of_rhs=t_of, group=36)
+    assert np.allclose(g36[:, 0], got[:, 0].reshape(2, 3, 16, 8).sum(1), rtol=1e-13, atol=1e-13)
+    one = c.trace_loops(eta, phi, lib.SINK_LOCAL, t_of_rhs=t_of, group=72)
+    assert np.allclose(one[0, 0], got[:, 0].sum(0), rtol=1e-13, atol=1e-13)
+    c.close()
+
+
+def test_tsm_time_diluted_smeared(lib):
+    """TSM with time dilution by translation and a smeared sink: HP loops equal the oracle's."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=10)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    lp = lib.Params(precision=2, fixed_iters=5, batch=8)
+    hp = lib.Params(tol=1e-11, precision=1, batch=8)
+    dil = noise.SPIN | noise.TIME
+    mean, var, pn = c.tsm_estimate(2, 4, 2, dil, -1, lp, hp, lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(2.0, 4),
+                                   per_noise=True)
+    eta = noise.make_sources(dims, 2, 4, 2, dil, t0=-1)
+    phi = np.stack([wilson.solve(U, e, kappa, -1.0, tol=1e-13)[0] for e in eta])
+    ref_s = loops.smeared_loops(U, eta, phi, 2.0, 4).reshape(2, 4, 16, 4).sum(1)
+    ref_l = loops.stochastic_loops(eta, phi).reshape(2, 4, 16, 4).sum(1)
+    assert loop_error(pn[4:6, 0].reshape(-1, 4), ref_l.reshape(-1, 4)) < 1e-8
+    assert loop_error(pn[4:6, 1].reshape(-1, 4), ref_s.reshape(-1, 4)) < 1e-8
+    c.close()

@@ -131,3 +131,13 @@ def test_bad_inputs_rejected(lib):
         c.solve(x)
     assert e.value.status == lib.ESTATE
     c.close()
+
+
+def test_fma_rate_measured(lib):
+    """The FMA microbenchmark returns a positive rate, FP32 above FP64, and rejects other precisions."""
+    f64, ms64 = lib.bench_fma(lib.PREC_F64)
+    f32, ms32 = lib.bench_fma(lib.PREC_F32)
+    assert f64 > 0 and ms64 > 0 and f32 > f64
+    with pytest.raises(lib.DlError) as e:
+        lib.bench_fma(lib.PREC_BF16)
+    assert e.value.status == lib.EINVAL
