@@ -79,7 +79,7 @@ def read_peaks():
 def read_traffic(kind: str):
     """Per-launch DRAM bytes of the hop kernel from the committed ncu summary, if current."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "hop_traffic.md")
+    path = os.path.join(ROOT, "profiles", "hop_f32_fused_n32_16x16x16x32.md")
     src = os.path.join(ROOT, "paper_1012_5168_gb300", "csrc", "hop.cuh")
     if not os.path.exists(path):
         return None
