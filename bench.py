@@ -225,9 +225,9 @@ def hop_profile(spec: str):
     ctx.set_kappa(w["kappa"])
     shape = ctx.tune_hop(prec, n, force_R=force_r, force_block=force_b, force_pf=kind)
     out = {"precision": parts[0], "n_rhs": n, "R": shape[0], "block": shape[1], "kind": shape[2]}
-    for fused in (0, 1):
+    for fused, name in ((0, "plain"), (1, "fused"), (2, "fused_bicg")):
         ms, by = ctx.bench_hop(prec, n, fused, reps=5)
-        out["fused" if fused else "plain"] = {"ms": round(ms, 5), "GB/s": round(by / ms / 1e6, 1)}
+        out[name] = {"ms": round(ms, 5), "GB/s": round(by / ms / 1e6, 1)}
     torch.cuda.synchronize()
     print(json.dumps(out), flush=True)
     ctx.close()
@@ -293,8 +293,10 @@ def workload_single_rhs():
 
 
 def workload_tsm():
-    """TSM on 8^3 x 16 (500 LP: BF16, 30 fixed iterations; 50 HP: FP32-inner to 1e-10) vs the exact
-    loops from all 12V point sources; spin x colour dilution, time dilution t0 = n mod T."""
+    """TSM on 8^3 x 16 (500 LP + 50 HP noise vectors, HP: FP32-inner to 1e-10) vs the exact loops
+    from all 12V point sources; spin x colour dilution, time dilution t0 = n mod T.  Two
+    low-precision maps: single-precision CG on the normal equations to 1e-6 (Sec. 2's choice)
+    and 30 fixed BF16 BiCGStab iterations."""
     import numpy as np
     import torch
     import paper_1012_5168_gb300 as dl
@@ -306,28 +308,33 @@ def workload_tsm():
     t_exact = time.perf_counter() - t0
     exact = exact[0]  # [16][T]
     dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_TIME
-    lp = dl.Params(precision=dl.PREC_BF16, fixed_iters=30, batch=64)
     hp = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=64)
-    t0 = time.perf_counter()
-    mean, var, pn = ctx.tsm_estimate(1, 500, 50, dil, -1, lp, hp, dl.SINK_LOCAL, per_noise=True)
-    t_tsm = time.perf_counter() - t0
-    mean, var = mean[0], var[0]
-    sig = np.sqrt(np.maximum(var.real + var.imag, 1e-300))
-    z = np.abs(mean - exact) / sig  # per Gamma and timeslice
     names = dl.GAMMA_NAMES
-    # per-Gamma spread of the single-noise estimators (LP ensemble) and bias of LP alone
-    lp_only = pn[:500, 0]
-    cover = np.array([[(i % T) == t for t in range(T)] for i in range(500)])
-    lp_mean = (lp_only * cover[:, None, :]).sum(0) / cover.sum(0)
     out = {"workload": "tsm_8x8x8x16", "exact_point_solves": 12 * V, "exact_seconds": round(t_exact, 2),
-           "exact_max_true_residual": st["true_residual"], "tsm_seconds": round(t_tsm, 2),
-           "n_lp": 500, "n_hp": 50, "dilution": "spin*colour*time",
-           "z_median": float(np.median(z)), "z_max": float(z.max()),
-           "per_gamma": {names[g]: {"exact_sum_t": [float(exact[g].sum().real), float(exact[g].sum().imag)],
-                                    "tsm_sum_t": [float(mean[g].sum().real), float(mean[g].sum().imag)],
-                                    "stderr_per_t": float(np.median(sig[g])),
-                                    "lp_bias_per_t": float(np.median(np.abs(lp_mean[g] - exact[g])))}
-                         for g in range(16)}}
+           "exact_max_true_residual": st["true_residual"], "n_lp": 500, "n_hp": 50,
+           "dilution": "spin*colour*time", "lp_maps": {}}
+    lps = {"f32_cgnr_tol1e-6": dl.Params(tol=1e-6, delta=1e-6, precision=dl.PREC_F32, batch=64,
+                                         method=dl.METHOD_CGNR),
+           "bf16_bicgstab_30_iterations": dl.Params(precision=dl.PREC_BF16, fixed_iters=30, batch=64)}
+    cover = np.array([[(i % T) == t for t in range(T)] for i in range(500)])
+    for label, lp in lps.items():
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mean, var, pn = ctx.tsm_estimate(1, 500, 50, dil, -1, lp, hp, dl.SINK_LOCAL, per_noise=True)
+        torch.cuda.synchronize()
+        t_tsm = time.perf_counter() - t0
+        mean, var = mean[0], var[0]
+        sig = np.sqrt(np.maximum(var.real + var.imag, 1e-300))
+        z = np.abs(mean - exact) / sig  # per Gamma and timeslice
+        lp_only = pn[:500, 0]
+        lp_mean = (lp_only * cover[:, None, :]).sum(0) / cover.sum(0)
+        out["lp_maps"][label] = {
+            "tsm_seconds": round(t_tsm, 2), "z_median": float(np.median(z)), "z_max": float(z.max()),
+            "per_gamma": {names[g]: {"exact_sum_t": [float(exact[g].sum().real), float(exact[g].sum().imag)],
+                                     "tsm_sum_t": [float(mean[g].sum().real), float(mean[g].sum().imag)],
+                                     "stderr_per_t": float(np.median(sig[g])),
+                                     "lp_bias_per_t": float(np.median(np.abs(lp_mean[g] - exact[g])))}
+                          for g in range(16)}}
     print(json.dumps(out), flush=True)
 
 

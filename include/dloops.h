@@ -63,6 +63,13 @@ typedef enum dl_status {
  * mixed-precision CG/BiCGStab. */
 enum { DL_PREC_F64 = 0, DL_PREC_F32 = 1, DL_PREC_BF16 = 2 };
 
+/* Krylov method of the inner solve.  BICGSTAB works on the even-site Schur
+ * system Mhat x = bhat directly.  CGNR is conjugate gradient on the normal
+ * equations Mhat^dag Mhat x = Mhat^dag bhat.  Sec. 2 names it: single-precision
+ * CG to a 1e-6 tolerance for the low-precision solves of the truncated solver
+ * method.  Both stop on the residual of Mhat x = bhat itself. */
+enum { DL_METHOD_BICGSTAB = 0, DL_METHOD_CGNR = 1 };
+
 /* Dilution bitmask (Sec. 2): spin (x4 inversions), colour (x3), even-odd
  * spatial partition (x2), cubic partition (x8: the vertex class
  * (x&1) + 2(y&1) + 4(z&1) of the elementary 3-cube), time (source on a single
@@ -77,23 +84,26 @@ typedef struct dl_ctx dl_ctx;
 typedef struct dl_solve_params {
     double tol;          /* stop when ||b - M x|| / ||b|| <= tol (FP64 true residual); > 0 */
     int precision;       /* DL_PREC_* */
-    int max_iter;        /* cap on inner BiCGStab iterations summed over outer cycles */
+    int max_iter;        /* cap on inner Krylov iterations summed over outer cycles */
     int fixed_iters;     /* > 0: run exactly this many inner iterations, one cycle, no
                             tolerance test (a deterministic low-precision map, as the
                             truncated solver method needs); 0: iterate to tol */
     double delta;        /* inner relative residual reduction per outer cycle (mixed
-                            precision); <= 0 picks 3e-6 (F32) or 1e-3 (BF16) */
+                            precision); <= 0 picks 3e-6 (F32) or 1e-3 (BF16).  A cycle
+                            stops earlier once its residual meets the outer tolerance
+                            with a margin of 4 */
     int max_outer;       /* cap on defect-correction cycles; <= 0 picks 60 */
     int batch;           /* right-hand sides solved together per launch (1..64, a power
                             of two for F32/BF16 >= 2); <= 0 picks 16 */
     int use_graph;       /* capture the inner iteration in CUDA graphs (1) or launch
                             directly (0) */
     int chunk;           /* inner iterations per graph launch / convergence poll; <= 0: 8 */
+    int method;          /* DL_METHOD_*; 0 (BiCGStab) by default */
 } dl_solve_params;
 
 typedef struct dl_solve_stats {
     int status;          /* dl_status of this right-hand side */
-    int iters;           /* inner BiCGStab iterations */
+    int iters;           /* inner Krylov iterations */
     int outer;           /* defect-correction cycles */
     double true_residual;/* ||b - M x|| / ||b||, full lattice, FP64 */
 } dl_solve_stats;
@@ -175,7 +185,11 @@ int dl_solve_adjoint(dl_ctx *ctx, const void *dev_b, void *dev_x, int n_rhs,
 
 /* --- operators (building blocks, FP64) ------------------------------------ */
 
-/* out = D in (Wilson hopping term, full lattice, FP64), n_rhs fields. */
+/* out = D in (Wilson hopping term, full lattice, FP64), n_rhs fields.  With
+ * the environment variable DLOOPS_HOP_ARITH=dff these two operators compute in
+ * float-float arithmetic (about 48 significant bits) on the same FP64 fields.
+ * Mixed-precision solves use that arithmetic for their defect-correction
+ * steps; the variable exposes it for testing. */
 int dl_apply_hop(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
 /* out = M in = in - kappa D in. */
 int dl_apply_m(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
@@ -262,10 +276,12 @@ int dl_trace_loops_noalloc(const void *dev_eta, const void *dev_phi, int n_rhs, 
 
 /* --- low-level kernels exposed for measurement ---------------------------- */
 
-/* Apply the even-odd hop D_{p,1-p} (p = out_parity) to an internal batch of
- * n_rhs random fields in storage precision `precision`, `reps` times, and
- * return the mean kernel time in *ms (CUDA events) and its algorithmic bytes
- * per launch in *bytes.  Used to time the Wilson hop alone. */
+/* Apply the even-odd hop to an internal batch of n_rhs random fields in
+ * storage precision `precision`, `reps` times, and return the mean kernel time
+ * in *ms (CUDA events) and its algorithmic bytes per launch in *bytes.  fused:
+ * 0 the plain hop; 1 the BiCGStab hop v = y - kappa^2 D x with <rhat, v>; 2 the
+ * hop t = y - kappa^2 D x with its five reductions.  Used to time the Wilson
+ * hop alone. */
 int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
                  double *ms, double *bytes);
 

@@ -19,14 +19,22 @@ spin projection, no batching tricks), in complex128:
 * ``loops``    - the loop contraction Tr[Gamma S_F(x,x)] per timeslice (Sec. 3,
                  Eq. 2), exact loops from the all-to-all diagonal, the stochastic
                  estimator, the truncated-solver-method combination (Sec. 2),
-                 and the adjoint-based loop gradients.
+                 and the adjoint-based loop gradients;
+* ``correlators`` - momentum-projected loops, the disconnected correlator and
+                 the connected meson correlator of a point source (Sec. 3,
+                 Eqs. 1 and 3);
+* ``krylov``   - the even-site Schur system written with parity projectors on
+                 full-lattice fields, and the fixed-iteration Krylov maps
+                 (CGNR, BiCGStab) that define the truncated solver method's
+                 low-precision solves.
 
 Pinning: every function is checked by ``tests/test_oracle_*.py`` against
 facts that do not come from the oracle itself (closed forms, a dense LAPACK
-inverse, the hopping expansion, gauge invariance, gamma5-hermiticity, numpy's
-Philox implementation).  The one piece without such a pin is noted in
-``loops.tsm_estimate`` (the low-precision solver map is parity unpinned beyond
-an error bound; the combination itself is pinned).
+inverse, numpy's least-squares solver, the hopping expansion, gauge
+invariance, gamma5-hermiticity, numpy's Philox implementation).  The one piece
+without such a pin is noted in ``loops.tsm_estimate``: the BF16 low-precision
+solver map is parity unpinned beyond an error bound.  Its FP64 counterpart
+(``krylov``) and the combination itself are pinned.
 """
 
-from . import lattice, wilson, philox, noise, smear, loops  # noqa: F401
+from . import lattice, wilson, philox, noise, smear, loops, krylov, correlators  # noqa: F401

@@ -28,6 +28,7 @@ LIB_PATH = os.path.join(_HERE, "libdloops.so")
 # enums of dloops.h
 OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, BREAKDOWN, NAN, ESTATE = range(8)
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
+METHOD_BICGSTAB, METHOD_CGNR = 0, 1
 DIL_SPIN, DIL_COLOUR, DIL_EVENODD, DIL_CUBIC, DIL_TIME = 1, 2, 4, 8, 16
 SINK_LOCAL, SINK_SMEARED = 1, 2
 
@@ -47,7 +48,8 @@ SYMBOLS = (
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("fixed_iters", ctypes.c_int), ("delta", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("batch", ctypes.c_int), ("use_graph", ctypes.c_int), ("chunk", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("use_graph", ctypes.c_int), ("chunk", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -136,10 +138,11 @@ class Params:
     batch: int = 16
     use_graph: int = 1
     chunk: int = 0
+    method: int = 0  # METHOD_BICGSTAB or METHOD_CGNR
 
     def c(self) -> SolveParams:
         return SolveParams(self.tol, self.precision, self.max_iter, self.fixed_iters, self.delta,
-                           self.max_outer, self.batch, self.use_graph, self.chunk)
+                           self.max_outer, self.batch, self.use_graph, self.chunk, self.method)
 
 
 def n_classes(dilution: int) -> int:
@@ -371,7 +374,8 @@ class Context:
                                      pn.ctypes.data_as(ctypes.c_void_p) if pn is not None else None))
         return (mean, var, pn) if per_noise else (mean, var)
 
-    def bench_hop(self, precision: int, n_rhs: int, fused: bool = False, reps: int = 20):
+    def bench_hop(self, precision: int, n_rhs: int, fused: int = 0, reps: int = 20):
+        """Time one hop kind alone (fused: 0 plain, 1 XPAY + <rhat, v>, 2 XPAY + five reductions)."""
         ms, by = ctypes.c_double(), ctypes.c_double()
         _check(lib().dl_bench_hop(self._h, precision, n_rhs, int(fused), reps, ctypes.byref(ms), ctypes.byref(by)))
         return ms.value, by.value

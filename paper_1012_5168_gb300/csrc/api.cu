@@ -148,7 +148,7 @@ static Launch make_launch(dl_ctx *c, long items, int block, size_t smem, int per
 
 static size_t half_elems(dl_ctx *c, int N) { return (size_t)c->Vh * 12 * N; }  // complex per half field
 
-static int storage_bytes(int prec) { return prec == P_F64 ? 8 : (prec == P_F32 ? 4 : 2); }
+static int storage_bytes(int prec) { return (prec == P_F64 || prec == P_DFF) ? 8 : (prec == P_F32 ? 4 : 2); }
 
 static cudaEvent_t get_event(dl_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -201,8 +201,11 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.y = y;
     a.z = z;
     a.rhat = rhat;
-    a.gauge = prec == P_F64 ? (const void *)c->d_gauge64
-                            : (prec == P_F32 ? (const void *)c->d_gauge32 : (const void *)c->d_gauge16);
+    const bool wide = prec == P_F64 || prec == P_DFF;  // FP64 fields, one right-hand side per thread
+    a.gauge = prec == P_F64   ? (const void *)c->d_gauge64
+              : prec == P_DFF ? (const void *)c->d_gauge_ff
+              : prec == P_F32 ? (const void *)c->d_gauge32
+                              : (const void *)c->d_gauge16;
     a.coords = c->d_coords;
     a.partials = partials;
     a.p = p;
@@ -213,16 +216,16 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.g = c->g;
     a.gauge8 = prec == P_F32 ? (const void *)c->d_gauge8_32 : (prec == P_BF16 ? (const void *)c->d_gauge8_16 : nullptr);
     a.err = c->d_err;
-    int R = prec == P_F64 ? 1 : c->hop_R[prec][ilog2(N)];
+    int R = wide ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
-    int block = c->hop_block[prec][ilog2(N)];
+    int block = prec == P_DFF ? 64 : c->hop_block[prec][ilog2(N)];
     if (block % G) block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G;
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
-    const int kind = prec == P_F64 ? 0 : c->hop_kind[prec][ilog2(N)];
-    size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (prec == P_F64 ? 16 : 8) : 0;
-    int per_sm = prec == P_F64 ? 4 : 8;
+    const int kind = wide ? 0 : c->hop_kind[prec][ilog2(N)];
+    size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (wide ? 16 : 8) : 0;
+    int per_sm = wide ? 4 : 8;
     long items = total;
     if (kind == 1) {
         smem = std::max(smem, 2 * pf_stage_bytes(prec, R) * block);
@@ -240,7 +243,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     if (timed) {
         tp.a = get_event(c);
         tp.b = get_event(c);
-        tp.kind = (prec == P_F64 ? 2 : 0) + (mode != MODE_PLAIN || red != RED_NONE ? 1 : 0);
+        tp.kind = (wide ? 2 : 0) + (mode != MODE_PLAIN || red != RED_NONE ? 1 : 0);
         const double S = 24.0 * storage_bytes(prec), L = 18.0 * storage_bytes(prec);
         int streams = 2 + (mode != MODE_PLAIN ? 1 : 0) + (mode == MODE_RESID ? 1 : 0) +
                       ((red == RED_R0DOT || red == RED_BICG) ? 1 : 0);
@@ -250,6 +253,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     }
     cudaError_t e;
     if (prec == P_F64) e = launch_hop_f64(R, mode, red, a, l);
+    else if (prec == P_DFF) e = launch_hop_dff(R, mode, red, a, l);
     else if (prec == P_F32) e = launch_hop_f32(R, mode, red, kind, a, l);
     else e = launch_hop_bf16(R, mode, red, kind, a, l);
     if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
@@ -769,11 +773,37 @@ static int enqueue_iteration(dl_ctx *c, int prec, int N) {
     return DL_OK;
 }
 
+// One CGNR iteration (blas.cuh): w = Mhat p; x, g5 r updated; u = Mhat g5 r; p = g5 u + beta p.
+// Fields: LX x, LR g5 r, LP p, LV w, LRH u, LTMP the odd intermediate.
+static int enqueue_iteration_cg(dl_ctx *c, int prec, int N) {
+    const double k2 = c->kappa * c->kappa;
+    const int Vh = (int)c->Vh;
+    double2 *pa = c->d_partials, *pb = c->d_partials + c->partials_cap / 2;
+    int nb = 0;
+    TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
+               Vh, nullptr, nullptr));
+    TRY(do_hop(c, prec, MODE_XPAY, RED_NORM, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, 0, N,
+               -k2, 0, Vh, pa, &nb));
+    cg_alpha_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, pa, nb, N);
+    VecLaunch v = vec_launch(c, prec, N, prec == P_F64 ? 16 : 8);
+    CK(launch_cg_update(v, c->d_rhs, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LP), lo_ptr(c, LV), pb));
+    const int nbv = v.l.grid;
+    TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LR), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
+               Vh, nullptr, nullptr));
+    TRY(do_hop(c, prec, MODE_XPAY, RED_NORM, lo_ptr(c, LRH), lo_ptr(c, LTMP), lo_ptr(c, LR), nullptr, nullptr, 0, N,
+               -k2, 0, Vh, pa, &nb));
+    cg_beta_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, pb, nbv, pa, nb, N);
+    CK(launch_cg_p(vec_launch(c, prec, N, 0), c->d_rhs, lo_ptr(c, LRH), lo_ptr(c, LP), 0));
+    c->kernel_launches += 4;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
 // Run `iters` inner iterations (graph or eager); returns the number of right-hand
 // sides still active in *active.
-static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int *active) {
+static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int *active, int method) {
     if (use_graph) {
-        auto key = std::make_tuple(prec, N, iters, c->timing ? 1 : 0);
+        auto key = std::make_tuple(prec + 4 * method, N, iters, c->timing ? 1 : 0);
         auto it = c->graphs.find(key);
         if (it == c->graphs.end()) {
             GraphEntry ge;
@@ -785,7 +815,8 @@ static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int 
             cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
             int rc = DL_OK;
             if (e == cudaSuccess) {
-                for (int k = 0; k < iters && rc == DL_OK; ++k) rc = enqueue_iteration(c, prec, N);
+                for (int k = 0; k < iters && rc == DL_OK; ++k)
+                    rc = method == DL_METHOD_CGNR ? enqueue_iteration_cg(c, prec, N) : enqueue_iteration(c, prec, N);
                 if (rc == DL_OK) {
                     count_active_kernel<<<1, 1, 0, c->cap_stream>>>(c->d_rhs, N, c->d_count);
                     c->kernel_launches++;
@@ -823,7 +854,8 @@ static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int 
         harvest(c, it->second.timed, false);
     } else {
         c->cur = c->stream;
-        for (int k = 0; k < iters; ++k) TRY(enqueue_iteration(c, prec, N));
+        for (int k = 0; k < iters; ++k)
+            TRY(method == DL_METHOD_CGNR ? enqueue_iteration_cg(c, prec, N) : enqueue_iteration(c, prec, N));
         count_active_kernel<<<1, 1, 0, c->stream>>>(c->d_rhs, N, c->d_count);
         c->kernel_launches++;
         CK(cudaGetLastError());
@@ -834,6 +866,8 @@ static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int 
 }
 
 struct SolveCfg {
+    int method;    // DL_METHOD_BICGSTAB or DL_METHOD_CGNR
+    bool outer_dff;   // defect-correction hops in float-float instead of FP64
     bool restart;  // restart BiCGStab every defect-correction cycle (default) instead of continuing it
     double tol;
     int prec;
@@ -857,6 +891,8 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
     if (!(p->tol > 0.0) || !std::isfinite(p->tol)) return fail(DL_EINVAL, "tol must be positive");
     if (p->precision < 0 || p->precision > 2) return fail(DL_EINVAL, "unknown precision");
     if (p->max_iter < 0 || p->fixed_iters < 0) return fail(DL_EINVAL, "negative iteration count");
+    if (p->method != DL_METHOD_BICGSTAB && p->method != DL_METHOD_CGNR) return fail(DL_EINVAL, "unknown method");
+    s->method = p->method;
     s->tol = p->tol;
     s->prec = p->precision;
     s->max_iter = p->max_iter > 0 ? p->max_iter : 20000;
@@ -874,6 +910,10 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
         // restart on the 16^3 x 32 workload for both inner precisions; kept as an option.
         const char *e = getenv("DLOOPS_CONTINUE_CYCLES");
         s->restart = !(e && e[0] == '1');
+        // Float-float defect-correction hops measured slower than FP64 ones on GB300
+        // (4.4 vs 3.4 ms per hop at 32 right-hand sides); kept as an option.
+        const char *f = getenv("DLOOPS_OUTER_DFF");
+        s->outer_dff = f && f[0] == '1';
     }
     return DL_OK;
 }
@@ -889,6 +929,9 @@ static int ready(dl_ctx *c) {
 // solution is left in c->x64.  host_os receives the N outer states.
 static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<OuterState> &host_os) {
     const double k = c->kappa, k2 = k * k;
+    // Defect-correction hops (bhat, residuals, reconstruction) in FP64, or in
+    // float-float on the same FP64 fields when selected (mixed precision only).
+    const int op = (P.prec != P_F64 && P.outer_dff) ? P_DFF : P_F64;
     const int Vh = (int)c->Vh;
     const size_t half = half_elems(c, N) * 2;  // doubles
     double *be = c->b64, *bo = c->b64 + half, *xe = c->x64, *xo = c->x64 + half;
@@ -907,7 +950,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         c->kernel_launches += 3;
     }
     // bhat = b_e + kappa D_eo b_o, |bhat|^2
-    TRY(do_hop(c, P_F64, MODE_XPAY, RED_NORM, c->bh64, bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
+    TRY(do_hop(c, op, MODE_XPAY, RED_NORM, c->bh64, bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
     outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 0, P.tol, P.max_outer, P.max_iter);
     c->kernel_launches++;
     CK(cudaMemcpyAsync(c->r64, c->bh64, half * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -918,38 +961,57 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         c->kernel_launches++;
         TRY(sync(c));
         if (*(volatile int *)c->h_count == 0) break;
-        VecLaunch v = vec_launch(c, prec, N, 2 * (prec == P_F64 ? 16 : 8));
-        CK(launch_inner_init(v, c->d_outer, c->d_rhs, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH),
-                             lo_ptr(c, LP), pa, (cycle == 0 || P.restart) ? 1 : 0));
         const int target = P.fixed_iters > 0 ? P.fixed_iters : P.max_iter;
-        inner_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
-                                                    P.max_iter, P.fixed_iters > 0 ? 1 : 0);
-        c->kernel_launches += 2;
+        if (P.method == DL_METHOD_CGNR) {
+            // g5 r_l and x_l = 0; u = Mhat g5 r_l (|u|^2 = |Mhat^dag r_l|^2); p = g5 u
+            VecLaunch v = vec_launch(c, prec, N, prec == P_F64 ? 16 : 8);
+            CK(launch_cg_init(v, c->d_outer, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), pb));
+            TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LR), nullptr, nullptr, nullptr, 1, N,
+                       1.0, 0, Vh, nullptr, nullptr));
+            TRY(do_hop(c, prec, MODE_XPAY, RED_NORM, lo_ptr(c, LRH), lo_ptr(c, LTMP), lo_ptr(c, LR), nullptr, nullptr,
+                       0, N, -k2, 0, Vh, pa, &nb));
+            cg_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pb, v.l.grid, pa, nb, N, P.delta, target,
+                                                     P.max_iter, P.fixed_iters > 0 ? 1 : 0);
+            CK(launch_cg_p(vec_launch(c, prec, N, 0), c->d_rhs, lo_ptr(c, LRH), lo_ptr(c, LP), 1));
+            c->kernel_launches += 3;
+        } else {
+            VecLaunch v = vec_launch(c, prec, N, 2 * (prec == P_F64 ? 16 : 8));
+            CK(launch_inner_init(v, c->d_outer, c->d_rhs, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH),
+                                 lo_ptr(c, LP), pa, (cycle == 0 || P.restart) ? 1 : 0));
+            inner_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
+                                                        P.max_iter, P.fixed_iters > 0 ? 1 : 0);
+            c->kernel_launches += 2;
+        }
         int done = 0;
         while (done < target) {
             const int kk = std::min(P.chunk, target - done);
             int active = 0;
-            TRY(run_chunk(c, prec, N, kk, P.use_graph, &active));
+            TRY(run_chunk(c, prec, N, kk, P.use_graph, &active, P.method));
             done += kk;
             if (active == 0) break;
         }
         c->cur = c->stream;
         CK(launch_accumulate(vec_launch(c, prec, N, 0), c->d_outer, lo_ptr(c, LX), xe));
         c->kernel_launches++;
-        if (P.fixed_iters > 0) break;
+        if (P.fixed_iters > 0) {
+            outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, 0, N, 2, P.tol, P.max_outer,
+                                                         P.max_iter);
+            c->kernel_launches++;
+            break;
+        }
         // r = bhat - Mhat x, recomputed in FP64 every cycle (true residual)
-        TRY(do_hop(c, P_F64, MODE_PLAIN, RED_NONE, c->t64, xe, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh, nullptr,
+        TRY(do_hop(c, op, MODE_PLAIN, RED_NONE, c->t64, xe, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh, nullptr,
                    nullptr));
-        TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->r64, c->t64, xe, c->bh64, nullptr, 0, N, -k2, 0, Vh, pa, &nb));
+        TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, c->t64, xe, c->bh64, nullptr, 0, N, -k2, 0, Vh, pa, &nb));
         outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 1, P.tol, P.max_outer,
                                                      P.max_iter);
         c->kernel_launches++;
     }
     // reconstruct x_o = b_o + kappa D_oe x_e
-    TRY(do_hop(c, P_F64, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
+    TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
     // full-lattice true residual b - M x
-    TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
-    TRY(do_hop(c, P_F64, MODE_RESID, RED_NORM, c->t64, xe, xo, bo, nullptr, 1, N, -k, 0, Vh, pb, &nb2));
+    TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
+    TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->t64, xe, xo, bo, nullptr, 1, N, -k, 0, Vh, pb, &nb2));
     full_norm_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 1);
     c->kernel_launches++;
     CK(cudaGetLastError());
@@ -1080,13 +1142,15 @@ static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool 
     const int Vh = (int)c->Vh;
     const int mode = with_m ? MODE_XPAY : MODE_PLAIN;
     const double coef = with_m ? -c->kappa : 1.0;
+    const char *ar = getenv("DLOOPS_HOP_ARITH");
+    const int op = (ar && std::string(ar) == "dff") ? P_DFF : P_F64;
     for (int j0 = 0; j0 < n_rhs; j0 += N) {
         const int n = std::min(N, n_rhs - j0);
         c->cur = c->stream;
         TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
-        TRY(do_hop(c, P_F64, mode, RED_NONE, c->x64, c->b64 + half, c->b64, nullptr, nullptr, 0, N, coef, 0, Vh,
+        TRY(do_hop(c, op, mode, RED_NONE, c->x64, c->b64 + half, c->b64, nullptr, nullptr, 0, N, coef, 0, Vh,
                    nullptr, nullptr));
-        TRY(do_hop(c, P_F64, mode, RED_NONE, c->x64 + half, c->b64, c->b64 + half, nullptr, nullptr, 1, N, coef, 0,
+        TRY(do_hop(c, op, mode, RED_NONE, c->x64 + half, c->b64, c->b64 + half, nullptr, nullptr, 1, N, coef, 0,
                    Vh, nullptr, nullptr));
         TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
     }
@@ -1669,7 +1733,11 @@ extern "C" int dl_bench_hop(dl_ctx *c, int precision, int n_rhs, int fused, int 
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(precision, c->lo[k], ne, 1234u + k, c->stream));
     const int Vh = (int)c->Vh;
+    if (fused < 0 || fused > 2) return fail(DL_EINVAL, "fused must be 0, 1 or 2");
     auto once = [&]() -> int {
+        if (fused == 2)
+            return do_hop(c, precision, MODE_XPAY, RED_BICG, lo_ptr(c, LT), lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr,
+                          lo_ptr(c, LRH), 0, N, -0.02, 0, Vh, c->d_partials, nullptr);
         if (fused)
             return do_hop(c, precision, MODE_XPAY, RED_R0DOT, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr,
                           lo_ptr(c, LRH), 0, N, -0.02, 0, Vh, c->d_partials, nullptr);

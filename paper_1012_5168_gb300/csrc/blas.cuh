@@ -79,6 +79,15 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2 *partials, in
     return make_double2(re, im);
 }
 
+// Relative reduction the inner phase aims for: delta, or less when less suffices
+// for the outer test |r| <= 0.5 tol min(|bhat|, |b|) (outer_update_kernel), with
+// a further factor of 2 for the drift of the low-precision recursive residual.
+__device__ __forceinline__ double inner_reduction(const OuterState &o, double delta) {
+    if (!(o.r2 > 0.0)) return delta;
+    const double need = 0.25 * sqrt(o.tol2 * fmin(o.b2, o.full_b2) / o.r2);
+    return fmax(delta, need);
+}
+
 // ---------------------------------------------------------------------------
 // scalar kernels: grid = N blocks of 32 threads (one warp per right-hand side)
 // ---------------------------------------------------------------------------
@@ -100,7 +109,8 @@ static __global__ void inner_start_kernel(RhsState *st, OuterState *os, const do
     s.beta = make_double2(0.0, 0.0);
     s.r2 = n2.x;
     s.r2_0 = n2.x;
-    s.target2 = delta * delta * n2.x;
+    const double red = inner_reduction(os[r], delta);
+    s.target2 = red * red * n2.x;
     s.iters = 0;
     s.status = ST_OK;
     const int left = max_total - os[r].iters;
@@ -500,7 +510,8 @@ static __global__ void cg_start_kernel(RhsState *st, OuterState *os, const doubl
     s.beta = make_double2(0.0, 0.0);
     s.r2 = n2.x;
     s.r2_0 = n2.x;
-    s.target2 = delta * delta * n2.x;
+    const double red = inner_reduction(os[r], delta);
+    s.target2 = red * red * n2.x;
     s.iters = 0;
     s.status = ST_OK;
     const int left = max_total - os[r].iters;
@@ -591,6 +602,7 @@ static __global__ void __launch_bounds__(256) accumulate_kernel(VecArgs a, const
 // ---------------------------------------------------------------------------
 // mode 0: initialise (b2 = |bhat|^2 from partials, r2 = b2, active = b2 > 0)
 // mode 1: after r = bhat - Mhat x: r2 from partials, convergence test, cycle count
+// mode 2: after a fixed-iteration phase: cycle and iteration counts only
 static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, const double2 *partials, int nblocks,
                                     int N, int mode, double tol, int max_outer, int max_iter) {
     const int r = blockIdx.x;
@@ -613,6 +625,7 @@ static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, c
     o.outer += 1;
     o.iters += st[r].iters;
     if (st[r].status == ST_NAN) o.status = ST_NAN;
+    if (mode == 2) return;
     o.r2 = n2.x;
     if (!isfinite(n2.x)) {
         o.status = ST_NAN;

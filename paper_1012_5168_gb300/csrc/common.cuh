@@ -68,13 +68,94 @@ template <typename T>
 __device__ __forceinline__ cx<T> zero() { return mk<T>(T(0), T(0)); }
 
 // ----------------------------------------------------------------------------
+// float-float ("double-float") reals: the unevaluated sum hi + lo of two
+// floats, about 48 significant bits.  Sums use Knuth's error-free two-sum and
+// products the FMA-based exact product (Dekker), each followed by a
+// renormalisation.  GB300 issues FP64 at about 1/60 of the FP32 rate, so FP64
+// work whose rounding needs more than FP32 but not all 53 bits runs faster in
+// this form on the FP32 pipes.
+// ----------------------------------------------------------------------------
+struct dfloat {
+    float hi, lo;
+    __device__ __forceinline__ dfloat() {}
+    __device__ __forceinline__ explicit dfloat(float h) : hi(h), lo(0.f) {}
+    __device__ __forceinline__ dfloat(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+};
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return dfloat(h, e - (h - s));
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float h = p + e;
+    return dfloat(h, e - (h - p));
+}
+__device__ __forceinline__ dfloat operator-(dfloat a) { return dfloat(-a.hi, -a.lo); }
+__device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df_add(a, b); }
+__device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return df_add(a, -b); }
+__device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) { return df_mul(a, b); }
+__device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = df_add(a, b); }
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return df_add(df_mul(a, b), c); }
+// double -> float-float with FP64 arithmetic (exact for normal floats).
+__device__ __forceinline__ dfloat df_from_double(double x) {
+    const float h = (float)x;
+    return dfloat(h, (float)(x - (double)h));
+}
+// double -> float-float from its bit pattern with integer operations only
+// (no FP64 instruction).  hi keeps the leading 24 significant bits
+// (truncated); lo is the remaining 29 bits rounded to a float, so hi + lo
+// agrees with x to about 2^-48 relative.  |x| below 2^-126 becomes 0, the lo
+// part of |x| below 2^-74 is dropped, and infinities and NaN propagate in hi.
+__device__ __forceinline__ dfloat df_from_bits(uint32_t w0, uint32_t w1) {
+    const uint32_t sign = w1 & 0x80000000u;
+    const int e = (int)((w1 >> 20) & 0x7ffu);
+    if (e == 0x7ff) {
+        const bool nan = ((w1 & 0xfffffu) | w0) != 0u;
+        return dfloat(__uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u)), 0.f);
+    }
+    const int eb = e - 1023 + 127;  // float exponent field of hi
+    if (eb <= 0) return dfloat(0.f, 0.f);
+    if (eb >= 255) return dfloat(__uint_as_float(sign | 0x7f800000u), 0.f);
+    const float hi = __uint_as_float(sign | ((uint32_t)eb << 23) | ((w1 & 0xfffffu) << 3) | (w0 >> 29));
+    const int es = e - 1075 + 127;  // float exponent field of 2^(e - 1075), the weight of mantissa bit 0
+    float lo = es > 0 ? __uint2float_rn(w0 & 0x1fffffffu) * __uint_as_float((uint32_t)es << 23) : 0.f;
+    return dfloat(hi, sign ? -lo : lo);
+}
+
+// Shuffle of a real across a warp (float-float: both halves).
+template <typename T>
+__device__ __forceinline__ T shfl_xor(T v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+template <>
+__device__ __forceinline__ dfloat shfl_xor<dfloat>(dfloat v, int off) {
+    return dfloat(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+}
+
+// A host-side double coefficient in the arithmetic type T.
+template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
+template <> __device__ __forceinline__ dfloat from_double<dfloat>(double x) { return df_from_double(x); }
+
+// ----------------------------------------------------------------------------
 // storage traits: S is the element type in memory (re and im interleaved);
 // arithmetic happens in Real<S> (double for FP64 storage, float otherwise).
+// dfs is FP64 storage with float-float arithmetic: fields stay double in
+// memory, links come from a float-float copy ([hi, lo] per real).
 // ----------------------------------------------------------------------------
+struct dfs {
+    double v;
+};
 template <typename S> struct Real;
 template <> struct Real<double> { typedef double type; };
 template <> struct Real<float> { typedef float type; };
 template <> struct Real<bf16> { typedef float type; };
+template <> struct Real<dfs> { typedef dfloat type; };
 
 template <typename S>
 __host__ __device__ constexpr int cbytes() { return 2 * (int)sizeof(S); }
@@ -174,6 +255,18 @@ template <> struct Conv<bf16> {
     }
 };
 
+template <> struct Conv<dfs> {
+    static constexpr int W = 4;
+    __device__ __forceinline__ static cx<dfloat> get(const uint32_t *w) {
+        return mk(df_from_bits(w[0], w[1]), df_from_bits(w[2], w[3]));
+    }
+    __device__ __forceinline__ static void put(cx<dfloat> z, uint32_t *w) {
+        const double r = (double)z.re, i = (double)z.im;
+        w[0] = (uint32_t)__double2loint(r); w[1] = (uint32_t)__double2hiint(r);
+        w[2] = (uint32_t)__double2loint(i); w[3] = (uint32_t)__double2hiint(i);
+    }
+};
+
 // Load / store R consecutive complex values of storage type S.
 template <typename S, int R, bool NC>
 __device__ __forceinline__ void ld_pack(const S *p, cx<typename Real<S>::type> (&v)[R]) {
@@ -198,6 +291,12 @@ __device__ __forceinline__ cx<typename Real<S>::type> ld_link(const S *p) {
     uint32_t w[cbytes<S>() / 4];
     RawLd<cbytes<S>(), true>::ld(p, w);
     return Conv<S>::get(w);
+}
+// float-float links: (re.hi, re.lo, im.hi, im.lo) in the 16 bytes of a complex
+template <>
+__device__ __forceinline__ cx<dfloat> ld_link<dfs>(const dfs *p) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return mk(dfloat(v.x, v.y), dfloat(v.z, v.w));
 }
 
 // ----------------------------------------------------------------------------
@@ -261,8 +360,8 @@ __device__ __forceinline__ void block_reduce(cx<T> (&v)[R][NV], int G, int N, do
         for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                v[r][k].re += __shfl_xor_sync(0xffffffffu, v[r][k].re, off);
-                v[r][k].im += __shfl_xor_sync(0xffffffffu, v[r][k].im, off);
+                v[r][k].re += shfl_xor(v[r][k].re, off);
+                v[r][k].im += shfl_xor(v[r][k].im, off);
             }
     }
     if (lane < GW) {

@@ -278,59 +278,22 @@ static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Gaussian smearing in float-float ("double-float") arithmetic.  A real is the
-// unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2, about 48
-// significant bits.  Sums use Knuth's error-free two-sum and products the
-// FMA-based exact product (Dekker), each followed by a renormalisation.  The
+// Gaussian smearing in float-float arithmetic (dfloat, common.cuh).  The
 // smearing runs on the FP32 pipes, which on GB300 issue about 60 times as fast
 // as FP64, while its rounding (~1e-14 relative per step) stays far below the
 // tolerance of the loops.  Fields in this format occupy the same 8 bytes per
 // real as FP64 and are converted in place before and after the iterations.
 // ---------------------------------------------------------------------------
-struct ff {
-    float hi, lo;
-};
-__device__ __forceinline__ ff ff_from(double x) {
-    ff r;
-    r.hi = (float)x;
-    r.lo = (float)(x - (double)r.hi);
-    return r;
-}
-__device__ __forceinline__ double ff_to(ff a) { return (double)a.hi + (double)a.lo; }
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-    const float s = a.hi + b.hi;
-    const float bb = s - a.hi;
-    float e = (a.hi - (s - bb)) + (b.hi - bb);
-    e += a.lo + b.lo;
-    ff r;
-    r.hi = s + e;
-    r.lo = e - (r.hi - s);
-    return r;
-}
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const float p = a.hi * b.hi;
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, e);
-    e = fmaf(a.lo, b.hi, e);
-    ff r;
-    r.hi = p + e;
-    r.lo = e - (r.hi - p);
-    return r;
-}
-__device__ __forceinline__ ff ff_neg(ff a) {
-    a.hi = -a.hi;
-    a.lo = -a.lo;
-    return a;
-}
+typedef dfloat ff;
 struct ffc {
     ff re, im;
 };
 // acc += a * b  (DAG: acc += conj(a) * b)
 template <bool DAG>
 __device__ __forceinline__ void ffc_mac(ffc &acc, ffc a, ffc b) {
-    const ff ai = DAG ? ff_neg(a.im) : a.im;
-    acc.re = ff_add(acc.re, ff_add(ff_mul(a.re, b.re), ff_neg(ff_mul(ai, b.im))));
-    acc.im = ff_add(acc.im, ff_add(ff_mul(a.re, b.im), ff_mul(ai, b.re)));
+    const ff ai = DAG ? -a.im : a.im;
+    acc.re = df_add(acc.re, df_add(df_mul(a.re, b.re), -df_mul(ai, b.im)));
+    acc.im = df_add(acc.im, df_add(df_mul(a.re, b.im), df_mul(ai, b.re)));
 }
 __device__ __forceinline__ ffc ld_ffc(const double *p) {
     const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
@@ -357,14 +320,14 @@ static __global__ void ff_convert_kernel(double *f, int Vh, int cb0, int cb1, in
         const int cb = cb0 + (int)(sp % nsite) + (tcol ? tcol[j] * V3h : 0);
         double *e = f + (((size_t)p * Vh + cb) * 12 * N + (size_t)c * N + j) * 2;
         if (to_ff) {
-            const ff a = ff_from(e[0]), b = ff_from(e[1]);
+            const ff a = df_from_double(e[0]), b = df_from_double(e[1]);
             *reinterpret_cast<float4 *>(e) = make_float4(a.hi, a.lo, b.hi, b.lo);
         } else {
             const float4 v = *reinterpret_cast<const float4 *>(e);
             ff a, b;
             a.hi = v.x; a.lo = v.y; b.hi = v.z; b.lo = v.w;
-            e[0] = ff_to(a);
-            e[1] = ff_to(b);
+            e[0] = (double)a;
+            e[1] = (double)b;
         }
     }
 }
@@ -372,7 +335,7 @@ static __global__ void ff_convert_kernel(double *f, int Vh, int cb0, int cb1, in
 // Links in float-float: [2][Vh][4][9] complex as (re.hi, re.lo, im.hi, im.lo).
 static __global__ void gauge_ff_kernel(const double *g64, float *out, long n_complex) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n_complex; i += (long)gridDim.x * blockDim.x) {
-        const ff a = ff_from(g64[2 * i]), b = ff_from(g64[2 * i + 1]);
+        const ff a = df_from_double(g64[2 * i]), b = df_from_double(g64[2 * i + 1]);
         reinterpret_cast<float4 *>(out)[i] = make_float4(a.hi, a.lo, b.hi, b.lo);
     }
 }
@@ -383,7 +346,7 @@ static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const
     const int nsite = A.cb1 - A.cb0;
     const int total = 2 * nsite * A.N;
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
-    const ff fa = ff_from(A.a), fc = ff_from(A.c);
+    const ff fa = df_from_double(A.a), fc = df_from_double(A.c);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         const int j = idx % A.N;
         if (j >= A.n) continue;
@@ -428,8 +391,8 @@ static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const
         for (int k = 0; k < 12; ++k) {
             const ffc q = ld_ffc(y + (size_t)k * A.N * 2);
             ffc r;
-            r.re = ff_add(ff_mul(fa, q.re), ff_mul(fc, acc[k].re));
-            r.im = ff_add(ff_mul(fa, q.im), ff_mul(fc, acc[k].im));
+            r.re = df_add(df_mul(fa, q.re), df_mul(fc, acc[k].re));
+            r.im = df_add(df_mul(fa, q.im), df_mul(fc, acc[k].im));
             *reinterpret_cast<float4 *>(o + (size_t)k * A.N * 2) = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
         }
     }

@@ -192,7 +192,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
 }
 
 template <typename S, int R, int MODE, int RED>
-__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
+__device__ __forceinline__ void hop_body(const HopArgs &A) {
     typedef typename Real<S>::type T;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     const int lgG = __ffs(G) - 1;
     const size_t N = (size_t)A.N;
     const int total = (A.cb_end - A.cb_begin) << lgG;  // < 2^31 (checked by the host)
-    const T cD = (T)A.c;
+    const T cD = from_double<T>(A.c);
     cx<T> red[R][NV];
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -267,6 +267,32 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
         }
     }
     if (RED != RED_NONE) block_reduce<R, NV, T>(red, G, A.N, A.partials, smem);
+}
+
+// Register caps of the direct hop (0: the compiler's choice under a 256-thread
+// launch bound).  The kernel is bound by memory latency: fewer registers per
+// thread let more warps, and so more loads, be in flight per SM.  Measured on
+// GB300 with FP32 storage, one right-hand side per thread and 32 right-hand
+// sides (bench.py --hop-profile), against the compiler's choice:
+//   plain hop            80 -> 64 registers: 0.142 -> 0.133 ms
+//   XPAY + <rhat, v>     80 -> 72 registers: 0.185 -> 0.170 ms
+//   XPAY + 5 reductions 110 -> 72 registers: 0.216 -> 0.182 ms
+// R > 1 spills and runs 3-4x slower under such caps.  BF16 at R = 1 gained
+// nothing from them and its tuner picks R = 2 or 4.  FP64 is bound by FP64
+// issue.  So all of these stay uncapped.
+template <typename S, int R, int MODE, int RED> struct HopRegCap {
+    static constexpr bool f32r1 = sizeof(S) == 4 && R == 1;
+    static constexpr int n = !f32r1 ? 0 : (MODE == MODE_PLAIN ? 64 : 72);
+};
+
+template <typename S, int R, int MODE, int RED>
+__global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
+    hop_body<S, R, MODE, RED>(A);
+}
+
+template <typename S, int R, int MODE, int RED, int CAP>
+__global__ void __maxnreg__(CAP) hop_kernel_cap(HopArgs A) {
+    hop_body<S, R, MODE, RED>(A);
 }
 
 
@@ -407,7 +433,7 @@ __global__ void __launch_bounds__(256) hop_kernel_pf(HopArgs A) {
     const size_t N = (size_t)A.N;
     const int total = (A.cb_end - A.cb_begin) << lgG;
     const int stride = gridDim.x * blockDim.x;
-    const T cD = (T)A.c;
+    const T cD = from_double<T>(A.c);
     cx<T> red[R][NV];
 #pragma unroll
     for (int r = 0; r < R; ++r)

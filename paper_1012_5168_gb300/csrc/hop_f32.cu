@@ -18,8 +18,14 @@ static cudaError_t go(const HopArgs &a, Launch &l, int pf) {
         return cudaGetLastError();
     }
     if (!pf) {
-        clamp_grid(l, resident_blocks(hop_kernel<float, R, MODE, RED>, l.block, l.smem));
-        hop_kernel<float, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        constexpr int cap = HopRegCap<float, R, MODE, RED>::n;
+        if constexpr (cap > 0) {
+            clamp_grid(l, resident_blocks(hop_kernel_cap<float, R, MODE, RED, cap>, l.block, l.smem));
+            hop_kernel_cap<float, R, MODE, RED, cap><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        } else {
+            clamp_grid(l, resident_blocks(hop_kernel<float, R, MODE, RED>, l.block, l.smem));
+            hop_kernel<float, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        }
         return cudaGetLastError();
     }
     static size_t opted = 0;  // largest dynamic shared memory opted in so far
@@ -40,14 +46,17 @@ cudaError_t launch_hop_f32(int R, int mode, int red, int pf, const HopArgs &a, L
     DL_CASE(1, MODE_XPAY, RED_NONE)
     DL_CASE(1, MODE_XPAY, RED_R0DOT)
     DL_CASE(1, MODE_XPAY, RED_BICG)
+    DL_CASE(1, MODE_XPAY, RED_NORM)
     DL_CASE(2, MODE_PLAIN, RED_NONE)
     DL_CASE(2, MODE_XPAY, RED_NONE)
     DL_CASE(2, MODE_XPAY, RED_R0DOT)
     DL_CASE(2, MODE_XPAY, RED_BICG)
+    DL_CASE(2, MODE_XPAY, RED_NORM)
     DL_CASE(4, MODE_PLAIN, RED_NONE)
     DL_CASE(4, MODE_XPAY, RED_NONE)
     DL_CASE(4, MODE_XPAY, RED_R0DOT)
     DL_CASE(4, MODE_XPAY, RED_BICG)
+    DL_CASE(4, MODE_XPAY, RED_NORM)
 #undef DL_CASE
     return cudaErrorInvalidValue;
 }

@@ -12,7 +12,9 @@
 
 namespace dl {
 
-enum { P_F64 = 0, P_F32 = 1, P_BF16 = 2 };
+// Storage precisions.  P_DFF is internal to the Wilson hop: FP64 fields and a
+// float-float link copy, float-float arithmetic (defect-correction residuals).
+enum { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_DFF = 3 };
 
 struct Launch {
     int grid;
@@ -49,6 +51,9 @@ inline void clamp_grid(Launch &l, int resident) {
 // lowered to the kernel's residency (l.num_sms > 0); the launch used is left in l.
 // Returns cudaErrorInvalidValue for a combination that is not instantiated.
 cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, Launch &l);
+// The same hop on FP64 fields in float-float arithmetic; a.gauge is the
+// float-float link copy [2][Vh][4][9] x (re.hi, re.lo, im.hi, im.lo).  R = 1.
+cudaError_t launch_hop_dff(int R, int mode, int red, const HopArgs &a, Launch &l);
 // kind (low precision only): 0 direct loads; 1 cp.async prefetching kernel,
 // dynamic shared memory pf_stage_bytes(prec, R) * 2 * block; 2 bulk-copy
 // staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R)).
@@ -82,6 +87,12 @@ cudaError_t launch_inner_init(const VecLaunch &v, const OuterState *os, const Rh
                               void *x, void *r, void *rhat, void *p, double2 *partials, int restart);
 cudaError_t launch_accumulate(const VecLaunch &v, const OuterState *os, const void *x, double *x64);
 cudaError_t launch_norm2(const VecLaunch &v, const void *x, double2 *partials);
+// CG on the normal equations (blas.cuh)
+cudaError_t launch_cg_init(const VecLaunch &v, const OuterState *os, const double *r64, void *x, void *r5,
+                           double2 *partials);
+cudaError_t launch_cg_update(const VecLaunch &v, const RhsState *st, void *x, void *r5, const void *p, const void *w,
+                             double2 *partials);
+cudaError_t launch_cg_p(const VecLaunch &v, const RhsState *st, const void *u, void *p, int init);
 cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s);
 
 }  // namespace dl

@@ -61,6 +61,34 @@ cudaError_t launch_norm2(const VecLaunch &v, const void *x, double2 *partials) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_cg_init(const VecLaunch &v, const OuterState *os, const double *r64, void *x, void *r5,
+                           double2 *partials) {
+#define CALL(S, RR)                                                                                     \
+    cg_init_kernel<S, RR><<<v.l.grid, v.l.block, v.l.smem, v.l.stream>>>(v.a, os, r64, (S *)x, (S *)r5, \
+                                                                        partials)
+    DL_DISPATCH(v.prec, v.R, CALL);
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(const VecLaunch &v, const RhsState *st, void *x, void *r5, const void *p, const void *w,
+                             double2 *partials) {
+#define CALL(S, RR)                                                                                      \
+    cg_update_kernel<S, RR><<<v.l.grid, v.l.block, v.l.smem, v.l.stream>>>(v.a, st, (S *)x, (S *)r5,      \
+                                                                          (const S *)p, (const S *)w, partials)
+    DL_DISPATCH(v.prec, v.R, CALL);
+#undef CALL
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_p(const VecLaunch &v, const RhsState *st, const void *u, void *p, int init) {
+#define CALL(S, RR) \
+    cg_p_kernel<S, RR><<<v.l.grid, v.l.block, 0, v.l.stream>>>(v.a, st, (const S *)u, (S *)p, init)
+    DL_DISPATCH(v.prec, v.R, CALL);
+#undef CALL
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s) {
     const int grid = 1024, block = 256;
     if (prec == P_F64) fill_kernel<double><<<grid, block, 0, s>>>((double *)x, n_complex, seed);

@@ -53,3 +53,31 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """sizeof and field offsets of the ABI structs, from the C compiler, equal the ctypes mirrors."""
+    import shutil
+    import subprocess
+    import paper_1012_5168_gb300 as dl
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"dl_solve_params": dl.SolveParams, "dl_solve_stats": dl.SolveStats, "dl_smear": dl.Smear,
+               "dl_timing": dl.Timing}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "dloops.h"', "int main(void) {"]
+    for name, py in mirrors.items():
+        lines.append(f'printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in py._fields_:
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l}
+    for name, py in mirrors.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(py), name
+        for field, _ in py._fields_:
+            assert got[(name, field)] == getattr(py, field).offset, (name, field)

@@ -48,6 +48,30 @@ def test_hop_matches_oracle(lib, dims, t_bc):
     c.close()
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8)])
+def test_float_float_hop_matches_oracle(lib, dims, monkeypatch):
+    """The float-float hop of the defect-correction steps: about 48 significant bits.
+
+    Inputs span magnitudes from 1e-20 to 1e3 with zeros, so the bit-level
+    double -> float-float split is exercised over many exponents.
+    """
+    c, U = ctx_for(lib, dims)
+    psi = synthetic.random_spinor(dims, seed=11, n=3)
+    rng = np.random.default_rng(3)
+    psi[1] *= 10.0 ** rng.uniform(-20, 3, size=psi[1].shape)
+    psi[2].reshape(-1)[::7] = 0.0
+    monkeypatch.setenv("DLOOPS_HOP_ARITH", "dff")
+    out = c.apply_hop(to_gpu(psi)).cpu().numpy()
+    m = c.apply_m(to_gpu(psi)).cpu().numpy()
+    monkeypatch.delenv("DLOOPS_HOP_ARITH")
+    for j in range(3):
+        ref = wilson.hop(U, psi[j:j + 1], -1.0)
+        assert np.linalg.norm(out[j:j + 1] - ref) < 2e-14 * np.linalg.norm(ref)
+        refm = wilson.apply_m(U, psi[j:j + 1], 0.13, -1.0)
+        assert np.linalg.norm(m[j:j + 1] - refm) < 2e-14 * np.linalg.norm(refm)
+    c.close()
+
+
 def test_hop_full_size(lib):
     dims = (16, 16, 16, 32)
     c, U = ctx_for(lib, dims, kappa=0.14, seed=1)

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import synthetic
-from oracle import wilson
+from oracle import krylov, wilson
 
 pytestmark = pytest.mark.gpu
 
@@ -172,4 +172,88 @@ def test_hop_kernel_kinds_full_size(lib):
         sols.append(x)
     for x in sols[1:]:
         assert (torch.linalg.vector_norm(x - sols[0]) / torch.linalg.vector_norm(sols[0])).item() < 1e-9
+    c.close()
+
+
+@pytest.mark.parametrize("method", [0, 1])
+@pytest.mark.parametrize("k", [1, 7, 25])
+def test_fixed_iteration_map_matches_oracle(lib, method, k):
+    """FP64 storage, k fixed iterations of BiCGStab (0) or CGNR (1) on the Schur system.
+
+    The GPU iterate, reconstructed on the full lattice, equals the oracle's
+    restatement of the same k steps (the low-precision map of the truncated
+    solver method, here without the rounding of a low-precision type).
+    """
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=12)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=13, n=3)
+    x, st = c.solve(to_gpu(b), lib.Params(precision=0, fixed_iters=k, batch=4, method=method))
+    x = x.cpu().numpy()
+    op = lambda v: krylov.schur_apply(U, v, kappa)  # noqa: E731
+    opd = lambda v: krylov.schur_apply_dag(U, v, kappa)  # noqa: E731
+    for j in range(3):
+        assert st[j]["iters"] == k
+        bhat = krylov.schur_rhs(U, b[j], kappa)
+        xe = krylov.cgnr(op, opd, bhat, n_iter=k)[0] if method else krylov.bicgstab_fixed(op, bhat, k)[0]
+        ref = krylov.schur_reconstruct(U, xe, b[j], kappa)
+        assert np.abs(x[j] - ref).max() < 1e-11 * np.abs(ref).max()
+    c.close()
+
+
+def test_bf16_lp_map_error_bound(lib):
+    """30 BF16 BiCGStab iterations (the benchmark's low-precision map) stay within a stated
+    bound of the same 30 iterations in FP64: BF16 keeps 8 significand bits, so the map is
+    parity-unpinned beyond that bound."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=14)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=15, n=2)
+    x, _ = c.solve(to_gpu(b), lib.Params(precision=2, fixed_iters=30, batch=2))
+    x = x.cpu().numpy()
+    op = lambda v: krylov.schur_apply(U, v, kappa)  # noqa: E731
+    for j in range(2):
+        bhat = krylov.schur_rhs(U, b[j], kappa)
+        ref = krylov.schur_reconstruct(U, krylov.bicgstab_fixed(op, bhat, 30)[0], b[j], kappa)
+        err = np.linalg.norm(x[j] - ref) / np.linalg.norm(ref)
+        print(f"bf16 30-iteration map: relative difference {err:.3e}")
+        assert err < 1e-2
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_cgnr_solve_small(lib, prec):
+    """CGNR inner solver with FP64 defect correction: ragged batch, graph and eager."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=16)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=17, n=5)
+    for graph in (1, 0):
+        x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=prec, batch=4, use_graph=graph, chunk=5,
+                                              method=lib.METHOD_CGNR))
+        assert all(s["status"] == 0 for s in st), st
+        assert np.all(residual(U, x.cpu().numpy(), b, kappa) <= 1e-11)
+    c.close()
+
+
+def test_cgnr_single_precision_lp_full_size(lib):
+    """Sec. 2's low-precision solve on 16^3 x 32: single-precision CG to a 1e-6 tolerance."""
+    w = synthetic.WORKLOADS["wilson_16x16x16x32"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    c = lib.Context(w["dims"])
+    c.load_gauge(U)
+    c.set_kappa(w["kappa"])
+    eta = c.make_sources(seed=2, noise_first=0, n_noise=16, dilution=0)
+    x, st = c.solve(eta, lib.Params(tol=1e-6, precision=1, delta=1e-6, batch=16, method=lib.METHOD_CGNR))
+    assert all(s["status"] == 0 and s["true_residual"] <= 1e-6 for s in st), st
+    b = eta[:1].cpu().numpy()
+    assert residual(U, x[:1].cpu().numpy(), b, w["kappa"])[0] <= 1e-6
+    x2, _ = c.solve(eta, lib.Params(tol=1e-6, precision=1, delta=1e-6, batch=16, method=lib.METHOD_CGNR))
+    assert torch.equal(x, x2)  # a deterministic map, as the truncated solver method needs
     c.close()

@@ -1,0 +1,79 @@
+"""Pins of the oracle's momentum loops and correlators (CPU)."""
+
+import numpy as np
+
+import synthetic
+from oracle import correlators, lattice, loops, wilson
+
+G16 = lattice.gamma_basis()
+
+
+def test_zero_momentum_loops_are_the_loops():
+    dims = (4, 2, 2, 4)
+    eta = synthetic.random_spinor(dims, seed=1, n=3)
+    phi = synthetic.random_spinor(dims, seed=2, n=3)
+    got = correlators.momentum_loops(eta, phi, [(0, 0, 0), (1, 0, 1)], G16)
+    assert np.abs(got[:, 0] - loops.stochastic_loops(eta, phi)).max() < 1e-12
+    # a plane wave at p: the momentum sum equals the zero-momentum sum of the phase-weighted field
+    ph = correlators.momentum_phases(dims, [(1, 0, 1)])[0]
+    ref = loops.stochastic_loops(eta, phi * ph[None, ..., None, None])
+    assert np.abs(got[:, 1] - ref).max() < 1e-12
+
+
+def test_exact_momentum_loops_zero_momentum_and_translation():
+    dims, kappa = (4, 2, 2, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.5, seed=3)
+    moms = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 1)]
+    L = correlators.exact_momentum_loops_dense(U, kappa, moms, G16)
+    assert np.abs(L[0] - loops.exact_loops_dense(U, kappa, -1.0)).max() < 1e-12
+    # U'(x) = U(x + e_x): M'^-1(x, x) = M^-1(x + e_x, x + e_x), so L'(p) = exp(+i p_x) L(p)
+    Us = np.roll(U, -1, axis=3)  # U has shape [T][Z][Y][X][mu][3][3]
+    Lt = correlators.exact_momentum_loops_dense(Us, kappa, moms, G16)
+    for i, n in enumerate(moms):
+        assert np.abs(Lt[i] - np.exp(2j * np.pi * n[0] / dims[0]) * L[i]).max() < 1e-11
+
+
+def test_free_field_has_no_loops_at_nonzero_momentum():
+    dims, kappa = (4, 2, 2, 4), 0.1
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (4, 2, 2, 4, 4, 3, 3)).copy()
+    L = correlators.exact_momentum_loops_dense(U, kappa, [(0, 0, 0), (1, 0, 0), (2, 1, 1)], G16)
+    assert np.abs(L[0, 0]).min() > 1.0
+    assert np.abs(L[1:]).max() < 1e-12
+
+
+def test_disconnected_by_hand():
+    rng = np.random.default_rng(0)
+    T = 5
+    lb = rng.standard_normal((2, T)) + 1j * rng.standard_normal((2, T))
+    la = rng.standard_normal((2, T)) + 1j * rng.standard_normal((2, T))
+    D = correlators.disconnected(lb, la, spatial_volume=8)
+    for dt in range(T):
+        ref = -sum(lb[:, (t + dt) % T] * la[:, t] for t in range(T)) / (8 * T)
+        assert np.allclose(D[:, dt], ref, rtol=1e-14, atol=1e-14)
+
+
+def test_free_point_propagator_fft_equals_the_solver():
+    dims, kappa, src = (4, 4, 2, 4), 0.11, (1, 2, 0, 3)
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (4, 2, 4, 4, 4, 3, 3)).copy()
+    solved = correlators.point_propagator(U, kappa, src)
+    fft = correlators.free_point_propagator(dims, kappa, src)
+    assert np.abs(solved - fft).max() < 1e-11 * np.abs(fft).max()
+
+
+def test_connected_pion_is_minus_sum_of_squares_and_symmetric():
+    dims, kappa, src = (4, 4, 2, 4), 0.11, (0, 0, 0, 0)
+    U = np.broadcast_to(np.eye(3, dtype=np.complex128), (4, 2, 4, 4, 4, 3, 3)).copy()
+    prop = correlators.free_point_propagator(dims, kappa, src)
+    C = correlators.connected(prop, src, [(0, 0, 0), (1, 0, 0)], G16)
+    pion = C[0, 5, 5]  # Gamma_A = Gamma_B = gamma5
+    direct = -np.array([np.sum(np.abs(prop[:, t]) ** 2) for t in range(dims[3])])
+    assert np.abs(pion - direct).max() < 1e-12 * np.abs(direct).max()
+    assert np.abs(pion.imag).max() < 1e-14 * np.abs(direct).max()
+    assert np.allclose(pion[1:], pion[1:][::-1], rtol=1e-10)  # C(t) = C(T - t) for a free field
+    # gauge links: the same reduction holds configuration by configuration
+    Ug = synthetic.gauge_field(dims, eps=0.4, seed=5)
+    pg = correlators.point_propagator(Ug, kappa, (1, 0, 1, 2))
+    Cg = correlators.connected(pg, (1, 0, 1, 2), [(0, 0, 0)], G16)
+    direct = -np.array([np.sum(np.abs(pg[:, t]) ** 2) for t in range(dims[3])])
+    assert np.abs(Cg[0, 5, 5] - np.roll(direct, -2)).max() < 1e-12 * np.abs(direct).max()
+    assert wilson.plaquette(Ug) < 0.99
