@@ -81,6 +81,28 @@ def disconnected(loops_b: np.ndarray, loops_a_minus_p: np.ndarray, spatial_volum
     return out
 
 
+def disconnected_pairs(loops: np.ndarray, cover, minus, spatial_volume: int) -> np.ndarray:
+    """D^{BA}(q, dt) from per-noise loops [n][Q][16][T], averaged over ordered pairs
+    (n, m), n != m, with n covering t + dt and m covering t:
+        D = -(1 / (L^3 T)) sum_t mean_{pairs} L^n_B(q, t + dt) L^m_A(-q, t).
+    cover: bool [n][T] (None: all); minus[q]: index of -q.  Returns [Q][16 A][16 B][T]."""
+    n, Q, _, T = loops.shape
+    cover = np.ones((n, T), dtype=bool) if cover is None else np.asarray(cover, dtype=bool)
+    out = np.zeros((Q, 16, 16, T), dtype=np.complex128)
+    for q in range(Q):
+        for dt in range(T):
+            acc = np.zeros((16, 16), dtype=np.complex128)  # [A][B]
+            for t in range(T):
+                t2 = (t + dt) % T
+                pairs = [(a, b) for a in range(n) for b in range(n) if a != b and cover[a, t2] and cover[b, t]]
+                if not pairs:
+                    continue
+                s = sum(np.outer(loops[b, minus[q], :, t], loops[a, q, :, t2]) for a, b in pairs)
+                acc += s / len(pairs)
+            out[q, :, :, dt] = -acc / (spatial_volume * T)
+    return out
+
+
 def point_propagator(U, kappa, src, t_bc=-1.0, tol=1e-13) -> np.ndarray:
     """The 12 solutions M phi = e_{src, alpha, a}: [12 = 3 alpha + a][T][Z][Y][X][4][3]."""
     lt, lz, ly, lx = U.shape[:4]

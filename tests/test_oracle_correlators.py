@@ -77,3 +77,29 @@ def test_connected_pion_is_minus_sum_of_squares_and_symmetric():
     direct = -np.array([np.sum(np.abs(pg[:, t]) ** 2) for t in range(dims[3])])
     assert np.abs(Cg[0, 5, 5] - np.roll(direct, -2)).max() < 1e-12 * np.abs(direct).max()
     assert wilson.plaquette(Ug) < 0.99
+
+
+def test_disconnected_pairs_reduces_to_the_product_formula():
+    """With identical per-noise loops and full coverage the pair average is the plain product."""
+    rng = np.random.default_rng(4)
+    Q, T = 3, 4
+    L = rng.standard_normal((Q, 16, T)) + 1j * rng.standard_normal((Q, 16, T))
+    minus = [0, 2, 1]
+    D = correlators.disconnected_pairs(np.stack([L] * 3), None, minus, spatial_volume=8)
+    for q in range(Q):
+        for A in (0, 5, 9):
+            for B in (0, 5, 14):
+                ref = correlators.disconnected(L[q, B], L[minus[q], A], 8)
+                assert np.allclose(D[q, A, B], ref, rtol=1e-13, atol=1e-15)
+
+
+def test_disconnected_pairs_excludes_self_products():
+    """Two noise vectors: only the cross products n != m enter, each ordered pair once."""
+    T = 2
+    L = np.zeros((2, 1, 16, T), dtype=np.complex128)
+    L[0, 0, 0] = [1.0, 2.0]
+    L[1, 0, 0] = [3.0, 5.0]
+    D = correlators.disconnected_pairs(L, None, [0], spatial_volume=1)
+    # dt = 0: t = 0 -> (1*3 + 3*1)/2, t = 1 -> (2*5 + 5*2)/2; dt = 1: t = 0 -> (L(1) L(0)): (2*3 + 5*1)/2, t = 1 -> (1*5 + 3*2)/2
+    assert np.isclose(D[0, 0, 0, 0], -(3.0 + 10.0) / 2)
+    assert np.isclose(D[0, 0, 0, 1], -((6.0 + 5.0) / 2 + (5.0 + 6.0) / 2) / 2)
