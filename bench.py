@@ -50,14 +50,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="stochastic",
                     choices=["stochastic", "exact_4x4x4x4", "single_rhs_16x16x16x32", "tsm_8x8x8x16",
-                             "autograd"],
+                             "autograd", "correlators_16x16x16x32", "dilution_8x8x8x16"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--hop-profile", metavar="PREC:N[:KIND[:R:BLOCK]]", default=None,
                     help="time the Wilson hop alone on the 16^3x32 workload (f32|bf16|f64, batch N, kernel kind "
                          "0 direct / 1 prefetch / 2 staged, right-hand sides per thread, block size; default "
                          "autotuned) and exit.  With all five fields the hop launches are, in order: 12 of the "
-                         "forced tuning run, 22 timing the choice, 8 plain (3 warm-up), 8 fused (3 warm-up)")
+                         "forced tuning run, 22 timing the choice, 8 plain (3 warm-up), 8 XPAY + <rhat, v> "
+                         "(3 warm-up), 8 XPAY + five reductions (3 warm-up)")
     return ap.parse_args()
 
 
@@ -338,6 +339,96 @@ def workload_tsm():
     print(json.dumps(out), flush=True)
 
 
+def workload_correlators():
+    """Sec. 3 two-point functions on 16^3 x 32 (kappa 0.140): the connected pion from one point source
+    (12 solves) and the disconnected function of 16 spin x colour x even-odd diluted noise vectors
+    (384 solves, all timeslices) at the 7 momenta 0, +-e_x, +-e_y, +-e_z; ratio D/C_pi (Eq. 4)."""
+    import numpy as np
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "wilson_16x16x16x32")
+    T = w["dims"][3]
+    moms = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    p = dl.Params(tol=w["tol"], precision=dl.PREC_F32, batch=32)
+    out = {"workload": "correlators_16x16x16x32", "momenta": moms}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prop, st = ctx.solve(ctx.make_point_sources(0, 12), p)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    C = ctx.meson_correlators(prop, (0, 0, 0, 0), moms)
+    t2 = time.perf_counter()
+    n_noise = 16
+    dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_EVENODD
+    eta = ctx.make_sources(seed=7, noise_first=0, n_noise=n_noise, dilution=dil)
+    K = eta.shape[0] // n_noise
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    phi, _ = ctx.solve(eta, p)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    L = ctx.trace_loops_mom(eta, phi, moms, dl.SINK_LOCAL, group=K)[:, 0]  # [n_noise][Q][16][T]
+    t5 = time.perf_counter()
+    D = ctx.disconnected(L, moms)
+    t6 = time.perf_counter()
+    pion, dg5 = C[0, 5, 5], D[0, 5, 5]
+    out.update({
+        "point_solves_s": round(t1 - t0, 3), "meson_contraction_s": round(t2 - t1, 4),
+        "noise_solves": int(eta.shape[0]), "noise_solve_s": round(t4 - t3, 3),
+        "momentum_loops_s": round(t5 - t4, 4), "disconnected_s": round(t6 - t5, 4),
+        "pion_t0_4": [float(v) for v in pion.real[:5]],
+        "pion_p1_t0_4": [float(v) for v in C[1, 5, 5].real[:5]],
+        "D_g5g5_t0_4": [float(v) for v in dg5.real[:5]],
+        "ratio_D_over_Cpi_t0_4": [float(v) for v in (dg5.real / pion.real)[:5]],
+    })
+    print(json.dumps(out), flush=True)
+
+
+def workload_dilution():
+    """Stochastic error vs number of inversions per dilution scheme (the study of Sec. 3, Figs. 3-4,
+    without the gauge-noise line, which needs an ensemble): 8^3 x 16 (kappa 0.140, eps 0.45), time
+    dilution by translation in every scheme, exact loops from all 12V point sources as the reference."""
+    import numpy as np
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "tsm_8x8x8x16")
+    V = int(np.prod(w["dims"]))
+    T = w["dims"][3]
+    p = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=64)
+    t0 = time.perf_counter()
+    exact, _ = ctx.exact_loops(0, 12 * V, p)
+    exact = exact[0]  # [16][T]
+    out = {"workload": "dilution_8x8x8x16", "exact_seconds": round(time.perf_counter() - t0, 2), "schemes": {}}
+    S, C, E, Q, TD = dl.DIL_SPIN, dl.DIL_COLOUR, dl.DIL_EVENODD, dl.DIL_CUBIC, dl.DIL_TIME
+    schemes = {"time": TD, "spin": S | TD, "colour": C | TD, "spin_colour": S | C | TD, "evenodd": E | TD,
+               "spin_colour_evenodd": S | C | E | TD, "cubic": Q | TD, "spin_colour_cubic": S | C | Q | TD}
+    names = dl.GAMMA_NAMES
+    scale = np.sqrt((np.abs(exact) ** 2).mean(axis=1))  # RMS over t of each Gamma's exact loop
+    for label, dil in schemes.items():
+        K = dl.n_classes(dil)
+        res = {"classes": K}
+        for n_inv in (384, 1536):
+            n_noise = max(2, n_inv // K)
+            eta = ctx.make_sources(seed=11, noise_first=0, n_noise=n_noise, dilution=dil, t0=-1)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            phi, _ = ctx.solve(eta, p)
+            t_of = [(j // K) % T for j in range(n_noise * K)]
+            L = ctx.trace_loops(eta, phi, dl.SINK_LOCAL, t_of_rhs=t_of, group=K)[:, 0]  # [n_noise][16][T]
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t1
+            cover = np.array([[(n % T) == t for t in range(T)] for n in range(n_noise)])
+            cnt = cover.sum(0)
+            est = L.sum(0) / np.maximum(cnt, 1)
+            err = np.sqrt((np.abs(est - exact) ** 2)[:, cnt > 0].mean(axis=1))  # RMS over covered t
+            res[f"n_inv_{n_noise * K}"] = {
+                "seconds": round(el, 3),
+                "rel_error": {names[g]: float(err[g] / scale[g]) if scale[g] > 0 else None for g in range(16)},
+                "error_times_sqrt_ninv": {names[g]: float(err[g] * np.sqrt(n_noise * K)) for g in range(16)}}
+        out["schemes"][label] = res
+    print(json.dumps(out), flush=True)
+
+
 def workload_autograd():
     """d/dkappa Tr[g5 M^-1] and grad wrt the Z2 sources through LoopTrace, 32 right-hand sides,
     on 8^3 x 16 and 16^3 x 32; FP64 central finite difference dkappa = 1e-5 as the check."""
@@ -390,7 +481,9 @@ def main():
         return hop_profile(args.hop_profile)
     if args.workload != "stochastic":
         return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
-                "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd}[args.workload]()
+                "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,
+                "correlators_16x16x16x32": workload_correlators,
+                "dilution_8x8x8x16": workload_dilution}[args.workload]()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 

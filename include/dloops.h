@@ -246,6 +246,52 @@ int dl_tsm_estimate(dl_ctx *ctx, uint64_t seed, int n_lp, int n_hp, unsigned dil
                     int sink, const dl_smear *smear,
                     double *mean_out, double *var_out, double *per_noise_out);
 
+/* --- two-point functions (Sec. 3, Eqs. 1 and 3) --------------------------- */
+
+/* Momentum-projected loops.  Sec. 3 puts the momentum phases inside the
+ * operators Gamma(p); with p = 2 pi n / L for integer spatial n (momenta:
+ * host int [n_mom][3], 1 <= n_mom <= 256):
+ *   L_Gamma(p, t) = sum_{x in t} exp(-i p.x) eta_j(x)^dag Gamma phi_j(x)
+ * for the local and/or smeared sink as in dl_trace_loops.  Fields are
+ * canonical complex128 device fields (n_rhs of each).  t_of_rhs (host, n_rhs
+ * ints, or NULL) restricts pair j to one timeslice; otherwise all T
+ * timeslices are used.  Consecutive runs of `group` (1..64, dividing n_rhs)
+ * pairs are summed.  host_out: double [n_rhs/group][n_sinks][n_mom][16][T][2].
+ * The device work is a per-site spin matrix, its Fourier sum over each
+ * timeslice (FP64, fixed order) and the Gamma traces.  Errors: DL_EINVAL for
+ * bad arguments, DL_ESTATE without a gauge field for the smeared sink,
+ * DL_ENOMEM, DL_ECUDA. */
+int dl_trace_loops_mom(dl_ctx *ctx, const void *dev_eta, const void *dev_phi, int n_rhs, int sink,
+                       const dl_smear *smear, const int *momenta, int n_mom, const int *t_of_rhs, int group,
+                       double *host_out);
+
+/* Connected meson two-point function of a point source at src = {x, y, z, t}
+ * (Eq. 1 with the source sum replaced by one point):
+ *   C^{BA}(p, t) = - sum_x exp(-i p.(x - y)) Tr[S(y; x) Gamma_B S(x; y) Gamma_A],
+ * evaluated as - sum_x exp(-i p.(x - y)) Tr[g5 S(x; y)^dag g5 Gamma_B S(x; y) Gamma_A]
+ * through gamma5-hermiticity, with t measured from the source timeslice.
+ * dev_prop: the 12 solutions of M phi_j = e_{src, alpha, a} (j = 3 alpha + a),
+ * canonical complex128 [12][V][4][3] on the device (from dl_make_point_sources
+ * and dl_solve).  host_out: double [n_mom][16 A][16 B][T][2] for all source
+ * (A) and sink (B) operators of the Gamma basis.  For A = B = gamma5 (the
+ * pion) the value is -sum_x Tr[S^dag S] < 0 in this sign convention.
+ * Allocates 4 KiB per lattice site of scratch device memory (kept by the
+ * context). */
+int dl_meson_correlators(dl_ctx *ctx, const void *dev_prop, const int src[4], const int *momenta, int n_mom,
+                         double *host_out);
+
+/* Disconnected two-point function from per-noise loops (Eq. 3, read as the
+ * product of two loop traces):
+ *   D^{BA}(p, dt) = -(1 / (L^3 T)) sum_t E[L_B(p, t + dt) L_A(-p, t)],
+ * with the expectation taken over ordered pairs of distinct noise vectors so
+ * that no vector's noise is multiplied with itself.  host_loops: double
+ * [n_noise][n_mom][16][T][2] (e.g. from dl_trace_loops_mom with one group per
+ * noise vector); host_cover: unsigned char [n_noise][T], 1 where a vector's
+ * loop estimates timeslice t (time dilution), or NULL for all; the list of
+ * momenta must contain -p for every p.  host_out: double [n_mom][16 A][16 B][T][2]. */
+int dl_disconnected(dl_ctx *ctx, const double *host_loops, const unsigned char *host_cover, int n_noise,
+                    const int *momenta, int n_mom, double *host_out);
+
 /* --- contraction without allocation --------------------------------------- */
 
 /* The paper has no counterpart to this call.  It exists for callers that

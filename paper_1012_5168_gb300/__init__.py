@@ -41,7 +41,7 @@ SYMBOLS = (
     "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
     "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
-    "dl_trace_loops_noalloc", "dl_bench_fma",
+    "dl_trace_loops_noalloc", "dl_bench_fma", "dl_trace_loops_mom", "dl_meson_correlators", "dl_disconnected",
 )
 
 
@@ -110,6 +110,9 @@ def lib() -> ctypes.CDLL:
         "dl_tune_hop": (i, [vp, i, i, i, i, i, P(i), P(i), P(i), P(d)]),
         "dl_trace_loops_noalloc": (i, [vp, vp, i, P(i), i, i, vp, vp]),
         "dl_bench_fma": (i, [i, vp, P(d), P(d)]),
+        "dl_trace_loops_mom": (i, [vp, vp, vp, i, i, P(Smear), P(i), i, P(i), i, vp]),
+        "dl_meson_correlators": (i, [vp, vp, P(i), P(i), i, vp]),
+        "dl_disconnected": (i, [vp, vp, vp, i, P(i), i, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -344,6 +347,56 @@ class Context:
         _check(lib().dl_trace_loops(self._h, ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()), n,
                                     sink, ctypes.byref(sm) if sm is not None else None, lo, hi, tarr, group,
                                     out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def trace_loops_mom(self, eta, phi, momenta, sink: int = SINK_LOCAL, smear=None, t_of_rhs=None,
+                        group: int = 1):
+        """Momentum-projected loops sum_{x in t} exp(-i p.x) eta^dag Gamma phi:
+        complex array [n/group][n_sinks][n_mom][16][T]; momenta: integer triples n (p = 2 pi n / L)."""
+        n = self._field(eta, "eta")
+        if self._field(phi, "phi") != n:
+            raise ValueError("eta and phi hold different numbers of fields")
+        T = self.dims[3]
+        mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+        n_sinks = (1 if sink & SINK_LOCAL else 0) + (1 if sink & SINK_SMEARED else 0)
+        out = np.zeros((n // group, n_sinks, len(mom), 16, T), dtype=np.complex128)
+        sm = Smear(*smear) if smear is not None else None
+        tarr = (ctypes.c_int * n)(*[int(t) for t in t_of_rhs]) if t_of_rhs is not None else None
+        _check(lib().dl_trace_loops_mom(self._h, ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                                        n, sink, ctypes.byref(sm) if sm is not None else None,
+                                        mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(mom), tarr, group,
+                                        out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def meson_correlators(self, prop, src, momenta=((0, 0, 0),)):
+        """Connected C^{BA}(p, t) of a point source: complex array [n_mom][16 A][16 B][T].
+        prop: the 12 canonical solutions for the source (column 3 alpha + a)."""
+        if self._field(prop, "prop") != 12:
+            raise ValueError("prop must hold the 12 point-source solutions")
+        T = self.dims[3]
+        mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+        out = np.zeros((len(mom), 16, 16, T), dtype=np.complex128)
+        _check(lib().dl_meson_correlators(self._h, ctypes.c_void_p(prop.data_ptr()), (ctypes.c_int * 4)(*src),
+                                          mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(mom),
+                                          out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def disconnected(self, loops, momenta, cover=None):
+        """D^{BA}(p, dt) from per-noise loops [n_noise][n_mom][16][T] (complex), over distinct noise
+        pairs; cover: optional bool [n_noise][T].  Returns complex [n_mom][16 A][16 B][T]."""
+        T = self.dims[3]
+        L = np.ascontiguousarray(np.asarray(loops, dtype=np.complex128))
+        mom = np.ascontiguousarray(np.asarray(momenta, dtype=np.int32).reshape(-1, 3))
+        if L.shape[1:] != (len(mom), 16, T):
+            raise ValueError("loops must be [n_noise][n_mom][16][T]")
+        cv = None
+        if cover is not None:
+            cv = np.ascontiguousarray(np.asarray(cover, dtype=np.uint8))
+        out = np.zeros((len(mom), 16, 16, T), dtype=np.complex128)
+        _check(lib().dl_disconnected(self._h, L.ctypes.data_as(ctypes.c_void_p),
+                                     cv.ctypes.data_as(ctypes.c_void_p) if cv is not None else None, L.shape[0],
+                                     mom.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(mom),
+                                     out.ctypes.data_as(ctypes.c_void_p)))
         return out
 
     def exact_loops(self, src_first: int, n_src: int, params: Params | None = None, sink: int = SINK_LOCAL,

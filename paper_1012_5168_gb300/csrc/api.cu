@@ -19,6 +19,7 @@
 #include "dloops.h"
 #include "fields.cuh"
 #include "launch.h"
+#include "momentum.cuh"
 
 using namespace dl;
 
@@ -107,6 +108,12 @@ struct dl_ctx {
     double2 *d_w = nullptr;      // gamma weights / spin matrices
     size_t w_cap = 0;
     int *d_tcol = nullptr;       // per-column timeslice of the current batch (64 ints)
+    // momentum projection and correlators (grown on demand)
+    struct Scratch {
+        void *p = nullptr;
+        size_t cap = 0;
+    };
+    Scratch s_phase, s_site, s_msum, s_mloops, s_mgroup, s_mom, s_cover, s_out;
 
     int *h_count = nullptr;  // pinned, mapped
     int *d_count = nullptr;
@@ -616,6 +623,9 @@ extern "C" int dl_destroy(dl_ctx *c) {
                     c->d_tcol,     c->d_acc2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (dl_ctx::Scratch *sc : {&c->s_phase, &c->s_site, &c->s_msum, &c->s_mloops, &c->s_mgroup, &c->s_mom,
+                                &c->s_cover, &c->s_out})
+        if (sc->p) cudaFree(sc->p);
     if (c->h_count) cudaFreeHost(c->h_count);
     if (c->h_err) cudaFreeHost(c->h_err);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1337,10 +1347,51 @@ static int contract_eo(dl_ctx *c, const double *eta, const double *phi, int n, i
     return DL_OK;
 }
 
+// Momentum-projected contraction (momentum.cuh): site spin matrices, their
+// Fourier sums against the phase table, Gamma traces into dst[j][q][16][T].
+struct MomSpec {
+    int n_mom;
+    const double2 *phase;  // [n_mom][V3]
+    double2 *site;         // [N][nt][V3][16]
+    double2 *msum;         // [N][nt][n_mom][16]
+    double2 *dst;          // [sink slot][N][n_mom][16][T]
+};
+
+static int contract_mom_eo(dl_ctx *c, const double *eta, const double *phi, int n, int N, int t_lo, int t_hi,
+                           const MomSpec &m, double2 *dst, const int *tcol) {
+    const int T = c->dims[3];
+    const int V3 = c->dims[0] * c->dims[1] * c->dims[2];
+    const int nt = tcol ? 1 : t_hi - t_lo;
+    SiteSpinArgs A;
+    A.eta = eta;
+    A.phi = phi;
+    A.coords = c->d_coords;
+    A.g = c->g;
+    A.N = N;
+    A.n = n;
+    A.t_lo = tcol ? 0 : t_lo;
+    A.nt = nt;
+    A.tcol = tcol;
+    A.out = m.site;
+    Launch l = make_launch(c, (long)nt * 2 * c->g.V3h * n, 128, 0, 8);
+    site_spin_kernel<<<l.grid, l.block, 0, c->cur>>>(A);
+    fourier_kernel<<<dim3(n * nt, (m.n_mom * 16 + 255) / 256), 256, 0, c->cur>>>(m.site, m.phase, V3, 16, m.n_mom,
+                                                                                 m.msum);
+    const int cnt = n * m.n_mom * 16 * T;
+    zero_kernel<<<std::max(1, (cnt + 255) / 256), 256, 0, c->cur>>>(dst, cnt);
+    const int tot = n * nt * m.n_mom * 16;
+    mom_gamma_kernel<<<std::max(1, (tot + 255) / 256), 256, 0, c->cur>>>(m.msum, c->d_gammas, n, nt, m.n_mom, T,
+                                                                         A.t_lo, tcol, dst);
+    c->kernel_launches += 4;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
 // Loops of the EO pair (eta in *eta_buf, phi in *phi_buf) for the requested
-// sinks into c->d_loops[j][sink][16][T]; smearing overwrites the buffers.
+// sinks into c->d_loops[j][sink][16][T] (or, with a MomSpec, into
+// mom->dst[sink][j][q][16][T]); smearing overwrites the buffers.
 static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, int sink, const dl_smear *sm, int t_lo,
-                    int t_hi, int n_sinks, const int *tcol = nullptr) {
+                    int t_hi, int n_sinks, const int *tcol = nullptr, const MomSpec *mom = nullptr) {
     const int T = c->dims[3];
     const int cb0 = t_lo * c->g.V3h, cb1 = t_hi * c->g.V3h;
     const int per = 16 * T;
@@ -1356,7 +1407,10 @@ static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, i
             TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, n, *sm, s0, s1, tcol));
         }
         // contract into the slot `slot` region of d_loops viewed as [sink][n][16][T]
-        TRY(contract_eo(c, e, f, n, N, t_lo, t_hi, c->d_loops + (size_t)slot * N * per, tcol));
+        if (mom)
+            TRY(contract_mom_eo(c, e, f, n, N, t_lo, t_hi, *mom, mom->dst + (size_t)slot * N * mom->n_mom * per, tcol));
+        else
+            TRY(contract_eo(c, e, f, n, N, t_lo, t_hi, c->d_loops + (size_t)slot * N * per, tcol));
         ++slot;
     }
     (void)n_sinks;
@@ -1456,6 +1510,162 @@ extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n
             }
         }
     }
+    TRY(sync(c));
+    return DL_OK;
+}
+
+static int ensure_scratch(dl_ctx::Scratch &sc, size_t bytes) {
+    if (sc.cap >= bytes) return DL_OK;
+    if (sc.p) cudaFree(sc.p);
+    sc.p = nullptr;
+    sc.cap = 0;
+    if (cudaMalloc(&sc.p, bytes) != cudaSuccess) return fail(DL_ENOMEM, "cudaMalloc (correlator scratch)");
+    sc.cap = bytes;
+    return DL_OK;
+}
+
+// Upload n_mom momenta and build the phase table exp(-i p.(x - o)) on the device.
+static int build_phases(dl_ctx *c, const int *momenta, int n_mom, int ox, int oy, int oz) {
+    const int V3 = c->dims[0] * c->dims[1] * c->dims[2];
+    TRY(ensure_scratch(c->s_mom, sizeof(int) * 3 * n_mom));
+    TRY(ensure_scratch(c->s_phase, sizeof(double2) * (size_t)n_mom * V3));
+    CK(cudaMemcpyAsync(c->s_mom.p, momenta, sizeof(int) * 3 * n_mom, cudaMemcpyHostToDevice, c->stream));
+    const int tot = n_mom * V3;
+    phase_table_kernel<<<std::max(1, std::min((tot + 255) / 256, 8 * c->num_sms)), 256, 0, c->stream>>>(
+        (double2 *)c->s_phase.p, (const int *)c->s_mom.p, n_mom, c->g, ox, oy, oz);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    return DL_OK;
+}
+
+extern "C" int dl_trace_loops_mom(dl_ctx *c, const void *eta, const void *phi, int n_rhs, int sink,
+                                  const dl_smear *sm, const int *momenta, int n_mom, const int *t_of_rhs, int group,
+                                  double *host_out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (!(sink & (DL_SINK_LOCAL | DL_SINK_SMEARED)) || (sink & ~3)) return fail(DL_EINVAL, "bad sink mask");
+    if ((sink & DL_SINK_SMEARED) && !sm) return fail(DL_EINVAL, "smeared sink needs smearing parameters");
+    if ((sink & DL_SINK_SMEARED) && !c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (sm && (sm->n_iter < 0 || !std::isfinite(sm->alpha))) return fail(DL_EINVAL, "bad smearing parameters");
+    if (!momenta || n_mom < 1 || n_mom > 256) return fail(DL_EINVAL, "need 1..256 momenta");
+    if (!host_out) return fail(DL_EINVAL, "null output");
+    if (group < 1 || group > 64 || (n_rhs > 0 && n_rhs % group)) return fail(DL_EINVAL, "group must be 1..64 and divide n_rhs");
+    const int T = c->dims[3];
+    if (t_of_rhs)
+        for (int j = 0; j < n_rhs; ++j)
+            if (t_of_rhs[j] < 0 || t_of_rhs[j] >= T) return fail(DL_EINVAL, "t_of_rhs entry outside the lattice");
+    if (n_rhs == 0) return DL_OK;
+    if (!eta || !phi) return fail(DL_EINVAL, "null field pointer");
+    const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
+    const int per = n_mom * 16 * T;
+    const int V3 = c->dims[0] * c->dims[1] * c->dims[2];
+    const int N = std::min(64, pow2_at_least(n_rhs));
+    const int per_batch = (N / group) * group;
+    const int nt = t_of_rhs ? 1 : T;
+    TRY(ensure_ws(c, N));
+    TRY(build_phases(c, momenta, n_mom, 0, 0, 0));
+    TRY(ensure_scratch(c->s_site, sizeof(double2) * (size_t)N * nt * V3 * 16));
+    TRY(ensure_scratch(c->s_msum, sizeof(double2) * (size_t)N * nt * n_mom * 16));
+    TRY(ensure_scratch(c->s_mloops, sizeof(double2) * (size_t)n_sinks * N * per));
+    TRY(ensure_scratch(c->s_mgroup, sizeof(double2) * (size_t)N * n_sinks * per));
+    MomSpec m;
+    m.n_mom = n_mom;
+    m.phase = (const double2 *)c->s_phase.p;
+    m.site = (double2 *)c->s_site.p;
+    m.msum = (double2 *)c->s_msum.p;
+    m.dst = (double2 *)c->s_mloops.p;
+    const size_t field = (size_t)c->V * 24;
+    const int cb0 = 0, cb1 = t_of_rhs ? c->g.V3h : (int)c->Vh;
+    c->cur = c->stream;
+    int g_done = 0;
+    for (int j0 = 0; j0 < n_rhs; j0 += per_batch) {
+        const int n = std::min(per_batch, n_rhs - j0);
+        const int *tcol = nullptr;
+        if (t_of_rhs) {
+            CK(cudaMemcpyAsync(c->d_tcol, t_of_rhs + j0, n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+            tcol = c->d_tcol;
+        }
+        TRY(canon_to_eo(c, (const double *)eta + j0 * field, c->b64, n, N, 0, cb0, cb1, tcol));
+        TRY(canon_to_eo(c, (const double *)phi + j0 * field, c->x64, n, N, 0, cb0, cb1, tcol));
+        TRY(trace_eo(c, c->b64, c->x64, n, N, sink, sm, 0, T, n_sinks, tcol, &m));
+        const int ng = n / group;
+        group_sum_kernel<<<std::max(1, (ng * n_sinks * per + 255) / 256), 256, 0, c->stream>>>(
+            m.dst, n, N, group, n_sinks, per, (double2 *)c->s_mgroup.p);
+        c->kernel_launches++;
+        CK(cudaMemcpyAsync(host_out + (size_t)g_done * n_sinks * per * 2, c->s_mgroup.p,
+                           sizeof(double2) * (size_t)ng * n_sinks * per, cudaMemcpyDeviceToHost, c->stream));
+        TRY(sync(c));
+        g_done += ng;
+    }
+    return DL_OK;
+}
+
+extern "C" int dl_meson_correlators(dl_ctx *c, const void *prop, const int src[4], const int *momenta, int n_mom,
+                                    double *host_out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!prop || !src || !momenta || !host_out) return fail(DL_EINVAL, "null pointer");
+    if (n_mom < 1 || n_mom > 256) return fail(DL_EINVAL, "need 1..256 momenta");
+    for (int mu = 0; mu < 4; ++mu)
+        if (src[mu] < 0 || src[mu] >= c->dims[mu]) return fail(DL_EINVAL, "source outside the lattice");
+    const int T = c->dims[3];
+    const int V3 = c->dims[0] * c->dims[1] * c->dims[2];
+    c->cur = c->stream;
+    TRY(build_phases(c, momenta, n_mom, src[0], src[1], src[2]));
+    TRY(ensure_scratch(c->s_site, sizeof(double2) * (size_t)c->V * 256));
+    TRY(ensure_scratch(c->s_msum, sizeof(double2) * (size_t)T * n_mom * 256));
+    TRY(ensure_scratch(c->s_out, sizeof(double2) * (size_t)n_mom * 256 * T));
+    Launch l = make_launch(c, c->V * 16, 128, 0, 8);
+    meson_site_kernel<<<l.grid, l.block, 0, c->stream>>>((const double *)prop, c->V, (double2 *)c->s_site.p);
+    fourier_kernel<<<dim3(T, n_mom), 256, 0, c->stream>>>((const double2 *)c->s_site.p,
+                                                          (const double2 *)c->s_phase.p, V3, 256, n_mom,
+                                                          (double2 *)c->s_msum.p);
+    const int tot = n_mom * 256 * T;
+    meson_gamma_kernel<<<std::max(1, std::min((tot + 255) / 256, 8 * c->num_sms)), 256, 0, c->stream>>>(
+        (const double2 *)c->s_msum.p, c->d_gammas, T, n_mom, src[3], (double2 *)c->s_out.p);
+    c->kernel_launches += 3;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, c->s_out.p, sizeof(double2) * (size_t)tot, cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync(c));
+    return DL_OK;
+}
+
+extern "C" int dl_disconnected(dl_ctx *c, const double *host_loops, const unsigned char *host_cover, int n_noise,
+                               const int *momenta, int n_mom, double *host_out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!host_loops || !momenta || !host_out) return fail(DL_EINVAL, "null pointer");
+    if (n_noise < 2) return fail(DL_EINVAL, "need at least two noise vectors");
+    if (n_mom < 1 || n_mom > 256) return fail(DL_EINVAL, "need 1..256 momenta");
+    std::vector<int> minus(n_mom, -1);
+    for (int q = 0; q < n_mom; ++q)
+        for (int r = 0; r < n_mom; ++r)
+            if (momenta[3 * r] == -momenta[3 * q] && momenta[3 * r + 1] == -momenta[3 * q + 1] &&
+                momenta[3 * r + 2] == -momenta[3 * q + 2]) {
+                minus[q] = r;
+                break;
+            }
+    for (int q = 0; q < n_mom; ++q)
+        if (minus[q] < 0) return fail(DL_EINVAL, "the momentum list must contain -p for every p");
+    const int T = c->dims[3];
+    const int V3 = c->dims[0] * c->dims[1] * c->dims[2];
+    const size_t nl = (size_t)n_noise * n_mom * 16 * T;
+    c->cur = c->stream;
+    TRY(ensure_scratch(c->s_mloops, sizeof(double2) * nl));
+    TRY(ensure_scratch(c->s_cover, (size_t)n_noise * T));
+    TRY(ensure_scratch(c->s_mom, sizeof(int) * n_mom));
+    TRY(ensure_scratch(c->s_out, sizeof(double2) * (size_t)n_mom * 256 * T));
+    CK(cudaMemcpyAsync(c->s_mloops.p, host_loops, sizeof(double2) * nl, cudaMemcpyHostToDevice, c->stream));
+    if (host_cover)
+        CK(cudaMemcpyAsync(c->s_cover.p, host_cover, (size_t)n_noise * T, cudaMemcpyHostToDevice, c->stream));
+    else
+        CK(cudaMemsetAsync(c->s_cover.p, 1, (size_t)n_noise * T, c->stream));
+    CK(cudaMemcpyAsync(c->s_mom.p, minus.data(), sizeof(int) * n_mom, cudaMemcpyHostToDevice, c->stream));
+    const int tot = n_mom * 256 * T;
+    disconnected_kernel<<<std::max(1, std::min((tot + 255) / 256, 8 * c->num_sms)), 256, 0, c->stream>>>(
+        (const double2 *)c->s_mloops.p, (const unsigned char *)c->s_cover.p, (const int *)c->s_mom.p, n_noise, n_mom,
+        T, 1.0 / ((double)V3 * T), (double2 *)c->s_out.p);
+    c->kernel_launches++;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, c->s_out.p, sizeof(double2) * (size_t)tot, cudaMemcpyDeviceToHost, c->stream));
     TRY(sync(c));
     return DL_OK;
 }
