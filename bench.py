@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="stochastic",
                     choices=["stochastic", "exact_4x4x4x4", "single_rhs_16x16x16x32", "tsm_8x8x8x16",
-                             "autograd", "correlators_16x16x16x32", "dilution_8x8x8x16"],
+                             "autograd", "correlators_16x16x16x32", "dilution_8x8x8x16",
+                             "batch_scan_16x16x16x32"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--hop-profile", metavar="PREC:N[:KIND[:R:BLOCK]]", default=None,
@@ -272,24 +273,80 @@ def workload_exact():
     print(json.dumps(out), flush=True)
 
 
+def _hop_rate(tim, kinds):
+    """(GB/s, ms per launch) of the hop launches of the given timing kinds."""
+    ms = sum(tim["hop_ms"][k] for k in kinds)
+    by = sum(tim["hop_bytes"][k] for k in kinds)
+    n = sum(tim["hop_launches"][k] for k in kinds)
+    return (by / (ms / 1e3) / 1e9 if ms > 0 else 0.0), (ms / n if n else 0.0)
+
+
 def workload_single_rhs():
-    """One Z2 source on 16^3 x 32 to 1e-10: plain FP64 vs FP32- and BF16-inner defect correction."""
+    """One right-hand side at a time on 16^3 x 32 to 1e-10: a point source and 8 Z2 sources (seeds
+    1-8), plain FP64 vs FP32- and BF16-inner defect correction, at kappa 0.140 (eps 0.45) and at
+    kappa 0.157 (eps 0.60); iterations, outer cycles and the hop bandwidth per precision."""
     import torch
     import paper_1012_5168_gb300 as dl
+    peak, _ = read_peaks()
+    out = {"workload": "single_rhs_16x16x16x32", "tol": 1e-10, "hbm_peak_gbs": peak, "lattices": {}}
+    for name in ("wilson_16x16x16x32", "wilson_16x16x16x32_k157"):
+        ctx, U, w = _ctx(dl, name)
+        srcs = [ctx.make_point_sources(0, 1)] + [ctx.make_sources(s, 0, 1, 0) for s in range(1, 9)]
+        res = {"kappa": w["kappa"], "eps": w["eps"]}
+        for pname, prec in (("f64", dl.PREC_F64), ("f32", dl.PREC_F32), ("bf16", dl.PREC_BF16)):
+            p = dl.Params(tol=w["tol"], precision=prec, batch=1)
+            ctx.solve(srcs[1], p)  # tune and warm up
+            ctx.set_timing(True)
+            ctx.get_timing(reset=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = [ctx.solve(b, p)[1][0] for b in srcs]
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / len(srcs)
+            tim = ctx.get_timing(reset=True)
+            ctx.set_timing(False)
+            gbs, ms = _hop_rate(tim, (2, 3) if prec == dl.PREC_F64 else (0, 1))
+            res[pname] = {"ms_per_solve": round(dt * 1e3, 2), "solves_per_s": round(1 / dt, 2),
+                          "iters": [s["iters"] for s in st], "outer": [s["outer"] for s in st],
+                          "max_true_residual": max(s["true_residual"] for s in st),
+                          "inner_hop_gbs": round(gbs, 1), "inner_hop_frac_of_peak": round(gbs / peak, 3),
+                          "inner_hop_ms": round(ms, 4)}
+        out["lattices"][name] = res
+        ctx.close()
+    print(json.dumps(out), flush=True)
+
+
+def workload_batch_scan():
+    """Stochastic-loop solves on 16^3 x 32 (4 noise vectors x 24 diluted sources = 96 right-hand sides,
+    FP32 inner to 1e-10) at batch widths N = 16, 32, 64, with and without CUDA graphs; solves/s and
+    the bandwidth of the inner hops at each N."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    peak, _ = read_peaks()
     ctx, U, w = _ctx(dl, "wilson_16x16x16x32")
-    eta = ctx.make_sources(1, 0, 4, 0)
-    out = {"workload": "single_rhs_16x16x16x32", "tol": w["tol"]}
-    for name, prec in (("f64", dl.PREC_F64), ("f32", dl.PREC_F32), ("bf16", dl.PREC_BF16)):
-        p = dl.Params(tol=w["tol"], precision=prec, batch=1)
-        ctx.solve(eta[:1], p)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, st = ctx.solve(eta[1:4], p)
-        torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / 3
-        out[name] = {"ms_per_solve": round(dt * 1e3, 2), "solves_per_s": round(1 / dt, 2),
-                     "iters": [s["iters"] for s in st], "outer": [s["outer"] for s in st],
-                     "true_residual": max(s["true_residual"] for s in st)}
+    dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_EVENODD | dl.DIL_TIME
+    eta = ctx.make_sources(seed=3, noise_first=0, n_noise=4, dilution=dil, t0=-1)
+    out = {"workload": "batch_scan_16x16x16x32", "rhs": int(eta.shape[0]), "hbm_peak_gbs": peak, "runs": []}
+    for N in (16, 32, 64):
+        for graph in (1, 0):
+            p = dl.Params(tol=w["tol"], precision=dl.PREC_F32, batch=N, use_graph=graph)
+            ctx.solve(eta[:N], p)  # tune, capture graphs
+            ctx.set_timing(True)
+            ctx.get_timing(reset=True)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = ctx.solve(eta, p)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            tim = ctx.get_timing(reset=True)
+            ctx.set_timing(False)
+            plain, ms_p = _hop_rate(tim, (0,))
+            fused, ms_f = _hop_rate(tim, (1,))
+            out["runs"].append({"batch": N, "graph": bool(graph), "solves_per_s": round(eta.shape[0] / dt, 1),
+                                "mean_iters": round(sum(s["iters"] for s in st) / len(st), 1),
+                                "plain_hop_gbs": round(plain, 1), "fused_hop_gbs": round(fused, 1),
+                                "fused_hop_frac_of_peak": round(fused / peak, 3),
+                                "kernel_launches": tim["kernel_launches"]})
     print(json.dumps(out), flush=True)
 
 
@@ -482,7 +539,7 @@ def main():
         return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
                 "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,
                 "correlators_16x16x16x32": workload_correlators,
-                "dilution_8x8x8x16": workload_dilution}[args.workload]()
+                "dilution_8x8x8x16": workload_dilution, "batch_scan_16x16x16x32": workload_batch_scan}[args.workload]()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 

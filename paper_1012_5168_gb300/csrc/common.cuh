@@ -103,7 +103,20 @@ __device__ __forceinline__ dfloat operator+(dfloat a, dfloat b) { return df_add(
 __device__ __forceinline__ dfloat operator-(dfloat a, dfloat b) { return df_add(a, -b); }
 __device__ __forceinline__ dfloat operator*(dfloat a, dfloat b) { return df_mul(a, b); }
 __device__ __forceinline__ dfloat &operator+=(dfloat &a, dfloat b) { return a = df_add(a, b); }
-__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return df_add(df_mul(a, b), c); }
+// a * b + c with one renormalisation: the exact product's error terms and the
+// two-sum error of p + c.hi are gathered into one low word.
+__device__ __forceinline__ dfloat df_fma(dfloat a, dfloat b, dfloat c) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    const float s = p + c.hi;
+    const float bb = s - p;
+    e += ((p - (s - bb)) + (c.hi - bb)) + c.lo;
+    const float h = s + e;
+    return dfloat(h, e - (h - s));
+}
+__device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return df_fma(a, b, c); }
 // double -> float-float with FP64 arithmetic (exact for normal floats).
 __device__ __forceinline__ dfloat df_from_double(double x) {
     const float h = (float)x;

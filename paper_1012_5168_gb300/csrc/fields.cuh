@@ -225,12 +225,11 @@ struct SmearArgs {
 
 static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
     const int nsite = A.cb1 - A.cb0;
-    const int total = 2 * nsite * A.N;
+    const int total = 2 * nsite * A.n;  // only the columns in use
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int j = idx % A.N;
-        if (j >= A.n) continue;
-        const int sp = idx / A.N;
+        const int j = idx % A.n;
+        const int sp = idx / A.n;
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
@@ -292,8 +291,10 @@ struct ffc {
 template <bool DAG>
 __device__ __forceinline__ void ffc_mac(ffc &acc, ffc a, ffc b) {
     const ff ai = DAG ? -a.im : a.im;
-    acc.re = df_add(acc.re, df_add(df_mul(a.re, b.re), -df_mul(ai, b.im)));
-    acc.im = df_add(acc.im, df_add(df_mul(a.re, b.im), df_mul(ai, b.re)));
+    acc.re = df_fma(a.re, b.re, acc.re);
+    acc.re = df_fma(-ai, b.im, acc.re);
+    acc.im = df_fma(a.re, b.im, acc.im);
+    acc.im = df_fma(ai, b.re, acc.im);
 }
 __device__ __forceinline__ ffc ld_ffc(const double *p) {
     const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
@@ -344,13 +345,12 @@ static __global__ void gauge_ff_kernel(const double *g64, float *out, long n_com
 // links in float-float format.
 static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const float *gauge_ff) {
     const int nsite = A.cb1 - A.cb0;
-    const int total = 2 * nsite * A.N;
+    const int total = 2 * nsite * A.n;  // only the columns in use
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
     const ff fa = df_from_double(A.a), fc = df_from_double(A.c);
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int j = idx % A.N;
-        if (j >= A.n) continue;
-        const int sp = idx / A.N;
+        const int j = idx % A.n;
+        const int sp = idx / A.n;
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
