@@ -54,6 +54,9 @@ def parse():
                              "batch_scan_16x16x16x32"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
+    ap.add_argument("--smear-profile", metavar="N", type=int, default=None,
+                    help="time the Gaussian smearing (alpha 4, 50 iterations) of N spin x colour x even-odd "
+                         "diluted fields on one timeslice of 16^3x32 alone and exit")
     ap.add_argument("--hop-profile", metavar="PREC:N[:KIND[:R:BLOCK]]", default=None,
                     help="time the Wilson hop alone on the 16^3x32 workload (f32|bf16|f64, batch N, kernel kind "
                          "0 direct / 1 prefetch / 2 staged, right-hand sides per thread, block size; default "
@@ -232,6 +235,27 @@ def hop_profile(spec: str):
         out[name] = {"ms": round(ms, 5), "GB/s": round(by / ms / 1e6, 1)}
     torch.cuda.synchronize()
     print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def smear_profile(n: int):
+    """Time the smearing of n fields on timeslice 0 (used for ncu captures); 3 repetitions."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "wilson_16x16x16x32")
+    dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_EVENODD
+    x = ctx.make_sources(seed=1, noise_first=0, n_noise=(n + 23) // 24, dilution=dil)[:n].contiguous()
+    reps = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.apply_smear(x, 4.0, 50, t_range=(0, 1))
+        torch.cuda.synchronize()
+        reps.append((time.perf_counter() - t0) * 1e3)
+    # per site and field and iteration: 6 directions x 4 spins x 9 complex multiply-adds (8 flops)
+    flops = 2 * (w["dims"][0] * w["dims"][1] * w["dims"][2] // 2) * n * 50 * 6 * 4 * 9 * 8
+    print(json.dumps({"fields": n, "ms": [round(r, 3) for r in reps], "ms_per_iteration": round(min(reps) / 50, 4),
+                      "fp64_equivalent_tflops": round(flops / (min(reps) / 1e3) / 1e12, 3)}), flush=True)
     ctx.close()
 
 
@@ -535,6 +559,8 @@ def main():
     rank, world, local = dist_env()
     if args.hop_profile:
         return hop_profile(args.hop_profile)
+    if args.smear_profile:
+        return smear_profile(args.smear_profile)
     if args.workload != "stochastic":
         return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
                 "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,
