@@ -223,6 +223,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.g = c->g;
     a.gauge8 = prec == P_F32 ? (const void *)c->d_gauge8_32 : (prec == P_BF16 ? (const void *)c->d_gauge8_16 : nullptr);
     a.err = c->d_err;
+    a.blocked = 0;
     int R = wide ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
@@ -244,7 +245,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
         items = (long)((cb1 - cb0 + sites - 1) / sites) * block;  // one chunk per block at a time
     }
     Launch l = make_launch(c, items, block, smem, kind == 0 ? 16 : per_sm);
-    if (kind == 0) l.num_sms = c->num_sms;  // the direct kernel runs at full residency (up to 16 blocks/SM)
+    if (kind == 0 || kind == 3) l.num_sms = c->num_sms;  // direct kernels size their grid from residency
     const bool timed = c->timing;
     TimedPair tp;
     if (timed) {
@@ -405,7 +406,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     float best = 1e30f;
     int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_kind[prec][l];
     const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 3); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 4); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
@@ -415,6 +416,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                 const int B = Bs[bi];
                 if (B % (N / R) || (force_block && B != force_block)) continue;
                 if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
+                if (pf == 3 && bi > 0) continue;  // the launcher picks the block
                 if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
                 c->hop_R[prec][l] = R;
                 c->hop_block[prec][l] = B;
@@ -1174,9 +1176,18 @@ extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return 
 
 // Smear the EO fields at *buf (full field, width N) over cb range; returns the
 // buffer holding the result (ping-pong with `spare`).
+// Smear *buf (and, if buf2 is set, *buf2 in the same launches) in place over the cb
+// range; spare / spare2 are scratch fields of the same shape.  On return *buf
+// (*buf2) points at whichever of the pair holds the result.
 static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const dl_smear &s, int cb0, int cb1,
-                    const int *tcol = nullptr) {
+                    const int *tcol = nullptr, double **buf2 = nullptr, double *spare2 = nullptr) {
+    if (buf2 && c->smear_fp64) {  // the FP64 kernel smears one field per launch
+        TRY(smear_eo(c, buf, spare, N, n, s, cb0, cb1, tcol));
+        return smear_eo(c, buf2, spare2, N, n, s, cb0, cb1, tcol);
+    }
     SmearArgs A;
+    A.in2 = nullptr;
+    A.out2 = nullptr;
     A.n = n;
     A.tcol = tcol;
     A.gauge = c->d_gauge64;
@@ -1198,16 +1209,26 @@ static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const 
             std::swap(src, dst);
         }
     } else {
+        double *src2 = buf2 ? *buf2 : nullptr, *dst2 = spare2;
+        const int nf = buf2 ? 2 : 1;
         Launch lc = make_launch(c, 2L * (cb1 - cb0) * 12 * n, 256, 0, 8);
         ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 1, tcol, c->g.V3h);
+        if (buf2)
+            ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src2, (int)c->Vh, cb0, cb1, N, n, 1, tcol, c->g.V3h);
         for (int it = 0; it < s.n_iter; ++it) {
             A.in = src;
             A.out = dst;
-            smear_ff_kernel<<<l.grid, l.block, 0, c->cur>>>(A, c->d_gauge_ff);
+            A.in2 = src2;
+            A.out2 = dst2;
+            smear_ff_kernel<<<dim3(l.grid, nf), l.block, 0, c->cur>>>(A, c->d_gauge_ff);
             std::swap(src, dst);
+            std::swap(src2, dst2);
         }
         ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 0, tcol, c->g.V3h);
-        c->kernel_launches += s.n_iter + 2;
+        if (buf2)
+            ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src2, (int)c->Vh, cb0, cb1, N, n, 0, tcol, c->g.V3h);
+        c->kernel_launches += s.n_iter + 2 * nf;
+        if (buf2) *buf2 = src2;
     }
     CK(cudaGetLastError());
     *buf = src;
@@ -1405,8 +1426,8 @@ static int trace_eo(dl_ctx *c, double *eta_buf, double *phi_buf, int n, int N, i
         double *e = eta_buf, *f = phi_buf;
         if (flag == DL_SINK_SMEARED) {
             const int s0 = tcol ? 0 : cb0, s1 = tcol ? c->g.V3h : cb1;
-            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, n, *sm, s0, s1, tcol));
-            TRY(smear_eo(c, &f, f == c->x64 ? c->s64b : c->x64, N, n, *sm, s0, s1, tcol));
+            TRY(smear_eo(c, &e, e == c->b64 ? c->s64a : c->b64, N, n, *sm, s0, s1, tcol, &f,
+                         f == c->x64 ? c->s64b : c->x64));
         }
         // contract into the slot `slot` region of d_loops viewed as [sink][n][16][T]
         if (mom)

@@ -214,6 +214,8 @@ static __global__ void point_source_kernel(int64_t first, int n, long V, double 
 struct SmearArgs {
     const double *in;   // [2][Vh][12][N]
     double *out;
+    const double *in2;  // optional second field smeared in the same launch by blockIdx.y = 1
+    double *out2;       // (float-float kernel); null: one field
     const double *gauge;  // [2][Vh][4][9] complex128
     const uint32_t *coords;
     Geom g;
@@ -343,18 +345,20 @@ static __global__ void gauge_ff_kernel(const double *g64, float *out, long n_com
 
 // One smearing step in float-float; same contract as smear_kernel, fields and
 // links in float-float format.
-static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const float *gauge_ff) {
+static __global__ void __launch_bounds__(128, 3) smear_ff_kernel(SmearArgs A, const float *gauge_ff) {
     const int nsite = A.cb1 - A.cb0;
     const int total = 2 * nsite * A.n;  // only the columns in use
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
     const ff fa = df_from_double(A.a), fc = df_from_double(A.c);
+    const double *__restrict__ fin = blockIdx.y ? A.in2 : A.in;  // the field of this grid row
+    double *__restrict__ fout = blockIdx.y ? A.out2 : A.out;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
         const int j = idx % A.n;
         const int sp = idx / A.n;
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
-        const double *inn = A.in + (size_t)(1 - p) * half;
+        const double *inn = fin + (size_t)(1 - p) * half;
         ffc acc[12];
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k].re = acc[k].im = ff{0.f, 0.f};
@@ -385,8 +389,8 @@ static __global__ void __launch_bounds__(256) smear_ff_kernel(SmearArgs A, const
                 }
             }
         }
-        const double *y = A.in + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
-        double *o = A.out + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
+        const double *y = fin + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
+        double *o = fout + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
             const ffc q = ld_ffc(y + (size_t)k * A.N * 2);

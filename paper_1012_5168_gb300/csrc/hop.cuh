@@ -56,6 +56,7 @@ struct HopArgs {
     Geom g;
     const void *gauge8;     // [2][Vh][8][9] complex, site-major links (staged kernel)
     int *err;               // set to 1 by the staged kernel when a bounded wait runs out
+    int blocked;            // direct kernel: 0 cyclic site mapping, 1 one contiguous range per block
 };
 
 // Load the 12 components of R right-hand sides at one neighbour site and
@@ -207,7 +208,19 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
 #pragma unroll
         for (int k = 0; k < NV; ++k) red[r][k] = zero<T>();
 
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    // Cyclic mapping: consecutive blocks take consecutive sites and the grid strides
+    // over the lattice.  Blocked mapping: each (large) block walks its own contiguous
+    // range of sites, so the neighbours loaded for one step (the same and the adjacent
+    // x-rows of the other parity) are still in L1 for the next steps.
+    int idx = blockIdx.x * blockDim.x + threadIdx.x, idx_end = total, stride = gridDim.x * blockDim.x;
+    if (A.blocked) {
+        const int per = ((total + (int)gridDim.x - 1) / (int)gridDim.x + (int)blockDim.x - 1) / (int)blockDim.x *
+                        (int)blockDim.x;
+        idx = blockIdx.x * per + threadIdx.x;
+        idx_end = min(total, (int)(blockIdx.x + 1) * per);
+        stride = blockDim.x;
+    }
+    for (; idx < idx_end; idx += stride) {
         const int cb = A.cb_begin + (idx >> lgG);
         const int r0 = (idx & (G - 1)) * R;
         const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);

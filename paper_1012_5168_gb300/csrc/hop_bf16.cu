@@ -17,6 +17,28 @@ static cudaError_t go(const HopArgs &a, Launch &l, int pf) {
         hop_kernel_tma<bf16, R, MODE, RED, TMA_STAGES><<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
     }
+    if (pf == 3) {
+        constexpr int cap = HopRegCap<bf16, R, MODE, RED>::n;
+        constexpr int NV = RedCount<RED>::n;
+        const int G = a.N / R;
+        const size_t per_warp = NV ? (size_t)(G < 32 ? G : 32) * R * NV * sizeof(cx<float>) : 0;
+        static int blk = 0, res = 1, blkN = 0;  // per instantiation, for the last G seen
+        auto kern = [] {
+            if constexpr (cap > 0) return hop_kernel_cap<bf16, R, MODE, RED, cap>;
+            else return hop_kernel<bf16, R, MODE, RED>;
+        }();
+        if (blk == 0 || blkN != G) {
+            blk = widest_block(kern, G > 32 ? G : 32, per_warp, &res);
+            blkN = G;
+        }
+        HopArgs b = a;
+        b.blocked = 1;
+        l.block = blk;
+        l.smem = per_warp * (blk / 32);
+        l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (res < 16 ? res : 16);
+        kern<<<l.grid, l.block, l.smem, l.stream>>>(b);
+        return cudaGetLastError();
+    }
     if (!pf) {
         constexpr int cap = HopRegCap<bf16, R, MODE, RED>::n;
         if constexpr (cap > 0) {

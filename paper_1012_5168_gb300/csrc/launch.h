@@ -39,6 +39,27 @@ inline int resident_blocks(K kernel, int block, size_t smem) {
     cached_smem[bi][si] = smem;
     return n;
 }
+// Largest block (a multiple of `unit` threads, at most the kernel's limit) that maximises the
+// resident threads per SM of `kernel`; smem_per_warp bytes of dynamic shared
+// memory per warp.  *resident receives the blocks per SM at that size.
+template <typename K>
+inline int widest_block(K kernel, int unit, size_t smem_per_warp, int *resident) {
+    int best = unit, best_thr = 0, best_res = 1;
+    cudaFuncAttributes fa;
+    const int max_thr = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.maxThreadsPerBlock : 256;
+    for (int b = max_thr / unit * unit; b >= unit; b -= unit) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, b, smem_per_warp * (b / 32)) != cudaSuccess) continue;
+        if (n * b > best_thr) {
+            best_thr = n * b;
+            best = b;
+            best_res = n;
+        }
+    }
+    *resident = best_res < 1 ? 1 : best_res;
+    return best;
+}
+
 // Resident blocks, at most 16 per SM (the partial-sum buffers are sized for that).
 inline void clamp_grid(Launch &l, int resident) {
     if (l.num_sms > 0) {
@@ -56,7 +77,9 @@ cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, Launch &l
 cudaError_t launch_hop_dff(int R, int mode, int red, const HopArgs &a, Launch &l);
 // kind (low precision only): 0 direct loads; 1 cp.async prefetching kernel,
 // dynamic shared memory pf_stage_bytes(prec, R) * 2 * block; 2 bulk-copy
-// staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R)).
+// staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R));
+// 3 direct loads with one contiguous site range per block, the widest resident
+// block and one wave of blocks (the launcher sets block, grid and shared memory).
 cudaError_t launch_hop_f32(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 cudaError_t launch_hop_bf16(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 

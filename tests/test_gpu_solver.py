@@ -135,10 +135,10 @@ def test_solve_full_size(lib, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
 @pytest.mark.parametrize("batch", [1, 4, 16, 64])
 def test_hop_kernel_kinds(lib, prec, kind, batch):
-    """Direct, cp.async-prefetching and bulk-copy-staged hops all solve to tolerance."""
+    """Direct, cp.async-prefetching, bulk-copy-staged and blocked-mapping hops all solve to tolerance."""
     dims, kappa = (4, 4, 4, 8), 0.12
     U = synthetic.gauge_field(dims, eps=0.45, seed=8)
     c = lib.Context(dims)
@@ -157,7 +157,7 @@ def test_hop_kernel_kinds(lib, prec, kind, batch):
 
 
 def test_hop_kernel_kinds_full_size(lib):
-    """The three hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides)."""
+    """The four hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides)."""
     w = synthetic.WORKLOADS["wilson_16x16x16x32"]
     U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
     c = lib.Context(w["dims"])
@@ -165,7 +165,7 @@ def test_hop_kernel_kinds_full_size(lib):
     c.set_kappa(w["kappa"])
     eta = c.make_sources(seed=4, noise_first=0, n_noise=32, dilution=0)
     sols = []
-    for kind in (0, 1, 2):
+    for kind in (0, 1, 2, 3):
         c.tune_hop(1, 32, force_pf=kind)
         x, st = c.solve(eta, lib.Params(tol=1e-10, precision=1, batch=32))
         assert all(s["status"] == 0 and s["true_residual"] <= 1e-10 for s in st)
