@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "hop.cuh"
 #include "blas.cuh"
@@ -25,18 +27,21 @@ struct Launch {
 };
 
 // Resident blocks per SM of `kernel` at this block size and dynamic shared
-// memory (cached per kernel, block and shared-memory size).
+// memory (cached per kernel, block and shared-memory size; each entry packs
+// the shared-memory size and the count into one atomic word, so contexts used
+// from several host threads may share the cache).
 template <typename K>
 inline int resident_blocks(K kernel, int block, size_t smem) {
-    static int cached[4][1024];
-    static size_t cached_smem[4][1024];
+    static std::atomic<uint64_t> cached[4][1024];
     const int bi = block == 64 ? 0 : (block == 128 ? 1 : (block == 256 ? 2 : 3));
     const int si = (int)((smem / 256) % 1024);
-    if (cached[bi][si] > 0 && cached_smem[bi][si] == smem) return cached[bi][si];
+    const uint64_t key = ((uint64_t)smem << 16) | (uint64_t)block;
+    const uint64_t v = cached[bi][si].load(std::memory_order_relaxed);
+    if ((v >> 8) == key && (v & 0xff) > 0) return (int)(v & 0xff);
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess || n < 1) n = 1;
-    cached[bi][si] = n;
-    cached_smem[bi][si] = smem;
+    if (n > 255) n = 255;
+    cached[bi][si].store((key << 8) | (uint64_t)n, std::memory_order_relaxed);
     return n;
 }
 // Largest block (a multiple of `unit` threads, at most the kernel's limit) that maximises the
