@@ -97,7 +97,7 @@ typedef struct dl_solve_params {
                             of two for F32/BF16 >= 2); <= 0 picks 16 */
     int use_graph;       /* capture the inner iteration in CUDA graphs (1) or launch
                             directly (0) */
-    int chunk;           /* inner iterations per graph launch / convergence poll; <= 0: 8 */
+    int chunk;           /* inner iterations per graph launch / convergence poll; <= 0: 2 */
     int method;          /* DL_METHOD_*; 0 (BiCGStab) by default */
 } dl_solve_params;
 

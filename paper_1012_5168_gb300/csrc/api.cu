@@ -916,7 +916,10 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
     if (b > 64) return fail(DL_EINVAL, "batch must be <= 64");
     s->batch = pow2_at_least(b);
     s->use_graph = p->use_graph != 0;
-    s->chunk = p->chunk > 0 ? p->chunk : 8;
+    // Poll convergence every 2 iterations: on 16^3 x 32 with 32 right-hand sides this
+    // ran 4% faster than every 8 (fewer iterations past convergence) and no slower
+    // than every iteration.
+    s->chunk = p->chunk > 0 ? p->chunk : 2;
     {
         // Continuing p and rhat across cycles (a reliable update) measured slower than a
         // restart on the 16^3 x 32 workload for both inner precisions; kept as an option.

@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) inner_init_kernel(VecArgs a, const OuterS
                                                         const double *r64, S *x_, S *r_, S *rhat_, S *p_,
                                                         double2 *partials, int restart) {
     typedef typename Real<S>::type T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
     const int total = a.n_elem << lgG;
     cx<T> red[R][2];
@@ -382,7 +382,7 @@ template <typename S, int R>
 __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, const OuterState *os, const double *r64, S *x_,
                                                      S *r5_, double2 *partials) {
     typedef typename Real<S>::type T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
     const int total = a.n_elem << lgG;
     cx<T> red[R][1];
@@ -416,7 +416,7 @@ template <typename S, int R>
 __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a, const RhsState *st, S *x_, S *r5_, const S *p_,
                                                        const S *w_, double2 *partials) {
     typedef typename Real<S>::type T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
     const int total = a.n_elem << lgG;
     cx<T> red[R][1];
@@ -665,7 +665,7 @@ namespace dl {
 template <typename S, int R>
 static __global__ void __launch_bounds__(256) norm2_kernel(VecArgs a, const S *v_, double2 *partials) {
     typedef typename Real<S>::type T;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
     const int total = a.n_elem << lgG;
     cx<T> red[R][1];

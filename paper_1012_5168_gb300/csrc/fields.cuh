@@ -420,7 +420,7 @@ struct ContractArgs {
 
 template <int R>
 static __global__ void __launch_bounds__(128) contract_kernel(ContractArgs A) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int p = blockIdx.z;
     const int t = A.t_lo + blockIdx.y;
     const int G = A.N / R;

@@ -196,7 +196,7 @@ template <typename S, int R, int MODE, int RED>
 __device__ __forceinline__ void hop_body(const HopArgs &A) {
     typedef typename Real<S>::type T;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int G = A.N / R;  // a power of two dividing 32 (checked by the host)
     const int lgG = __ffs(G) - 1;
     const size_t N = (size_t)A.N;
@@ -307,6 +307,8 @@ template <typename S, int R, int MODE, int RED, int CAP>
 __global__ void __maxnreg__(CAP) hop_kernel_cap(HopArgs A) {
     hop_body<S, R, MODE, RED>(A);
 }
+
+
 
 
 // ---------------------------------------------------------------------------
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(256) hop_kernel_pf(HopArgs A) {
     typedef typename Real<S>::type T;
     typedef PfLayout<S, R> L;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int nthreads = blockDim.x;
     unsigned char *stage[2] = {smem, smem + (size_t)L::STAGE * nthreads};
     const int G = A.N / R;
