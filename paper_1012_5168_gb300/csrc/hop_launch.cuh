@@ -1,0 +1,104 @@
+// Launch of one Wilson-hop instantiation for a low-precision storage type S
+// (float or bf16): the kernel kind picks the direct, prefetching, staged or
+// blocked-mapping kernel.  hop_f32.cu and hop_bf16.cu instantiate it.  The
+// one-time settings (shared-memory opt-ins, the blocked kernel's block shape)
+// are guarded so that contexts used from several host threads can launch
+// concurrently.
+#pragma once
+
+#include <mutex>
+
+#include "hop_tma.cuh"
+#include "launch.h"
+
+namespace dl {
+
+// Raise a kernel's dynamic shared-memory limit to at least `smem` (beyond the
+// default 48 KiB), once per larger request.
+template <typename K>
+inline cudaError_t opt_in_smem(K kernel, size_t smem, size_t &opted, std::mutex &m) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    std::lock_guard<std::mutex> g(m);
+    if (smem <= opted) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) opted = smem;
+    return e;
+}
+
+template <typename S, int R, int MODE, int RED>
+cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
+    constexpr int cap = HopRegCap<S, R, MODE, RED>::n;
+    auto direct = [] {
+        if constexpr (cap > 0) return hop_kernel_cap<S, R, MODE, RED, cap>;
+        else return hop_kernel<S, R, MODE, RED>;
+    }();
+    if (kind == 0) {
+        clamp_grid(l, resident_blocks(direct, l.block, l.smem));
+        direct<<<l.grid, l.block, l.smem, l.stream>>>(a);
+        return cudaGetLastError();
+    }
+    if (kind == 1) {
+        static size_t opted = 0;
+        static std::mutex m;
+        const cudaError_t e = opt_in_smem(hop_kernel_pf<S, R, MODE, RED>, l.smem, opted, m);
+        if (e != cudaSuccess) return e;
+        hop_kernel_pf<S, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        return cudaGetLastError();
+    }
+    if (kind == 2) {
+        static size_t opted = 0;
+        static std::mutex m;
+        const cudaError_t e = opt_in_smem(hop_kernel_tma<S, R, MODE, RED, TMA_STAGES>, l.smem, opted, m);
+        if (e != cudaSuccess) return e;
+        hop_kernel_tma<S, R, MODE, RED, TMA_STAGES><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        return cudaGetLastError();
+    }
+    if (kind == 3) {
+        constexpr int NV = RedCount<RED>::n;
+        const int G = a.N / R;
+        const size_t per_warp = NV ? (size_t)(G < 32 ? G : 32) * R * NV * sizeof(cx<float>) : 0;
+        // block shape for the G last seen: block | resident << 16 | G << 24
+        static std::atomic<uint32_t> shape{0};
+        uint32_t sh = shape.load(std::memory_order_relaxed);
+        if (sh == 0 || (int)(sh >> 24) != G) {
+            int res = 1;
+            const int blk = widest_block(direct, G > 32 ? G : 32, per_warp, &res);
+            sh = (uint32_t)blk | ((uint32_t)(res < 16 ? res : 16) << 16) | ((uint32_t)G << 24);
+            shape.store(sh, std::memory_order_relaxed);
+        }
+        HopArgs b = a;
+        b.blocked = 1;
+        l.block = (int)(sh & 0xffff);
+        l.smem = per_warp * (l.block / 32);
+        l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (int)((sh >> 16) & 0xff);
+        direct<<<l.grid, l.block, l.smem, l.stream>>>(b);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The (R, MODE, RED) combinations the solvers use, for storage type S.
+template <typename S>
+cudaError_t launch_hop_low(int R, int mode, int red, int kind, const HopArgs &a, Launch &l) {
+#define DL_CASE(r, m, rd) \
+    if (R == r && mode == m && red == rd) return go_hop<S, r, m, rd>(a, l, kind);
+    DL_CASE(1, MODE_PLAIN, RED_NONE)
+    DL_CASE(1, MODE_XPAY, RED_NONE)
+    DL_CASE(1, MODE_XPAY, RED_R0DOT)
+    DL_CASE(1, MODE_XPAY, RED_BICG)
+    DL_CASE(1, MODE_XPAY, RED_NORM)
+    DL_CASE(2, MODE_PLAIN, RED_NONE)
+    DL_CASE(2, MODE_XPAY, RED_NONE)
+    DL_CASE(2, MODE_XPAY, RED_R0DOT)
+    DL_CASE(2, MODE_XPAY, RED_BICG)
+    DL_CASE(2, MODE_XPAY, RED_NORM)
+    DL_CASE(4, MODE_PLAIN, RED_NONE)
+    DL_CASE(4, MODE_XPAY, RED_NONE)
+    DL_CASE(4, MODE_XPAY, RED_R0DOT)
+    DL_CASE(4, MODE_XPAY, RED_BICG)
+    DL_CASE(4, MODE_XPAY, RED_NORM)
+#undef DL_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dl
