@@ -770,14 +770,14 @@ static int enqueue_iteration(dl_ctx *c, int prec, int N) {
                Vh, nullptr, nullptr));
     TRY(do_hop(c, prec, MODE_XPAY, RED_R0DOT, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr,
                lo_ptr(c, LRH), 0, N, -k2, 0, Vh, part, &nb));
-    scalar_alpha_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, part, nb, N);
+    scalar_alpha_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, part, nb, N);
     VecLaunch v = vec_launch(c, prec, N, 0);
     CK(launch_axpy_s(v, c->d_rhs, lo_ptr(c, LR), lo_ptr(c, LV), lo_ptr(c, LS)));
     TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
                Vh, nullptr, nullptr));
     TRY(do_hop(c, prec, MODE_XPAY, RED_BICG, lo_ptr(c, LT), lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, lo_ptr(c, LRH),
                0, N, -k2, 0, Vh, part, &nb));
-    scalar_omega_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, part, nb, N);
+    scalar_omega_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, part, nb, N);
     CK(launch_update(v, c->d_rhs, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LP), lo_ptr(c, LS), lo_ptr(c, LT),
                      lo_ptr(c, LV)));
     c->kernel_launches += 4;
@@ -796,7 +796,7 @@ static int enqueue_iteration_cg(dl_ctx *c, int prec, int N) {
                Vh, nullptr, nullptr));
     TRY(do_hop(c, prec, MODE_XPAY, RED_NORM, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, 0, N,
                -k2, 0, Vh, pa, &nb));
-    cg_alpha_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, pa, nb, N);
+    cg_alpha_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, pa, nb, N);
     VecLaunch v = vec_launch(c, prec, N, prec == P_F64 ? 16 : 8);
     CK(launch_cg_update(v, c->d_rhs, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LP), lo_ptr(c, LV), pb));
     const int nbv = v.l.grid;
@@ -804,7 +804,7 @@ static int enqueue_iteration_cg(dl_ctx *c, int prec, int N) {
                Vh, nullptr, nullptr));
     TRY(do_hop(c, prec, MODE_XPAY, RED_NORM, lo_ptr(c, LRH), lo_ptr(c, LTMP), lo_ptr(c, LR), nullptr, nullptr, 0, N,
                -k2, 0, Vh, pa, &nb));
-    cg_beta_kernel<<<N, 32, 0, c->cur>>>(c->d_rhs, pb, nbv, pa, nb, N);
+    cg_beta_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, pb, nbv, pa, nb, N);
     CK(launch_cg_p(vec_launch(c, prec, N, 0), c->d_rhs, lo_ptr(c, LRH), lo_ptr(c, LP), 0));
     c->kernel_launches += 4;
     CK(cudaGetLastError());
@@ -961,12 +961,12 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         nb = v.l.grid;
         CK(launch_norm2(v, bo, pb));
         nb2 = v.l.grid;
-        full_norm_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 0);
+        full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 0);
         c->kernel_launches += 3;
     }
     // bhat = b_e + kappa D_eo b_o, |bhat|^2
     TRY(do_hop(c, op, MODE_XPAY, RED_NORM, c->bh64, bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
-    outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 0, P.tol, P.max_outer, P.max_iter);
+    outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 0, P.tol, P.max_outer, P.max_iter);
     c->kernel_launches++;
     CK(cudaMemcpyAsync(c->r64, c->bh64, half * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(xe, 0, half * sizeof(double), c->stream));
@@ -985,7 +985,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
                        1.0, 0, Vh, nullptr, nullptr));
             TRY(do_hop(c, prec, MODE_XPAY, RED_NORM, lo_ptr(c, LRH), lo_ptr(c, LTMP), lo_ptr(c, LR), nullptr, nullptr,
                        0, N, -k2, 0, Vh, pa, &nb));
-            cg_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pb, v.l.grid, pa, nb, N, P.delta, target,
+            cg_start_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_rhs, c->d_outer, pb, v.l.grid, pa, nb, N, P.delta, target,
                                                      P.max_iter, P.fixed_iters > 0 ? 1 : 0);
             CK(launch_cg_p(vec_launch(c, prec, N, 0), c->d_rhs, lo_ptr(c, LRH), lo_ptr(c, LP), 1));
             c->kernel_launches += 3;
@@ -993,7 +993,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
             VecLaunch v = vec_launch(c, prec, N, 2 * (prec == P_F64 ? 16 : 8));
             CK(launch_inner_init(v, c->d_outer, c->d_rhs, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH),
                                  lo_ptr(c, LP), pa, (cycle == 0 || P.restart) ? 1 : 0));
-            inner_start_kernel<<<N, 32, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
+            inner_start_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
                                                         P.max_iter, P.fixed_iters > 0 ? 1 : 0);
             c->kernel_launches += 2;
         }
@@ -1009,7 +1009,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         CK(launch_accumulate(vec_launch(c, prec, N, 0), c->d_outer, lo_ptr(c, LX), xe));
         c->kernel_launches++;
         if (P.fixed_iters > 0) {
-            outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, 0, N, 2, P.tol, P.max_outer,
+            outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, 0, N, 2, P.tol, P.max_outer,
                                                          P.max_iter);
             c->kernel_launches++;
             break;
@@ -1018,7 +1018,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         TRY(do_hop(c, op, MODE_PLAIN, RED_NONE, c->t64, xe, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh, nullptr,
                    nullptr));
         TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, c->t64, xe, c->bh64, nullptr, 0, N, -k2, 0, Vh, pa, &nb));
-        outer_update_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 1, P.tol, P.max_outer,
+        outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 1, P.tol, P.max_outer,
                                                      P.max_iter);
         c->kernel_launches++;
     }
@@ -1029,7 +1029,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
     // part b_e - x_e + kappa D_eo x_o uses the reconstructed x_o, so it checks the
     // reconstruction as well as the Schur solve.
     TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
-    full_norm_kernel<<<N, 32, 0, c->stream>>>(c->d_outer, pa, nb, pb, 0, N, 1);
+    full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, 0, N, 1);
     c->kernel_launches++;
     CK(cudaGetLastError());
     host_os.resize(N);

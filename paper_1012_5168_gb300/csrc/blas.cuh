@@ -62,11 +62,14 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// Sum partials[b][rhs][k] over blocks b for one right-hand side (one warp).
-__device__ __forceinline__ double2 warp_sum_partials(const double2 *partials, int nblocks, int N, int NV,
-                                                     int rhs, int k) {
+// Sum partials[b][rhs][k] over blocks b for one right-hand side, by the whole
+// thread block (a multiple of 32 threads), in a fixed order: strided per-thread
+// sums, then warp shuffles, then the warps in index order.  Every thread gets
+// the total.
+__device__ __forceinline__ double2 sum_partials(const double2 *partials, int nblocks, int N, int NV, int rhs, int k) {
+    __shared__ double2 wsum[32];
     double re = 0.0, im = 0.0;
-    for (int b = threadIdx.x & 31; b < nblocks; b += 32) {
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
         const double2 v = partials[((size_t)b * N + rhs) * NV + k];
         re += v.x;
         im += v.y;
@@ -76,8 +79,22 @@ __device__ __forceinline__ double2 warp_sum_partials(const double2 *partials, in
         re += __shfl_xor_sync(0xffffffffu, re, off);
         im += __shfl_xor_sync(0xffffffffu, im, off);
     }
+    const int nw = blockDim.x >> 5;
+    if (nw == 1) return make_double2(re, im);
+    __syncthreads();  // an earlier call may still be reading wsum
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = make_double2(re, im);
+    __syncthreads();
+    re = 0.0;
+    im = 0.0;
+    for (int w = 0; w < nw; ++w) {
+        re += wsum[w].x;
+        im += wsum[w].y;
+    }
     return make_double2(re, im);
 }
+
+// Threads per block of the per-right-hand-side scalar kernels (grid = N blocks).
+constexpr int kScalarThreads = 256;
 
 // Relative reduction the inner phase aims for: delta, or less when less suffices
 // for the outer test |r| <= 0.5 tol min(|bhat|, |b|) (outer_update_kernel), with
@@ -89,7 +106,7 @@ __device__ __forceinline__ double inner_reduction(const OuterState &o, double de
 }
 
 // ---------------------------------------------------------------------------
-// scalar kernels: grid = N blocks of 32 threads (one warp per right-hand side)
+// scalar kernels: grid = N blocks of kScalarThreads (one block per right-hand side)
 // ---------------------------------------------------------------------------
 
 // Start an inner phase: rho = <rhat, r_l>, r2 = |r_l|^2 (from the partials of
@@ -98,8 +115,8 @@ __device__ __forceinline__ double inner_reduction(const OuterState &o, double de
 static __global__ void inner_start_kernel(RhsState *st, OuterState *os, const double2 *partials,
                                    int nblocks, int N, double delta, int max_iters, int max_total, int fixed) {
     const int r = blockIdx.x;
-    const double2 rho = warp_sum_partials(partials, nblocks, N, 2, r, 0);
-    const double2 n2 = warp_sum_partials(partials, nblocks, N, 2, r, 1);
+    const double2 rho = sum_partials(partials, nblocks, N, 2, r, 0);
+    const double2 n2 = sum_partials(partials, nblocks, N, 2, r, 1);
     if (threadIdx.x != 0) return;
     os[r].sigma = os[r].active ? sqrt(os[r].r2) : 0.0;
     RhsState s;
@@ -126,7 +143,7 @@ static __global__ void inner_start_kernel(RhsState *st, OuterState *os, const do
 // After v = Mhat p: alpha = rho / <rhat, v>.
 static __global__ void scalar_alpha_kernel(RhsState *st, const double2 *partials, int nblocks, int N) {
     const int r = blockIdx.x;
-    const double2 d = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    const double2 d = sum_partials(partials, nblocks, N, 1, r, 0);
     if (threadIdx.x != 0) return;
     RhsState &s = st[r];
     s.active = s.next_active;
@@ -146,7 +163,7 @@ static __global__ void scalar_omega_kernel(RhsState *st, const double2 *partials
     const int r = blockIdx.x;
     double2 v[5];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) v[k] = warp_sum_partials(partials, nblocks, N, 5, r, k);
+    for (int k = 0; k < 5; ++k) v[k] = sum_partials(partials, nblocks, N, 5, r, k);
     if (threadIdx.x != 0) return;
     RhsState &s = st[r];
     if (!s.active) return;
@@ -499,8 +516,8 @@ __global__ void __launch_bounds__(256) cg_p_kernel(VecArgs a, const RhsState *st
 static __global__ void cg_start_kernel(RhsState *st, OuterState *os, const double2 *pr, int nr, const double2 *pu,
                                        int nu, int N, double delta, int max_iters, int max_total, int fixed) {
     const int r = blockIdx.x;
-    const double2 n2 = warp_sum_partials(pr, nr, N, 1, r, 0);
-    const double2 zz = warp_sum_partials(pu, nu, N, 1, r, 0);
+    const double2 n2 = sum_partials(pr, nr, N, 1, r, 0);
+    const double2 zz = sum_partials(pu, nu, N, 1, r, 0);
     if (threadIdx.x != 0) return;
     os[r].sigma = os[r].active ? sqrt(os[r].r2) : 0.0;
     RhsState s;
@@ -527,7 +544,7 @@ static __global__ void cg_start_kernel(RhsState *st, OuterState *os, const doubl
 // After w = Mhat p: alpha = |z|^2 / |w|^2.
 static __global__ void cg_alpha_kernel(RhsState *st, const double2 *partials, int nblocks, int N) {
     const int r = blockIdx.x;
-    const double2 ww = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    const double2 ww = sum_partials(partials, nblocks, N, 1, r, 0);
     if (threadIdx.x != 0) return;
     RhsState &s = st[r];
     s.active = s.next_active;
@@ -545,8 +562,8 @@ static __global__ void cg_alpha_kernel(RhsState *st, const double2 *partials, in
 // After the update (pr: |r|^2) and u = Mhat g5 r (pu: |u|^2): beta, stopping test.
 static __global__ void cg_beta_kernel(RhsState *st, const double2 *pr, int nr, const double2 *pu, int nu, int N) {
     const int r = blockIdx.x;
-    const double2 n2 = warp_sum_partials(pr, nr, N, 1, r, 0);
-    const double2 zz = warp_sum_partials(pu, nu, N, 1, r, 0);
+    const double2 n2 = sum_partials(pr, nr, N, 1, r, 0);
+    const double2 zz = sum_partials(pu, nu, N, 1, r, 0);
     if (threadIdx.x != 0) return;
     RhsState &s = st[r];
     if (!s.active) return;
@@ -598,7 +615,7 @@ static __global__ void __launch_bounds__(256) accumulate_kernel(VecArgs a, const
 }
 
 // ---------------------------------------------------------------------------
-// outer (FP64) bookkeeping: grid = N blocks of 32 threads
+// outer (FP64) bookkeeping: grid = N blocks of kScalarThreads
 // ---------------------------------------------------------------------------
 // mode 0: initialise (b2 = |bhat|^2 from partials, r2 = b2, active = b2 > 0)
 // mode 1: after r = bhat - Mhat x: r2 from partials, convergence test, cycle count
@@ -606,7 +623,7 @@ static __global__ void __launch_bounds__(256) accumulate_kernel(VecArgs a, const
 static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, const double2 *partials, int nblocks,
                                     int N, int mode, double tol, int max_outer, int max_iter) {
     const int r = blockIdx.x;
-    const double2 n2 = warp_sum_partials(partials, nblocks, N, 1, r, 0);
+    const double2 n2 = sum_partials(partials, nblocks, N, 1, r, 0);
     if (threadIdx.x != 0) return;
     OuterState &o = os[r];
     if (mode == 0) {
@@ -651,8 +668,8 @@ static __global__ void outer_count_kernel(const OuterState *os, int N, int *out)
 static __global__ void full_norm_kernel(OuterState *os, const double2 *pa, int na, const double2 *pb, int nb, int N,
                                  int mode) {
     const int r = blockIdx.x;
-    const double2 a = warp_sum_partials(pa, na, N, 1, r, 0);
-    const double2 b = warp_sum_partials(pb, nb, N, 1, r, 0);
+    const double2 a = sum_partials(pa, na, N, 1, r, 0);
+    const double2 b = sum_partials(pb, nb, N, 1, r, 0);
     if (threadIdx.x != 0) return;
     if (mode == 0) os[r].full_b2 = a.x + b.x;
     else os[r].full_r2 = a.x + b.x;
