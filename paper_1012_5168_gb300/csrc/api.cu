@@ -970,6 +970,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
     c->kernel_launches++;
     CK(cudaMemcpyAsync(c->r64, c->bh64, half * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(xe, 0, half * sizeof(double), c->stream));
+    bool residual_current = false;  // c->r64 and x_o belong to the current x_e
     const int prec = P.prec;
     for (int cycle = 0; cycle < P.max_outer; ++cycle) {
         outer_count_kernel<<<1, 1, 0, c->stream>>>(c->d_outer, N, c->d_count);
@@ -1008,29 +1009,27 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         c->cur = c->stream;
         CK(launch_accumulate(vec_launch(c, prec, N, 0), c->d_outer, lo_ptr(c, LX), xe));
         c->kernel_launches++;
-        if (P.fixed_iters > 0) {
-            outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, 0, N, 2, P.tol, P.max_outer,
-                                                         P.max_iter);
-            c->kernel_launches++;
-            break;
-        }
-        // r = bhat - Mhat x, recomputed in FP64 every cycle (true residual)
-        TRY(do_hop(c, op, MODE_PLAIN, RED_NONE, c->t64, xe, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh, nullptr,
-                   nullptr));
-        TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, c->t64, xe, c->bh64, nullptr, 0, N, -k2, 0, Vh, pa, &nb));
-        outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 1, P.tol, P.max_outer,
-                                                     P.max_iter);
+        // The true residual, in FP64 every cycle, through the reconstruction
+        //   x_o = b_o + kappa D_oe x_e,   r = b_e - x_e + kappa D_eo x_o.
+        // The odd rows of b - M x vanish by construction of x_o (up to FP64
+        // rounding) and the even rows equal bhat - Mhat x_e, so r is both the
+        // Schur residual that drives the next cycle and the full-lattice residual;
+        // the final solution needs no further hop.
+        TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
+        TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
+        residual_current = true;
+        outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N,
+                                                                 P.fixed_iters > 0 ? 2 : 1, P.tol, P.max_outer,
+                                                                 P.max_iter);
+        c->kernel_launches++;
+        if (P.fixed_iters > 0) break;
+    }
+    if (!residual_current) {  // no cycle ran (every right-hand side was zero): x = (0, b_o)
+        TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
+        TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
+        full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, 0, N, 1);
         c->kernel_launches++;
     }
-    // reconstruct x_o = b_o + kappa D_oe x_e
-    TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
-    // full-lattice true residual b - M x.  Its odd part b_o - x_o + kappa D_oe x_e is
-    // zero up to FP64 rounding: x_o was just computed from the same hop.  The even
-    // part b_e - x_e + kappa D_eo x_o uses the reconstructed x_o, so it checks the
-    // reconstruction as well as the Schur solve.
-    TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
-    full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, 0, N, 1);
-    c->kernel_launches++;
     CK(cudaGetLastError());
     host_os.resize(N);
     CK(cudaMemcpyAsync(host_os.data(), c->d_outer, N * sizeof(OuterState), cudaMemcpyDeviceToHost, c->stream));

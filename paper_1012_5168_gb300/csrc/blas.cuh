@@ -618,8 +618,10 @@ static __global__ void __launch_bounds__(256) accumulate_kernel(VecArgs a, const
 // outer (FP64) bookkeeping: grid = N blocks of kScalarThreads
 // ---------------------------------------------------------------------------
 // mode 0: initialise (b2 = |bhat|^2 from partials, r2 = b2, active = b2 > 0)
-// mode 1: after r = bhat - Mhat x: r2 from partials, convergence test, cycle count
-// mode 2: after a fixed-iteration phase: cycle and iteration counts only
+// mode 1: after the true residual r (partials: |r|^2, which is also the
+//         full-lattice residual): r2, full_r2, convergence test, cycle count
+// mode 2: after a fixed-iteration phase and its residual: full_r2 and the
+//         cycle and iteration counts only
 static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, const double2 *partials, int nblocks,
                                     int N, int mode, double tol, int max_outer, int max_iter) {
     const int r = blockIdx.x;
@@ -638,6 +640,7 @@ static __global__ void outer_update_kernel(OuterState *os, const RhsState *st, c
         if (!isfinite(n2.x)) { o.status = ST_NAN; o.active = 0; }
         return;
     }
+    o.full_r2 = n2.x;  // every right-hand side: an inactive one's x is unchanged
     if (!o.active) return;
     o.outer += 1;
     o.iters += st[r].iters;
