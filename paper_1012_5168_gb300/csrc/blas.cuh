@@ -231,9 +231,9 @@ template <typename S, int R>
 static __global__ void __launch_bounds__(256) axpy_s_kernel(VecArgs a, const RhsState *st, const S *r_, const S *v_, S *s_) {
     typedef typename Real<S>::type T;
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         bool any = false;
         cx<T> al[R];
 #pragma unroll
@@ -260,9 +260,9 @@ static __global__ void __launch_bounds__(256) update_kernel(VecArgs a, const Rhs
                                                     const S *s_, const S *t_, const S *v_) {
     typedef typename Real<S>::type T;
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         bool any = false;
         bool on[R];
         cx<T> al[R], om[R], be[R];
@@ -320,12 +320,12 @@ __global__ void __launch_bounds__(256) inner_init_kernel(VecArgs a, const OuterS
     typedef typename Real<S>::type T;
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
     cx<T> red[R][2];
 #pragma unroll
     for (int k = 0; k < R; ++k) red[k][0] = red[k][1] = zero<T>();
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         const size_t off = ((size_t)e * a.N + r0) * 2;
         cx<double> src[R];
         ld_pack<double, R, true>(r64 + off, src);
@@ -401,12 +401,12 @@ __global__ void __launch_bounds__(256) cg_init_kernel(VecArgs a, const OuterStat
     typedef typename Real<S>::type T;
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
     cx<T> red[R][1];
 #pragma unroll
     for (int k = 0; k < R; ++k) red[k][0] = zero<T>();
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         const size_t off = ((size_t)e * a.N + r0) * 2;
         const double sg = g5_negates(e) ? -1.0 : 1.0;
         cx<double> src[R];
@@ -435,12 +435,12 @@ __global__ void __launch_bounds__(256) cg_update_kernel(VecArgs a, const RhsStat
     typedef typename Real<S>::type T;
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
     cx<T> red[R][1];
 #pragma unroll
     for (int k = 0; k < R; ++k) red[k][0] = zero<T>();
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         bool on[R];
         bool any = false;
         T al[R];
@@ -479,9 +479,9 @@ template <typename S, int R>
 __global__ void __launch_bounds__(256) cg_p_kernel(VecArgs a, const RhsState *st, const S *u_, S *p_, int init) {
     typedef typename Real<S>::type T;
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         bool on[R];
         bool any = false;
         T be[R];
@@ -593,9 +593,9 @@ template <typename S, int R>
 static __global__ void __launch_bounds__(256) accumulate_kernel(VecArgs a, const OuterState *os, const S *x_, double *x64) {
     typedef typename Real<S>::type T;
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         const size_t off = ((size_t)e * a.N + r0) * 2;
         cx<T> xl[R];
         ld_pack<S, R, true>(x_ + off, xl);
@@ -687,12 +687,12 @@ static __global__ void __launch_bounds__(256) norm2_kernel(VecArgs a, const S *v
     typedef typename Real<S>::type T;
     extern __shared__ __align__(128) unsigned char smem[];
     const int G = a.N / R, lgG = __ffs(G) - 1;
-    const int total = a.n_elem << lgG;
+    const long total = (long)a.n_elem << lgG;  // elements x groups: may exceed 2^31
     cx<T> red[R][1];
 #pragma unroll
     for (int k = 0; k < R; ++k) red[k][0] = zero<T>();
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx >> lgG, r0 = (idx & (G - 1)) * R;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int e = (int)(idx >> lgG), r0 = (int)(idx & (G - 1)) * R;
         cx<T> v[R];
         ld_pack<S, R, true>(v_ + ((size_t)e * a.N + r0) * 2, v);
 #pragma unroll

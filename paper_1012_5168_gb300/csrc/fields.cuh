@@ -227,11 +227,11 @@ struct SmearArgs {
 
 static __global__ void __launch_bounds__(256) smear_kernel(SmearArgs A) {
     const int nsite = A.cb1 - A.cb0;
-    const int total = 2 * nsite * A.n;  // only the columns in use
+    const long total = 2L * nsite * A.n;  // only the columns in use
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int j = idx % A.n;
-        const int sp = idx / A.n;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % A.n);
+        const int sp = (int)(idx / A.n);
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
@@ -347,14 +347,14 @@ static __global__ void gauge_ff_kernel(const double *g64, float *out, long n_com
 // links in float-float format.
 static __global__ void __launch_bounds__(128, 3) smear_ff_kernel(SmearArgs A, const float *gauge_ff) {
     const int nsite = A.cb1 - A.cb0;
-    const int total = 2 * nsite * A.n;  // only the columns in use
+    const long total = 2L * nsite * A.n;  // only the columns in use
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
     const ff fa = df_from_double(A.a), fc = df_from_double(A.c);
     const double *__restrict__ fin = blockIdx.y ? A.in2 : A.in;  // the field of this grid row
     double *__restrict__ fout = blockIdx.y ? A.out2 : A.out;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int j = idx % A.n;
-        const int sp = idx / A.n;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx % A.n);
+        const int sp = (int)(idx / A.n);
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);

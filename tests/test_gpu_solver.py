@@ -257,3 +257,40 @@ def test_cgnr_single_precision_lp_full_size(lib):
     x2, _ = c.solve(eta, lib.Params(tol=1e-6, precision=1, delta=1e-6, batch=16, method=lib.METHOD_CGNR))
     assert torch.equal(x, x2)  # a deterministic map, as the truncated solver method needs
     c.close()
+
+
+def test_nan_source_reports_nan_and_spares_the_batch(lib):
+    """A NaN placed on the host in one source: that right-hand side reports DL_NAN, the others converge."""
+    dims, kappa = (4, 4, 4, 4), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=18)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=19, n=4)
+    b[2, 1, 2, 3, 0, 1, 2] = np.nan
+    for prec in (0, 1):
+        x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=prec, batch=4), allow_fail=True)
+        assert st[2]["status"] == lib.NAN
+        good = [0, 1, 3]
+        assert all(st[j]["status"] == 0 for j in good), st
+        res = residual(U, x.cpu().numpy()[good], b[good], kappa)
+        assert np.all(res <= 1e-11), res
+    c.close()
+
+
+def test_dilution_linearity(lib):
+    """Sum over the dilution classes of the solutions equals the solution of the undiluted noise vector."""
+    dims, kappa = (4, 4, 2, 8), 0.12
+    c = lib.Context(dims)
+    c.load_gauge(synthetic.gauge_field(dims, eps=0.45, seed=20))
+    c.set_kappa(kappa)
+    p = lib.Params(tol=1e-12, precision=1, batch=16)
+    dil = lib.DIL_SPIN | lib.DIL_COLOUR | lib.DIL_EVENODD
+    eta = c.make_sources(seed=9, noise_first=3, n_noise=1, dilution=dil)  # 24 classes of one vector
+    xi = c.make_sources(seed=9, noise_first=3, n_noise=1, dilution=0)
+    assert torch.equal(eta.sum(0), xi[0])
+    phi, _ = c.solve(eta, p)
+    phi_xi, _ = c.solve(xi, p)
+    diff = (phi.sum(0) - phi_xi[0]).abs().max().item()
+    assert diff < 1e-10 * phi_xi.abs().max().item()
+    c.close()
