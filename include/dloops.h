@@ -35,6 +35,17 @@
  *   host outputs; device outputs may be partially written.  No call aborts the
  *   process or traps on the device; device-side iteration loops are bounded.
  *   There is no CPU fallback: a missing or unusable GPU is DL_ECUDA.
+ * Threads: separate contexts may be used from separate host threads, each on
+ *   its own stream; one context is not safe for concurrent calls.
+ * Environment (read when a call starts; all off by default):
+ *   DLOOPS_SMEAR_FP64=1       smearing in FP64 instead of float-float arithmetic
+ *                             (read by dl_create);
+ *   DLOOPS_CONTINUE_CYCLES=1  keep the BiCGStab search direction and shadow
+ *                             residual across defect-correction cycles instead of
+ *                             restarting (measured slower);
+ *   DLOOPS_OUTER_DFF=1        defect-correction hops of mixed-precision solves in
+ *                             float-float arithmetic (measured slower than FP64);
+ *   DLOOPS_HOP_ARITH=dff      dl_apply_hop / dl_apply_m in float-float arithmetic.
  */
 #ifndef DLOOPS_H
 #define DLOOPS_H
