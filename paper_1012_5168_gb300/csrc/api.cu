@@ -1217,12 +1217,15 @@ static int smear_eo(dl_ctx *c, double **buf, double *spare, int N, int n, const 
         ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src, (int)c->Vh, cb0, cb1, N, n, 1, tcol, c->g.V3h);
         if (buf2)
             ff_convert_kernel<<<lc.grid, lc.block, 0, c->cur>>>(src2, (int)c->Vh, cb0, cb1, N, n, 1, tcol, c->g.V3h);
+        // one thread per (site, colour row, column): three times the threads of
+        // the whole-site kernel, each with a third of the registers
+        Launch lr = make_launch(c, 2L * (cb1 - cb0) * 3 * n, 256, 0, 6);
         for (int it = 0; it < s.n_iter; ++it) {
             A.in = src;
             A.out = dst;
             A.in2 = src2;
             A.out2 = dst2;
-            smear_ff_kernel<<<dim3(l.grid, nf), l.block, 0, c->cur>>>(A, c->d_gauge_ff);
+            smear_ff_rows_kernel<<<dim3(lr.grid, nf), lr.block, 0, c->cur>>>(A, c->d_gauge_ff);
             std::swap(src, dst);
             std::swap(src2, dst2);
         }

@@ -343,25 +343,32 @@ static __global__ void gauge_ff_kernel(const double *g64, float *out, long n_com
     }
 }
 
-// One smearing step in float-float; same contract as smear_kernel, fields and
-// links in float-float format.
-static __global__ void __launch_bounds__(128, 3) smear_ff_kernel(SmearArgs A, const float *gauge_ff) {
+// One smearing step in float-float (same contract as smear_kernel, fields
+// and links in float-float format), with the three colour rows of a site on
+// three threads: thread (site, a, j) produces the four spin components of
+// colour a.  It holds one link row and one colour vector at a time instead of
+// the whole link and the 12-component accumulator, so it needs far fewer
+// registers and more warps stay resident; the three threads of a site read the
+// same neighbour spinors, which then come from L1.
+static __global__ void __launch_bounds__(256, 3) smear_ff_rows_kernel(SmearArgs A, const float *gauge_ff) {
     const int nsite = A.cb1 - A.cb0;
-    const long total = 2L * nsite * A.n;  // only the columns in use
+    const long total = 2L * nsite * 3 * A.n;  // only the columns in use
     const size_t half = (size_t)A.g.Vh * 12 * A.N * 2;
     const ff fa = df_from_double(A.a), fc = df_from_double(A.c);
     const double *__restrict__ fin = blockIdx.y ? A.in2 : A.in;  // the field of this grid row
     double *__restrict__ fout = blockIdx.y ? A.out2 : A.out;
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         const int j = (int)(idx % A.n);
-        const int sp = (int)(idx / A.n);
+        const long rest = idx / A.n;
+        const int a = (int)(rest % 3);
+        const int sp = (int)(rest / 3);
         const int p = sp / nsite;
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
         const double *inn = fin + (size_t)(1 - p) * half;
-        ffc acc[12];
+        ffc acc[4];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) acc[k].re = acc[k].im = ff{0.f, 0.f};
+        for (int k = 0; k < 4; ++k) acc[k].re = acc[k].im = ff{0.f, 0.f};
 #pragma unroll
         for (int mu = 0; mu < 3; ++mu) {
 #pragma unroll
@@ -370,33 +377,30 @@ static __global__ void __launch_bounds__(128, 3) smear_ff_kernel(SmearArgs A, co
                 const double *up = reinterpret_cast<const double *>(
                     gauge_ff + (dir == 0 ? (((size_t)p * A.g.Vh + cb) * 4 + mu) * 36
                                          : (((size_t)(1 - p) * A.g.Vh + nb) * 4 + mu) * 36));
-                ffc u[9];
+                // forward: row a of U; backward: column a of U, conjugated in the product
+                ffc u[3];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) u[k] = ld_ffc(up + 2 * k);
+                for (int b = 0; b < 3; ++b) u[b] = ld_ffc(up + 2 * (dir == 0 ? a * 3 + b : b * 3 + a));
                 const double *src = inn + (size_t)nb * 12 * A.N * 2 + (size_t)j * 2;
 #pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    ffc v[3];
+                for (int s = 0; s < 4; ++s)
 #pragma unroll
-                    for (int b = 0; b < 3; ++b) v[b] = ld_ffc(src + (size_t)(3 * s + b) * A.N * 2);
-#pragma unroll
-                    for (int aa = 0; aa < 3; ++aa)
-#pragma unroll
-                        for (int b = 0; b < 3; ++b) {
-                            if (dir == 0) ffc_mac<false>(acc[3 * s + aa], u[aa * 3 + b], v[b]);
-                            else ffc_mac<true>(acc[3 * s + aa], u[b * 3 + aa], v[b]);
-                        }
-                }
+                    for (int b = 0; b < 3; ++b) {
+                        const ffc v = ld_ffc(src + (size_t)(3 * s + b) * A.N * 2);
+                        if (dir == 0) ffc_mac<false>(acc[s], u[b], v);
+                        else ffc_mac<true>(acc[s], u[b], v);
+                    }
             }
         }
         const double *y = fin + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
         double *o = fout + (size_t)p * half + (size_t)cb * 12 * A.N * 2 + (size_t)j * 2;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) {
+        for (int s = 0; s < 4; ++s) {
+            const int k = 3 * s + a;
             const ffc q = ld_ffc(y + (size_t)k * A.N * 2);
             ffc r;
-            r.re = df_add(df_mul(fa, q.re), df_mul(fc, acc[k].re));
-            r.im = df_add(df_mul(fa, q.im), df_mul(fc, acc[k].im));
+            r.re = df_add(df_mul(fa, q.re), df_mul(fc, acc[s].re));
+            r.im = df_add(df_mul(fa, q.im), df_mul(fc, acc[s].im));
             *reinterpret_cast<float4 *>(o + (size_t)k * A.N * 2) = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
         }
     }
