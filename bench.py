@@ -684,6 +684,13 @@ def main():
                 "launches": tim["hop_launches"][dom], "ms_per_launch": round(per_launch_ms, 5),
                 "hop_share_of_step": round(sum(tim["hop_ms"]) / ms, 3) if ms > 0 else None}
 
+    # defect-correction hops (b_hat, reconstruction, residual) of the timed steps
+    n_oh = tim["hop_launches"][2] + tim["hop_launches"][3]
+    outer_hop = {"arith": "fp64" if os.environ.get("DLOOPS_OUTER_DFF", "1").startswith("0") or w["tol"] < 1e-11
+                 else "float-float", "launches": int(n_oh),
+                 "ms_per_launch": round((tim["hop_ms"][2] + tim["hop_ms"][3]) / n_oh, 4) if n_oh else None,
+                 "share_of_step": round((tim["hop_ms"][2] + tim["hop_ms"][3]) / ms, 4) if ms > 0 else None}
+
     line = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -700,7 +707,7 @@ def main():
         "config": {"workload": w["name"], "lattice": "16x16x16x32", "kappa": w["kappa"], "eps": w["eps"],
                    "noise_vectors_per_gpu": w["n_noise"], "rhs_per_gpu": w["n_noise"] * K,
                    "dilution": w["dilution"], "tol": w["tol"], "solver": "even-odd BiCGStab, "
-                   f"{args.precision} inner + FP64 defect correction, batch {args.batch}, CUDA graphs",
+                   f"{args.precision} inner + defect correction on FP64 fields, batch {args.batch}, CUDA graphs",
                    "sinks": "local + smeared(alpha=4, n=50)", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world} (disjoint noise ranges)"},
         "loops_per_s": round(value / K, 3),
@@ -716,6 +723,7 @@ def main():
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(tim["kernel_launches"]),
         "roofline": roofline,
+        "defect_correction_hops": outer_hop,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -740,6 +748,13 @@ def reference_arm(args, rank, world):
         if s >= args.warmup:
             steps.append((rate, time.perf_counter() - t0))
     value = statistics.median(r for r, _ in steps)
+    # defect-correction hops (b_hat, reconstruction, residual) of the timed steps
+    n_oh = tim["hop_launches"][2] + tim["hop_launches"][3]
+    outer_hop = {"arith": "fp64" if os.environ.get("DLOOPS_OUTER_DFF", "1").startswith("0") or w["tol"] < 1e-11
+                 else "float-float", "launches": int(n_oh),
+                 "ms_per_launch": round((tim["hop_ms"][2] + tim["hop_ms"][3]) / n_oh, 4) if n_oh else None,
+                 "share_of_step": round((tim["hop_ms"][2] + tim["hop_ms"][3]) / ms, 4) if ms > 0 else None}
+
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t for _, t in steps), 1),

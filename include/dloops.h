@@ -37,14 +37,15 @@
  *   There is no CPU fallback: a missing or unusable GPU is DL_ECUDA.
  * Threads: separate contexts may be used from separate host threads, each on
  *   its own stream; one context is not safe for concurrent calls.
- * Environment (read when a call starts; all off by default):
+ * Environment (read when a call starts):
  *   DLOOPS_SMEAR_FP64=1       smearing in FP64 instead of float-float arithmetic
  *                             (read by dl_create);
  *   DLOOPS_CONTINUE_CYCLES=1  keep the BiCGStab search direction and shadow
  *                             residual across defect-correction cycles instead of
  *                             restarting (measured slower);
- *   DLOOPS_OUTER_DFF=1        defect-correction hops of mixed-precision solves in
- *                             float-float arithmetic (measured slower than FP64);
+ *   DLOOPS_OUTER_DFF=0        defect-correction hops of mixed-precision solves in
+ *                             FP64 instead of float-float arithmetic (float-float is
+ *                             used only for tol >= 1e-11);
  *   DLOOPS_HOP_ARITH=dff      dl_apply_hop / dl_apply_m in float-float arithmetic.
  */
 #ifndef DLOOPS_H
@@ -69,9 +70,10 @@ typedef enum dl_status {
 
 /* Precision of the Krylov iteration.  DL_PREC_F64 is a plain double-precision
  * BiCGStab; F32 and BF16 keep spinors and links in that storage type with FP32
- * arithmetic inside an FP64 defect-correction loop (true residual, solution
- * accumulation and final result in FP64).  Sec. 2: the paper's inversions use
- * mixed-precision CG/BiCGStab. */
+ * arithmetic inside a defect-correction loop on FP64 fields (solution
+ * accumulation and final result in FP64; the true residual in float-float
+ * arithmetic, about 48 significant bits, for tol >= 1e-11, else in FP64).
+ * Sec. 2: the paper's inversions use mixed-precision CG/BiCGStab. */
 enum { DL_PREC_F64 = 0, DL_PREC_F32 = 1, DL_PREC_BF16 = 2 };
 
 /* Krylov method of the inner solve.  BICGSTAB works on the even-site Schur
@@ -93,7 +95,7 @@ enum { DL_SINK_LOCAL = 1, DL_SINK_SMEARED = 2 };
 typedef struct dl_ctx dl_ctx;
 
 typedef struct dl_solve_params {
-    double tol;          /* stop when ||b - M x|| / ||b|| <= tol (FP64 true residual); > 0 */
+    double tol;          /* stop when ||b - M x|| / ||b|| <= tol (true residual on FP64 fields); > 0 */
     int precision;       /* DL_PREC_* */
     int max_iter;        /* cap on inner Krylov iterations summed over outer cycles */
     int fixed_iters;     /* > 0: run exactly this many inner iterations, one cycle, no
@@ -116,7 +118,7 @@ typedef struct dl_solve_stats {
     int status;          /* dl_status of this right-hand side */
     int iters;           /* inner Krylov iterations */
     int outer;           /* defect-correction cycles */
-    double true_residual;/* ||b - M x|| / ||b||, full lattice, FP64 */
+    double true_residual;/* ||b - M x|| / ||b||, full lattice, FP64 fields */
 } dl_solve_stats;
 
 typedef struct dl_smear {

@@ -200,8 +200,10 @@ static void record(dl_ctx *c, cudaEvent_t e) {
 }
 
 // Wilson hop launch.  kind >= 0 marks launches timed with CUDA events.
+// P_DFF: `in` is float-float; ffmt flags FF_Y / FF_OUT give the formats of y and out.
 static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void *in, const void *y, const void *z,
-                  const void *rhat, int p, int N, double coef, int cb0, int cb1, double2 *partials, int *nblocks) {
+                  const void *rhat, int p, int N, double coef, int cb0, int cb1, double2 *partials, int *nblocks,
+                  int ffmt = 0) {
     HopArgs a;
     a.out = out;
     a.in = in;
@@ -227,9 +229,9 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     int R = wide ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
-    int block = prec == P_DFF ? 64 : c->hop_block[prec][ilog2(N)];
+    int block = prec == P_DFF ? 192 : c->hop_block[prec][ilog2(N)];  // P_DFF: a multiple of 3 N
     if (block % G) block = 128;  // a multiple of G (N <= 64)
-    const long total = (long)(cb1 - cb0) * G;
+    const long total = (long)(cb1 - cb0) * G * (prec == P_DFF ? 3 : 1);
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
     const int kind = wide ? 0 : c->hop_kind[prec][ilog2(N)];
     size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (wide ? 16 : 8) : 0;
@@ -261,7 +263,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     }
     cudaError_t e;
     if (prec == P_F64) e = launch_hop_f64(R, mode, red, a, l);
-    else if (prec == P_DFF) e = launch_hop_dff(R, mode, red, a, l);
+    else if (prec == P_DFF) e = launch_hop_ff(mode, red, ffmt, a, l);
     else if (prec == P_F32) e = launch_hop_f32(R, mode, red, kind, a, l);
     else e = launch_hop_bf16(R, mode, red, kind, a, l);
     if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
@@ -877,6 +879,11 @@ static int run_chunk(dl_ctx *c, int prec, int N, int iters, bool use_graph, int 
     return DL_OK;
 }
 
+// Smallest tolerance for which mixed-precision solves form their residuals in
+// float-float arithmetic: its rounding, about 1e-14 of |x|, stays three orders
+// of magnitude below it.
+constexpr double kFFMinTol = 1e-11;
+
 struct SolveCfg {
     int method;    // DL_METHOD_BICGSTAB or DL_METHOD_CGNR
     bool outer_dff;   // defect-correction hops in float-float instead of FP64
@@ -925,10 +932,10 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
         // restart on the 16^3 x 32 workload for both inner precisions; kept as an option.
         const char *e = getenv("DLOOPS_CONTINUE_CYCLES");
         s->restart = !(e && e[0] == '1');
-        // Float-float defect-correction hops measured slower than FP64 ones on GB300
-        // (4.4 vs 3.4 ms per hop at 32 right-hand sides); kept as an option.
+        // Float-float defect-correction hops (the default for mixed precision);
+        // DLOOPS_OUTER_DFF=0 selects FP64 ones.
         const char *f = getenv("DLOOPS_OUTER_DFF");
-        s->outer_dff = f && f[0] == '1';
+        s->outer_dff = !(f && f[0] == '0');
     }
     return DL_OK;
 }
@@ -940,13 +947,46 @@ static int ready(dl_ctx *c) {
     return DL_OK;
 }
 
+// FP64 <-> float-float copy of n_complex values (in place when dst == src).
+static int ff_cast(dl_ctx *c, const double *src, double *dst, size_t n_complex, int to_ff) {
+    const long grid = std::max<long>(1, std::min<long>(((long)n_complex + 255) / 256, (long)c->num_sms * 8));
+    CK(launch_ff_cast(src, dst, n_complex, to_ff, (int)grid, c->cur));
+    c->kernel_launches++;
+    return DL_OK;
+}
+
+// The reconstruction x_o = b_o + kappa D_oe x_e and the residual
+// r = b_e - x_e + kappa D_eo x_o into c->r64 with |r|^2 partials in pa.  The
+// odd rows of b - M x vanish by construction of x_o (up to rounding) and the
+// even rows equal bhat - Mhat x_e, so r is both the Schur residual that drives
+// the next cycle and the full-lattice residual; the final solution needs no
+// further hop.  op = P_DFF: b_o is float-float, x_o is left float-float and x_e
+// is first copied to float-float in c->bh64.
+static int outer_residual(dl_ctx *c, int op, int N, const double *be, const double *bo, const double *xe,
+                          double *xo, double2 *pa, int *nb) {
+    const double k = c->kappa;
+    const int Vh = (int)c->Vh;
+    if (op == P_DFF) {
+        TRY(ff_cast(c, xe, c->bh64, half_elems(c, N), 1));
+        TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, c->bh64, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr,
+                   FF_Y | FF_OUT));
+        return do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, c->bh64, be, nullptr, 0, N, -k, 0, Vh, pa, nb, FF_Y);
+    }
+    TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
+    return do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, nb);
+}
+
 // Solve the batch held in c->b64 (n right-hand sides, layout width N); the
 // solution is left in c->x64.  host_os receives the N outer states.
 static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<OuterState> &host_os) {
     const double k = c->kappa, k2 = k * k;
-    // Defect-correction hops (bhat, residuals, reconstruction) in FP64, or in
-    // float-float on the same FP64 fields when selected (mixed precision only).
-    const int op = (P.prec != P_F64 && P.outer_dff) ? P_DFF : P_F64;
+    // Defect-correction hops (bhat, residuals, reconstruction) in float-float
+    // arithmetic for mixed-precision solves whose tolerance lies well above its
+    // rounding (~1e-14 relative), else in FP64.  In float-float, b_o and x_o are
+    // held as float-float fields until the batch ends and x_e is copied to that
+    // format (into the bhat buffer, free once r = bhat) before each residual.
+    const int op = (P.prec != P_F64 && P.outer_dff && P.tol >= kFFMinTol) ? P_DFF : P_F64;
+    const bool ffo = op == P_DFF;
     const int Vh = (int)c->Vh;
     const size_t half = half_elems(c, N) * 2;  // doubles
     double *be = c->b64, *bo = c->b64 + half, *xe = c->x64, *xo = c->x64 + half;
@@ -965,6 +1005,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         c->kernel_launches += 3;
     }
     // bhat = b_e + kappa D_eo b_o, |bhat|^2
+    if (ffo) TRY(ff_cast(c, bo, bo, half / 2, 1));
     TRY(do_hop(c, op, MODE_XPAY, RED_NORM, c->bh64, bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
     outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 0, P.tol, P.max_outer, P.max_iter);
     c->kernel_launches++;
@@ -1009,14 +1050,8 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         c->cur = c->stream;
         CK(launch_accumulate(vec_launch(c, prec, N, 0), c->d_outer, lo_ptr(c, LX), xe));
         c->kernel_launches++;
-        // The true residual, in FP64 every cycle, through the reconstruction
-        //   x_o = b_o + kappa D_oe x_e,   r = b_e - x_e + kappa D_eo x_o.
-        // The odd rows of b - M x vanish by construction of x_o (up to FP64
-        // rounding) and the even rows equal bhat - Mhat x_e, so r is both the
-        // Schur residual that drives the next cycle and the full-lattice residual;
-        // the final solution needs no further hop.
-        TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
-        TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
+        // The true residual, every cycle, through the reconstruction of x_o.
+        TRY(outer_residual(c, op, N, be, bo, xe, xo, pa, &nb));
         residual_current = true;
         outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N,
                                                                  P.fixed_iters > 0 ? 2 : 1, P.tol, P.max_outer,
@@ -1025,10 +1060,13 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         if (P.fixed_iters > 0) break;
     }
     if (!residual_current) {  // no cycle ran (every right-hand side was zero): x = (0, b_o)
-        TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, xe, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr));
-        TRY(do_hop(c, op, MODE_RESID, RED_NORM, c->r64, xo, xe, be, nullptr, 0, N, -k, 0, Vh, pa, &nb));
+        TRY(outer_residual(c, op, N, be, bo, xe, xo, pa, &nb));
         full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, 0, N, 1);
         c->kernel_launches++;
+    }
+    if (ffo) {  // back to FP64: the solution's odd half and the source
+        TRY(ff_cast(c, xo, xo, half / 2, 0));
+        TRY(ff_cast(c, bo, bo, half / 2, 0));
     }
     CK(cudaGetLastError());
     host_os.resize(N);
@@ -1164,10 +1202,13 @@ static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool 
         const int n = std::min(N, n_rhs - j0);
         c->cur = c->stream;
         TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
+        // float-float: each half is converted in place before it is gathered
+        if (op == P_DFF) TRY(ff_cast(c, c->b64 + half, c->b64 + half, half / 2, 1));
         TRY(do_hop(c, op, mode, RED_NONE, c->x64, c->b64 + half, c->b64, nullptr, nullptr, 0, N, coef, 0, Vh,
                    nullptr, nullptr));
+        if (op == P_DFF) TRY(ff_cast(c, c->b64, c->b64, half / 2, 1));
         TRY(do_hop(c, op, mode, RED_NONE, c->x64 + half, c->b64, c->b64 + half, nullptr, nullptr, 1, N, coef, 0,
-                   Vh, nullptr, nullptr));
+                   Vh, nullptr, nullptr, op == P_DFF && with_m ? FF_Y : 0));
         TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
     }
     return DL_OK;

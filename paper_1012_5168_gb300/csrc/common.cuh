@@ -142,6 +142,43 @@ __device__ __forceinline__ dfloat df_from_bits(uint32_t w0, uint32_t w1) {
     float lo = es > 0 ? __uint2float_rn(w0 & 0x1fffffffu) * __uint_as_float((uint32_t)es << 23) : 0.f;
     return dfloat(hi, sign ? -lo : lo);
 }
+// float-float -> double with integer operations only.  hi is widened exactly to
+// a 53-bit significand and lo, which lies at least 24 binary places below it
+// once renormalised, is added on that integer significand; bits of lo below its
+// last place are truncated (error below 2^-52 relative).  A zero or subnormal
+// hi gives a signed zero, an infinite or NaN hi propagates, and an
+// unnormalised pair (lo within 24 places of hi) takes the FP64 sum.
+__device__ __forceinline__ double df_to_f64(dfloat x) {
+    const uint32_t hb = __float_as_uint(x.hi), lb = __float_as_uint(x.lo);
+    const int he = (int)((hb >> 23) & 0xffu), le = (int)((lb >> 23) & 0xffu);
+    const uint64_t sign = (uint64_t)(hb >> 31) << 63;
+    if (he == 0) return __longlong_as_double((long long)sign);
+    if (he == 0xff)
+        return __longlong_as_double((long long)(sign | (0x7ffull << 52) | ((hb & 0x7fffffu) ? (1ull << 51) : 0ull)));
+    const uint32_t lsig = le ? ((lb & 0x7fffffu) | 0x800000u) : (lb & 0x7fffffu);  // subnormal lo: no hidden bit
+    const int sh = he - (le ? le : 1);
+    if (lsig != 0 && sh < 24) return (double)x.hi + (double)x.lo;
+    uint64_t m = (uint64_t)((hb & 0x7fffffu) | 0x800000u) << 29;  // hi on 53 bits
+    int e = he;
+    if (lsig != 0 && sh < 53) {
+        const uint64_t l = lsig;
+        const uint64_t lm = sh <= 29 ? (l << (29 - sh)) : (l >> (sh - 29));  // lo in units of m's last place
+        if ((hb ^ lb) >> 31) {
+            m -= lm;
+            if (!(m >> 52)) {
+                m <<= 1;
+                --e;
+            }
+        } else {
+            m += lm;
+            if (m >> 53) {
+                m >>= 1;
+                ++e;
+            }
+        }
+    }
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127 + 1023) << 52) | (m & ((1ull << 52) - 1))));
+}
 
 // Shuffle of a real across a warp (float-float: both halves).
 template <typename T>
@@ -158,17 +195,11 @@ template <> __device__ __forceinline__ dfloat from_double<dfloat>(double x) { re
 // ----------------------------------------------------------------------------
 // storage traits: S is the element type in memory (re and im interleaved);
 // arithmetic happens in Real<S> (double for FP64 storage, float otherwise).
-// dfs is FP64 storage with float-float arithmetic: fields stay double in
-// memory, links come from a float-float copy ([hi, lo] per real).
 // ----------------------------------------------------------------------------
-struct dfs {
-    double v;
-};
 template <typename S> struct Real;
 template <> struct Real<double> { typedef double type; };
 template <> struct Real<float> { typedef float type; };
 template <> struct Real<bf16> { typedef float type; };
-template <> struct Real<dfs> { typedef dfloat type; };
 
 template <typename S>
 __host__ __device__ constexpr int cbytes() { return 2 * (int)sizeof(S); }
@@ -268,18 +299,6 @@ template <> struct Conv<bf16> {
     }
 };
 
-template <> struct Conv<dfs> {
-    static constexpr int W = 4;
-    __device__ __forceinline__ static cx<dfloat> get(const uint32_t *w) {
-        return mk(df_from_bits(w[0], w[1]), df_from_bits(w[2], w[3]));
-    }
-    __device__ __forceinline__ static void put(cx<dfloat> z, uint32_t *w) {
-        const double r = (double)z.re, i = (double)z.im;
-        w[0] = (uint32_t)__double2loint(r); w[1] = (uint32_t)__double2hiint(r);
-        w[2] = (uint32_t)__double2loint(i); w[3] = (uint32_t)__double2hiint(i);
-    }
-};
-
 // Load / store R consecutive complex values of storage type S.
 template <typename S, int R, bool NC>
 __device__ __forceinline__ void ld_pack(const S *p, cx<typename Real<S>::type> (&v)[R]) {
@@ -304,12 +323,6 @@ __device__ __forceinline__ cx<typename Real<S>::type> ld_link(const S *p) {
     uint32_t w[cbytes<S>() / 4];
     RawLd<cbytes<S>(), true>::ld(p, w);
     return Conv<S>::get(w);
-}
-// float-float links: (re.hi, re.lo, im.hi, im.lo) in the 16 bytes of a complex
-template <>
-__device__ __forceinline__ cx<dfloat> ld_link<dfs>(const dfs *p) {
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-    return mk(dfloat(v.x, v.y), dfloat(v.z, v.w));
 }
 
 // ----------------------------------------------------------------------------

@@ -14,8 +14,8 @@
 
 namespace dl {
 
-// Storage precisions.  P_DFF is internal to the Wilson hop: FP64 fields and a
-// float-float link copy, float-float arithmetic (defect-correction residuals).
+// Storage precisions.  P_DFF is internal to the Wilson hop: FP64 storage
+// (float-float gathered field), float-float arithmetic (defect correction).
 enum { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_DFF = 3 };
 
 struct Launch {
@@ -77,9 +77,15 @@ inline void clamp_grid(Launch &l, int resident) {
 // lowered to the kernel's residency (l.num_sms > 0); the launch used is left in l.
 // Returns cudaErrorInvalidValue for a combination that is not instantiated.
 cudaError_t launch_hop_f64(int R, int mode, int red, const HopArgs &a, Launch &l);
-// The same hop on FP64 fields in float-float arithmetic; a.gauge is the
-// float-float link copy [2][Vh][4][9] x (re.hi, re.lo, im.hi, im.lo).  R = 1.
-cudaError_t launch_hop_dff(int R, int mode, int red, const HopArgs &a, Launch &l);
+// The same hop in float-float arithmetic, one colour row per thread
+// (hop_ff.cuh): a.in is a float-float field, a.gauge the float-float link copy
+// [2][Vh][4][9] x (re.hi, re.lo, im.hi, im.lo); fmt flags FF_Y (y float-float,
+// else FP64) and FF_OUT (out float-float, else FP64); z is FP64.  l.block is a
+// multiple of 3 N.
+enum { FF_Y = 1, FF_OUT = 2 };
+cudaError_t launch_hop_ff(int mode, int red, int fmt, const HopArgs &a, Launch &l);
+// n_complex values FP64 -> float-float (to_ff = 1) or back; dst may equal src.
+cudaError_t launch_ff_cast(const double *src, double *dst, size_t n_complex, int to_ff, int grid, cudaStream_t s);
 // kind (low precision only): 0 direct loads; 1 cp.async prefetching kernel,
 // dynamic shared memory pf_stage_bytes(prec, R) * 2 * block; 2 bulk-copy
 // staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R));

@@ -46,6 +46,37 @@ def test_solve_small(lib, prec, graph):
     c.close()
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+def test_float_float_defect_correction(lib, prec, monkeypatch):
+    """Residual steps in float-float (the mixed-precision default) and in FP64 both reach tol.
+
+    Both solutions are checked against the oracle's FP64 M on the CPU, and the
+    residual the library reports must match that CPU residual.
+    """
+    dims, kappa = (6, 4, 4, 8), 0.13
+    U = synthetic.gauge_field(dims, eps=0.45, seed=31)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=32, n=6)
+    b[5] *= 1e-7  # a right-hand side far from unit norm
+    tol = 1e-10
+    sols = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DLOOPS_OUTER_DFF", flag)
+        x, st = c.solve(to_gpu(b), lib.Params(tol=tol, precision=prec, batch=8))
+        x = x.cpu().numpy()
+        assert all(s["status"] == 0 for s in st), st
+        res = residual(U, x, b, kappa)
+        assert np.all(res <= tol), (flag, res)
+        assert all(abs(s["true_residual"] - r) < 0.01 * tol + 1e-3 * r for s, r in zip(st, res)), (flag, st, res)
+        sols.append(x)
+    monkeypatch.delenv("DLOOPS_OUTER_DFF")
+    for j in range(len(b)):
+        assert np.abs(sols[0][j] - sols[1][j]).max() < 1e-8 * np.abs(sols[1][j]).max()
+    c.close()
+
+
 def test_graph_and_eager_agree_bitwise(lib):
     """The inner iteration is deterministic: graph replay == direct launches, run twice."""
     dims, kappa = (4, 4, 4, 4), 0.12
