@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--smear-profile", metavar="N", type=int, default=None,
                     help="time the Gaussian smearing (alpha 4, 50 iterations) of N spin x colour x even-odd "
                          "diluted fields on one timeslice of 16^3x32 alone and exit")
+    ap.add_argument("--solve-profile", metavar="N", type=int, default=None,
+                    help="time two FP32-inner solves of N time-diluted noise sources on 16^3x32 (batch N) and "
+                         "report the defect-correction hop timing of the second, then exit")
     ap.add_argument("--hop-profile", metavar="PREC:N[:KIND[:R:BLOCK]]", default=None,
                     help="time the Wilson hop alone on the 16^3x32 workload (f32|bf16|f64, batch N, kernel kind "
                          "0 direct / 1 prefetch / 2 staged, right-hand sides per thread, block size; default "
@@ -256,6 +259,33 @@ def smear_profile(n: int):
     flops = 2 * (w["dims"][0] * w["dims"][1] * w["dims"][2] // 2) * n * 50 * 6 * 4 * 9 * 8
     print(json.dumps({"fields": n, "ms": [round(r, 3) for r in reps], "ms_per_iteration": round(min(reps) / 50, 4),
                       "fp64_equivalent_tflops": round(flops / (min(reps) / 1e3) / 1e12, 3)}), flush=True)
+    ctx.close()
+
+
+def solve_profile(n: int):
+    """Two mixed-precision solves of n time-diluted noise sources on 16^3x32 (batch n, FP32
+    inner, tol 1e-10) with the defect-correction hop timing of the second (used for ncu
+    captures: each solve launches the float-float hop for b_hat and twice per cycle)."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "wilson_16x16x16x32")
+    dil = dl.DIL_SPIN | dl.DIL_COLOUR | dl.DIL_EVENODD | dl.DIL_TIME
+    eta = ctx.make_sources(seed=3, noise_first=0, n_noise=(n + 23) // 24, dilution=dil)[:n].contiguous()
+    params = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=n)
+    out = {"rhs": n, "ms": []}
+    for rep in range(2):
+        ctx.set_timing(rep == 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st = ctx.solve(eta, params)
+        torch.cuda.synchronize()
+        out["ms"].append(round((time.perf_counter() - t0) * 1e3, 2))
+    tim = ctx.get_timing(reset=True)
+    n_oh = tim["hop_launches"][2] + tim["hop_launches"][3]
+    out["outer"] = [s["outer"] for s in st][:4]
+    out["defect_correction_hops"] = {"launches": int(n_oh), "ms_per_launch":
+                                     round((tim["hop_ms"][2] + tim["hop_ms"][3]) / max(n_oh, 1), 4)}
+    print(json.dumps(out), flush=True)
     ctx.close()
 
 
@@ -561,6 +591,8 @@ def main():
         return hop_profile(args.hop_profile)
     if args.smear_profile:
         return smear_profile(args.smear_profile)
+    if args.solve_profile:
+        return solve_profile(args.solve_profile)
     if args.workload != "stochastic":
         return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
                 "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,

@@ -117,6 +117,46 @@ __device__ __forceinline__ dfloat df_fma(dfloat a, dfloat b, dfloat c) {
     return dfloat(h, e - (h - s));
 }
 __device__ __forceinline__ dfloat fma(dfloat a, dfloat b, dfloat c) { return df_fma(a, b, c); }
+// a + b as an unnormalised pair: the two-sum of the high parts with the low
+// parts added to its error, without the final renormalisation (8 instructions
+// instead of 11).  Used for operands of products, where a low part up to a few
+// units of the high part's last place costs no accuracy: the error stays below
+// 2^-47 of |a| + |b|.
+__device__ __forceinline__ dfloat df_add_lazy(dfloat a, dfloat b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return dfloat(s, e + (a.lo + b.lo));
+}
+
+// Unnormalised float-float accumulator: the value is s + e, where s is the
+// running float sum of the high parts and e gathers the two-sum errors of
+// those additions and the low parts of the terms.  One addition costs 8
+// instructions and a product-accumulate 12 (against 11 and 15 with a
+// renormalisation each time); da_norm renormalises once at the end.  Over K
+// terms the error stays below about K 2^-48 of the sum of their magnitudes.
+struct dacc {
+    float s, e;
+};
+__device__ __forceinline__ void da_add(dacc &a, float hi, float lo) {
+    const float t = a.s + hi;
+    const float bb = t - a.s;
+    const float err = (a.s - (t - bb)) + (hi - bb);
+    a.s = t;
+    a.e += err + lo;
+}
+// a += x * y (the exact product of the high parts, the two cross terms; x.lo y.lo dropped)
+__device__ __forceinline__ void da_mac(dacc &a, dfloat x, dfloat y) {
+    const float p = x.hi * y.hi;
+    float pe = fmaf(x.hi, y.hi, -p);
+    pe = fmaf(x.hi, y.lo, pe);
+    pe = fmaf(x.lo, y.hi, pe);
+    da_add(a, p, pe);
+}
+__device__ __forceinline__ dfloat da_norm(dacc a) {
+    const float h = a.s + a.e;
+    return dfloat(h, a.e - (h - a.s));
+}
 // double -> float-float with FP64 arithmetic (exact for normal floats).
 __device__ __forceinline__ dfloat df_from_double(double x) {
     const float h = (float)x;
