@@ -157,6 +157,41 @@ __device__ __forceinline__ dfloat da_norm(dacc a) {
     const float h = a.s + a.e;
     return dfloat(h, a.e - (h - a.s));
 }
+// Complex lazy accumulator and its updates.
+struct cdacc {
+    dacc re, im;
+};
+__device__ __forceinline__ cdacc cda_zero() {
+    cdacc z;
+    z.re.s = z.re.e = z.im.s = z.im.e = 0.f;
+    return z;
+}
+// w += u h (DAG: conj(u) h)
+template <bool DAG>
+__device__ __forceinline__ void cda_mac(cdacc &w, cx<dfloat> u, cx<dfloat> h) {
+    const dfloat ui = DAG ? -u.im : u.im;
+    da_mac(w.re, u.re, h.re);
+    da_mac(w.re, -ui, h.im);
+    da_mac(w.im, u.re, h.im);
+    da_mac(w.im, ui, h.re);
+}
+// acc += r w with r = 1, i, -1, -i for ROT = 0, 1, 2, 3
+template <int ROT>
+__device__ __forceinline__ void cda_add(cdacc &acc, const cdacc &w) {
+    if (ROT == 0) {
+        da_add(acc.re, w.re.s, w.re.e);
+        da_add(acc.im, w.im.s, w.im.e);
+    } else if (ROT == 1) {
+        da_add(acc.re, -w.im.s, -w.im.e);
+        da_add(acc.im, w.re.s, w.re.e);
+    } else if (ROT == 2) {
+        da_add(acc.re, -w.re.s, -w.re.e);
+        da_add(acc.im, -w.im.s, -w.im.e);
+    } else {
+        da_add(acc.re, w.im.s, w.im.e);
+        da_add(acc.im, -w.re.s, -w.re.e);
+    }
+}
 // double -> float-float with FP64 arithmetic (exact for normal floats).
 __device__ __forceinline__ dfloat df_from_double(double x) {
     const float h = (float)x;

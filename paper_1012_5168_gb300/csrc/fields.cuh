@@ -289,15 +289,6 @@ typedef dfloat ff;
 struct ffc {
     ff re, im;
 };
-// acc += a * b  (DAG: acc += conj(a) * b)
-template <bool DAG>
-__device__ __forceinline__ void ffc_mac(ffc &acc, ffc a, ffc b) {
-    const ff ai = DAG ? -a.im : a.im;
-    acc.re = df_fma(a.re, b.re, acc.re);
-    acc.re = df_fma(-ai, b.im, acc.re);
-    acc.im = df_fma(a.re, b.im, acc.im);
-    acc.im = df_fma(ai, b.re, acc.im);
-}
 __device__ __forceinline__ ffc ld_ffc(const double *p) {
     const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
     ffc z;
@@ -366,9 +357,9 @@ static __global__ void __launch_bounds__(256, 3) smear_ff_rows_kernel(SmearArgs 
         const int cb = A.cb0 + sp % nsite + col_offset(A.tcol, j, A.n, A.g);
         const Site st = decode(__ldg(A.coords + (size_t)p * A.g.Vh + cb), A.g);
         const double *inn = fin + (size_t)(1 - p) * half;
-        ffc acc[4];
+        cdacc acc[4];  // unnormalised sums (common.cuh), renormalised once at the end
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k].re = acc[k].im = ff{0.f, 0.f};
+        for (int k = 0; k < 4; ++k) acc[k] = cda_zero();
 #pragma unroll
         for (int mu = 0; mu < 3; ++mu) {
 #pragma unroll
@@ -378,17 +369,20 @@ static __global__ void __launch_bounds__(256, 3) smear_ff_rows_kernel(SmearArgs 
                     gauge_ff + (dir == 0 ? (((size_t)p * A.g.Vh + cb) * 4 + mu) * 36
                                          : (((size_t)(1 - p) * A.g.Vh + nb) * 4 + mu) * 36));
                 // forward: row a of U; backward: column a of U, conjugated in the product
-                ffc u[3];
+                cx<ff> u[3];
 #pragma unroll
-                for (int b = 0; b < 3; ++b) u[b] = ld_ffc(up + 2 * (dir == 0 ? a * 3 + b : b * 3 + a));
+                for (int b = 0; b < 3; ++b) {
+                    const ffc w = ld_ffc(up + 2 * (dir == 0 ? a * 3 + b : b * 3 + a));
+                    u[b] = mk(w.re, w.im);
+                }
                 const double *src = inn + (size_t)nb * 12 * A.N * 2 + (size_t)j * 2;
 #pragma unroll
                 for (int s = 0; s < 4; ++s)
 #pragma unroll
                     for (int b = 0; b < 3; ++b) {
                         const ffc v = ld_ffc(src + (size_t)(3 * s + b) * A.N * 2);
-                        if (dir == 0) ffc_mac<false>(acc[s], u[b], v);
-                        else ffc_mac<true>(acc[s], u[b], v);
+                        if (dir == 0) cda_mac<false>(acc[s], u[b], mk(v.re, v.im));
+                        else cda_mac<true>(acc[s], u[b], mk(v.re, v.im));
                     }
             }
         }
@@ -399,8 +393,8 @@ static __global__ void __launch_bounds__(256, 3) smear_ff_rows_kernel(SmearArgs 
             const int k = 3 * s + a;
             const ffc q = ld_ffc(y + (size_t)k * A.N * 2);
             ffc r;
-            r.re = df_add(df_mul(fa, q.re), df_mul(fc, acc[s].re));
-            r.im = df_add(df_mul(fa, q.im), df_mul(fc, acc[s].im));
+            r.re = df_add(df_mul(fa, q.re), df_mul(fc, da_norm(acc[s].re)));
+            r.im = df_add(df_mul(fa, q.im), df_mul(fc, da_norm(acc[s].im)));
             *reinterpret_cast<float4 *>(o + (size_t)k * A.N * 2) = make_float4(r.re.hi, r.re.lo, r.im.hi, r.im.lo);
         }
     }

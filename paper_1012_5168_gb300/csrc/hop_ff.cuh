@@ -42,41 +42,6 @@ __device__ __forceinline__ cff ld_f64_as_ff(const double *p) {
               df_from_bits((uint32_t)__double2loint(v.y), (uint32_t)__double2hiint(v.y)));
 }
 
-// Complex lazy accumulator (dacc, common.cuh) and its updates.
-struct cdacc {
-    dacc re, im;
-};
-__device__ __forceinline__ cdacc cda_zero() {
-    cdacc z;
-    z.re.s = z.re.e = z.im.s = z.im.e = 0.f;
-    return z;
-}
-// w += u h (DAG: conj(u) h)
-template <bool DAG>
-__device__ __forceinline__ void cda_mac(cdacc &w, cff u, cff h) {
-    const dfloat ui = DAG ? -u.im : u.im;
-    da_mac(w.re, u.re, h.re);
-    da_mac(w.re, -ui, h.im);
-    da_mac(w.im, u.re, h.im);
-    da_mac(w.im, ui, h.re);
-}
-// acc += r w with r = 1, i, -1, -i for ROT = 0, 1, 2, 3
-template <int ROT>
-__device__ __forceinline__ void cda_add(cdacc &acc, const cdacc &w) {
-    if (ROT == 0) {
-        da_add(acc.re, w.re.s, w.re.e);
-        da_add(acc.im, w.im.s, w.im.e);
-    } else if (ROT == 1) {
-        da_add(acc.re, -w.im.s, -w.im.e);
-        da_add(acc.im, w.re.s, w.re.e);
-    } else if (ROT == 2) {
-        da_add(acc.re, -w.re.s, -w.re.e);
-        da_add(acc.im, -w.im.s, -w.im.e);
-    } else {
-        da_add(acc.re, w.im.s, w.im.e);
-        da_add(acc.im, -w.re.s, -w.re.e);
-    }
-}
 __device__ __forceinline__ cff cadd_lazy(cff a, cff b) { return mk(df_add_lazy(a.re, b.re), df_add_lazy(a.im, b.im)); }
 
 // Projection h = psi_up + s X_mu psi_down of colour b (s = SG), as in
