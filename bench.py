@@ -388,10 +388,12 @@ def workload_batch_scan():
             ctx.set_timing(True)
             ctx.get_timing(reset=True)
             torch.cuda.synchronize()
+            clocks = ClockSampler(torch.cuda.current_device())
             t0 = time.perf_counter()
             _, st = ctx.solve(eta, p)
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
+            clk = clocks.stop()
             tim = ctx.get_timing(reset=True)
             ctx.set_timing(False)
             plain, ms_p = _hop_rate(tim, (0,))
@@ -400,7 +402,7 @@ def workload_batch_scan():
                                 "mean_iters": round(sum(s["iters"] for s in st) / len(st), 1),
                                 "plain_hop_gbs": round(plain, 1), "fused_hop_gbs": round(fused, 1),
                                 "fused_hop_frac_of_peak": round(fused / peak, 3),
-                                "kernel_launches": tim["kernel_launches"]})
+                                "kernel_launches": tim["kernel_launches"], "clocks": clk})
     print(json.dumps(out), flush=True)
 
 
@@ -780,13 +782,6 @@ def reference_arm(args, rank, world):
         if s >= args.warmup:
             steps.append((rate, time.perf_counter() - t0))
     value = statistics.median(r for r, _ in steps)
-    # defect-correction hops (b_hat, reconstruction, residual) of the timed steps
-    n_oh = tim["hop_launches"][2] + tim["hop_launches"][3]
-    outer_hop = {"arith": "fp64" if os.environ.get("DLOOPS_OUTER_DFF", "1").startswith("0") or w["tol"] < 1e-11
-                 else "float-float", "launches": int(n_oh),
-                 "ms_per_launch": round((tim["hop_ms"][2] + tim["hop_ms"][3]) / n_oh, 4) if n_oh else None,
-                 "share_of_step": round((tim["hop_ms"][2] + tim["hop_ms"][3]) / ms, 4) if ms > 0 else None}
-
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(t for _, t in steps), 1),
