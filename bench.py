@@ -382,9 +382,10 @@ def workload_batch_scan():
     eta = ctx.make_sources(seed=3, noise_first=0, n_noise=4, dilution=dil, t0=-1)
     out = {"workload": "batch_scan_16x16x16x32", "rhs": int(eta.shape[0]), "hbm_peak_gbs": peak, "runs": []}
     for N in (16, 32, 64):
+        shape = ctx.tune_hop(dl.PREC_F32, N)  # (R, block, kernel kind, ms of one plain + one fused hop)
         for graph in (1, 0):
             p = dl.Params(tol=w["tol"], precision=dl.PREC_F32, batch=N, use_graph=graph)
-            ctx.solve(eta[:N], p)  # tune, capture graphs
+            ctx.solve(eta[:N], p)  # capture graphs
             ctx.set_timing(True)
             ctx.get_timing(reset=True)
             torch.cuda.synchronize()
@@ -402,7 +403,9 @@ def workload_batch_scan():
                                 "mean_iters": round(sum(s["iters"] for s in st) / len(st), 1),
                                 "plain_hop_gbs": round(plain, 1), "fused_hop_gbs": round(fused, 1),
                                 "fused_hop_frac_of_peak": round(fused / peak, 3),
-                                "kernel_launches": tim["kernel_launches"], "clocks": clk})
+                                "kernel_launches": tim["kernel_launches"], "clocks": clk,
+                                "hop_shape": {"R": shape[0], "block": shape[1], "kind": shape[2],
+                                              "tuned_ms": round(shape[3], 4)}})
     print(json.dumps(out), flush=True)
 
 
