@@ -7,6 +7,9 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 #include "hop.cuh"
@@ -27,21 +30,25 @@ struct Launch {
 };
 
 // Resident blocks per SM of `kernel` at this block size and dynamic shared
-// memory (cached per kernel, block and shared-memory size; each entry packs
-// the shared-memory size and the count into one atomic word, so contexts used
-// from several host threads may share the cache).
+// memory, cached per (kernel, block, shared memory).  The cache is guarded by a
+// mutex so that contexts used from several host threads may share it.  (Kernels
+// of one signature share this function's statics, so the kernel must be part of
+// the key: a cache keyed on the shape alone once handed the residency of a
+// 255-register kernel to a 64-register one and shrank its grid fourfold.)
 template <typename K>
 inline int resident_blocks(K kernel, int block, size_t smem) {
-    static std::atomic<uint64_t> cached[4][1024];
-    const int bi = block == 64 ? 0 : (block == 128 ? 1 : (block == 256 ? 2 : 3));
-    const int si = (int)((smem / 256) % 1024);
-    const uint64_t key = ((uint64_t)smem << 16) | (uint64_t)block;
-    const uint64_t v = cached[bi][si].load(std::memory_order_relaxed);
-    if ((v >> 8) == key && (v & 0xff) > 0) return (int)(v & 0xff);
+    static std::mutex m;
+    static std::map<std::tuple<const void *, int, size_t>, int> cache;
+    const auto key = std::make_tuple(reinterpret_cast<const void *>(kernel), block, smem);
+    {
+        std::lock_guard<std::mutex> g(m);
+        const auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block, smem) != cudaSuccess || n < 1) n = 1;
-    if (n > 255) n = 255;
-    cached[bi][si].store((key << 8) | (uint64_t)n, std::memory_order_relaxed);
+    std::lock_guard<std::mutex> g(m);
+    cache[key] = n;
     return n;
 }
 // Largest block (a multiple of `unit` threads, at most the kernel's limit) that maximises the
