@@ -408,9 +408,9 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     float best = 1e30f;
     int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_kind[prec][l];
     const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
-    // Two sweeps over the shapes, keeping each shape's faster time: a shape timed
-    // while something else disturbed the GPU (a batch-width switch once made the
-    // best shape read 20% slow) gets a second chance.
+    // Two sweeps over the shapes, keeping each shape's faster time, so that a
+    // shape timed while the GPU was still ramping its clocks or finishing other
+    // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
     for (int pf = 0; pf < (prec == P_F64 ? 1 : 4); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
