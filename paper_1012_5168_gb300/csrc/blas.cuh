@@ -93,6 +93,55 @@ __device__ __forceinline__ double2 sum_partials(const double2 *partials, int nbl
     return make_double2(re, im);
 }
 
+// All NV values of right-hand side `rhs` at once, each summed in exactly the
+// order of sum_partials (so the results are bitwise the same), in one pass over
+// the blocks: a thread reads the NV contiguous values of each of its blocks.
+template <int NV>
+__device__ __forceinline__ void sum_partials_all(const double2 *partials, int nblocks, int N, int rhs,
+                                                 double2 (&out)[NV]) {
+    __shared__ double2 wsum[32][NV];
+    double re[NV], im[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) re[k] = im[k] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double2 *p = partials + ((size_t)b * N + rhs) * NV;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double2 v = p[k];
+            re[k] += v.x;
+            im[k] += v.y;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            re[k] += __shfl_xor_sync(0xffffffffu, re[k], off);
+            im[k] += __shfl_xor_sync(0xffffffffu, im[k], off);
+        }
+    const int nw = blockDim.x >> 5;
+    if (nw == 1) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = make_double2(re[k], im[k]);
+        return;
+    }
+    __syncthreads();  // an earlier call may still be reading wsum
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) wsum[threadIdx.x >> 5][k] = make_double2(re[k], im[k]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double sr = 0.0, si = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            sr += wsum[w][k].x;
+            si += wsum[w][k].y;
+        }
+        out[k] = make_double2(sr, si);
+    }
+}
+
 // Threads per block of the per-right-hand-side scalar kernels (grid = N blocks).
 constexpr int kScalarThreads = 256;
 
@@ -115,8 +164,9 @@ __device__ __forceinline__ double inner_reduction(const OuterState &o, double de
 static __global__ void inner_start_kernel(RhsState *st, OuterState *os, const double2 *partials,
                                    int nblocks, int N, double delta, int max_iters, int max_total, int fixed) {
     const int r = blockIdx.x;
-    const double2 rho = sum_partials(partials, nblocks, N, 2, r, 0);
-    const double2 n2 = sum_partials(partials, nblocks, N, 2, r, 1);
+    double2 v[2];
+    sum_partials_all<2>(partials, nblocks, N, r, v);
+    const double2 rho = v[0], n2 = v[1];
     if (threadIdx.x != 0) return;
     os[r].sigma = os[r].active ? sqrt(os[r].r2) : 0.0;
     RhsState s;
@@ -162,8 +212,7 @@ static __global__ void scalar_alpha_kernel(RhsState *st, const double2 *partials
 static __global__ void scalar_omega_kernel(RhsState *st, const double2 *partials, int nblocks, int N) {
     const int r = blockIdx.x;
     double2 v[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) v[k] = sum_partials(partials, nblocks, N, 5, r, k);
+    sum_partials_all<5>(partials, nblocks, N, r, v);
     if (threadIdx.x != 0) return;
     RhsState &s = st[r];
     if (!s.active) return;
