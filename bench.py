@@ -63,9 +63,9 @@ def parse():
     ap.add_argument("--hop-profile", metavar="PREC:N[:KIND[:R:BLOCK]]", default=None,
                     help="time the Wilson hop alone on the 16^3x32 workload (f32|bf16|f64, batch N, kernel kind "
                          "0 direct / 1 prefetch / 2 staged, right-hand sides per thread, block size; default "
-                         "autotuned) and exit.  With all five fields the hop launches are, in order: 12 of the "
-                         "forced tuning run, 22 timing the choice, 8 plain (3 warm-up), 8 XPAY + <rhat, v> "
-                         "(3 warm-up), 8 XPAY + five reductions (3 warm-up)")
+                         "autotuned) and exit.  With all five fields the hop launches are, in order: 24 of the "
+                         "forced tuning run (two sweeps), 22 timing the choice, 8 plain (3 warm-up), 8 XPAY + "
+                         "<rhat, v> (3 warm-up), 8 XPAY + five reductions (3 warm-up)")
     return ap.parse_args()
 
 

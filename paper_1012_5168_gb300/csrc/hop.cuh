@@ -133,14 +133,14 @@ __device__ __forceinline__ void su3_mul(const cx<T> (&u)[9], const cx<T> (&h)[6]
         }
 }
 
-template <typename S, int R, int MU>
+template <typename S, int R, int MU, int NC>
 __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb, int r0,
                                         cx<typename Real<S>::type> (&acc)[R][12]) {
     typedef typename Real<S>::type T;
     constexpr bool G8 = sizeof(S) < sizeof(double);  // FP32 / BF16 read the site-major link rows
     const S *in = reinterpret_cast<const S *>(A.in);
     const S *gauge = reinterpret_cast<const S *>(A.gauge);
-    const size_t N = (size_t)A.N;
+    const size_t N = NC ? (size_t)NC : (size_t)A.N;
     // ---- forward: (1 - g_mu) U_mu(x) psi(x + mu)
     {
         const int nb = nbr_fwd(st, A.g, MU);
@@ -192,14 +192,18 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
     }
 }
 
-template <typename S, int R, int MODE, int RED>
+// NC > 0: the number of right-hand sides in the layout is the compile-time
+// constant NC (= A.N), so component offsets fold into the load and store
+// instructions; NC = 0 reads it from A.N.
+template <typename S, int R, int MODE, int RED, int NC = 0>
 __device__ __forceinline__ void hop_body(const HopArgs &A) {
     typedef typename Real<S>::type T;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int G = A.N / R;  // a power of two dividing 32 (checked by the host)
+    const int NN = NC ? NC : A.N;
+    const int G = NN / R;  // a power of two dividing 32 (checked by the host)
     const int lgG = __ffs(G) - 1;
-    const size_t N = (size_t)A.N;
+    const size_t N = (size_t)NN;
     const int total = (A.cb_end - A.cb_begin) << lgG;  // < 2^31 (checked by the host)
     const T cD = from_double<T>(A.c);
     cx<T> red[R][NV];
@@ -229,10 +233,10 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
         for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[r][c] = zero<T>();
-        hop_dir<S, R, 0>(A, st, cb, r0, acc);
-        hop_dir<S, R, 1>(A, st, cb, r0, acc);
-        hop_dir<S, R, 2>(A, st, cb, r0, acc);
-        hop_dir<S, R, 3>(A, st, cb, r0, acc);
+        hop_dir<S, R, 0, NC>(A, st, cb, r0, acc);
+        hop_dir<S, R, 1, NC>(A, st, cb, r0, acc);
+        hop_dir<S, R, 2, NC>(A, st, cb, r0, acc);
+        hop_dir<S, R, 3, NC>(A, st, cb, r0, acc);
 
         const size_t base = (size_t)cb * 12 * N * 2 + (size_t)r0 * 2;
         S *out = reinterpret_cast<S *>(A.out);
@@ -279,7 +283,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
             }
         }
     }
-    if (RED != RED_NONE) block_reduce<R, NV, T>(red, G, A.N, A.partials, smem);
+    if (RED != RED_NONE) block_reduce<R, NV, T>(red, G, NN, A.partials, smem);
 }
 
 // Register caps of the direct hop (0: the compiler's choice under a 256-thread
@@ -303,9 +307,9 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
     hop_body<S, R, MODE, RED>(A);
 }
 
-template <typename S, int R, int MODE, int RED, int CAP>
+template <typename S, int R, int MODE, int RED, int CAP, int NC = 0>
 __global__ void __maxnreg__(CAP) hop_kernel_cap(HopArgs A) {
-    hop_body<S, R, MODE, RED>(A);
+    hop_body<S, R, MODE, RED, NC>(A);
 }
 
 

@@ -33,6 +33,13 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
         else return hop_kernel<S, R, MODE, RED>;
     }();
     if (kind == 0) {
+        if constexpr (cap > 0) {
+            if (a.N == 32) {  // the benchmark width: offsets as compile-time constants
+                clamp_grid(l, resident_blocks(hop_kernel_cap<S, R, MODE, RED, cap, 32>, l.block, l.smem));
+                hop_kernel_cap<S, R, MODE, RED, cap, 32><<<l.grid, l.block, l.smem, l.stream>>>(a);
+                return cudaGetLastError();
+            }
+        }
         clamp_grid(l, resident_blocks(direct, l.block, l.smem));
         direct<<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
