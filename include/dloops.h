@@ -349,8 +349,8 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
  * {1, 2, 4}, threads per block in {64, 128, 256}, and for FP32/BF16 the
  * kernel kind: 0 direct, 1 cp.async-prefetching, 2 bulk-copy staged, 3 direct
  * with one contiguous range of sites per (widest resident) block.  Each
- * candidate runs one plain and one fused hop on random fields; the fastest is
- * kept for this context.
+ * candidate runs one plain and one fused hop on random fields, in two sweeps
+ * over all candidates; the fastest is kept for this context.
  * force_R / force_block > 0 and force_pf >= 0 restrict the candidates.  Solves
  * tune their (precision, batch) on first use.  *R_out, *block_out, *pf_out and
  * *ms_out (may be NULL) receive the choice and its time for one plain plus one
