@@ -1,6 +1,6 @@
 // Launch of one Wilson-hop instantiation for a low-precision storage type S
 // (float or bf16): the kernel kind picks the direct, prefetching, staged or
-// blocked-mapping kernel.  hop_f32.cu and hop_bf16.cu instantiate it.  The
+// blocked-mapping kernel.  hop_f32*.cu and hop_bf16*.cu instantiate it.  The
 // one-time settings (shared-memory opt-ins, the blocked kernel's block shape)
 // are guarded so that contexts used from several host threads can launch
 // concurrently.
@@ -84,28 +84,27 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
     return cudaErrorInvalidValue;
 }
 
-// The (R, MODE, RED) combinations the solvers use, for storage type S.
-template <typename S>
-cudaError_t launch_hop_low(int R, int mode, int red, int kind, const HopArgs &a, Launch &l) {
-#define DL_CASE(r, m, rd) \
-    if (R == r && mode == m && red == rd) return go_hop<S, r, m, rd>(a, l, kind);
-    DL_CASE(1, MODE_PLAIN, RED_NONE)
-    DL_CASE(1, MODE_XPAY, RED_NONE)
-    DL_CASE(1, MODE_XPAY, RED_R0DOT)
-    DL_CASE(1, MODE_XPAY, RED_BICG)
-    DL_CASE(1, MODE_XPAY, RED_NORM)
-    DL_CASE(2, MODE_PLAIN, RED_NONE)
-    DL_CASE(2, MODE_XPAY, RED_NONE)
-    DL_CASE(2, MODE_XPAY, RED_R0DOT)
-    DL_CASE(2, MODE_XPAY, RED_BICG)
-    DL_CASE(2, MODE_XPAY, RED_NORM)
-    DL_CASE(4, MODE_PLAIN, RED_NONE)
-    DL_CASE(4, MODE_XPAY, RED_NONE)
-    DL_CASE(4, MODE_XPAY, RED_R0DOT)
-    DL_CASE(4, MODE_XPAY, RED_BICG)
-    DL_CASE(4, MODE_XPAY, RED_NORM)
+// The (MODE, RED) combinations the solvers use, for storage type S and R
+// right-hand sides per thread.  Each (S, R) pair is instantiated in its own
+// translation unit (hop_f32.cu, hop_f32_r2.cu, ...), so the build compiles the
+// kernel variants in parallel.
+template <typename S, int R>
+cudaError_t launch_hop_low_r(int mode, int red, int kind, const HopArgs &a, Launch &l) {
+#define DL_CASE(m, rd) \
+    if (mode == m && red == rd) return go_hop<S, R, m, rd>(a, l, kind);
+    DL_CASE(MODE_PLAIN, RED_NONE)
+    DL_CASE(MODE_XPAY, RED_NONE)
+    DL_CASE(MODE_XPAY, RED_R0DOT)
+    DL_CASE(MODE_XPAY, RED_BICG)
+    DL_CASE(MODE_XPAY, RED_NORM)
 #undef DL_CASE
     return cudaErrorInvalidValue;
 }
+
+// The R = 2 and R = 4 instantiations (hop_*_r2.cu, hop_*_r4.cu).
+cudaError_t launch_hop_f32_r2(int mode, int red, int kind, const HopArgs &a, Launch &l);
+cudaError_t launch_hop_f32_r4(int mode, int red, int kind, const HopArgs &a, Launch &l);
+cudaError_t launch_hop_bf16_r2(int mode, int red, int kind, const HopArgs &a, Launch &l);
+cudaError_t launch_hop_bf16_r4(int mode, int red, int kind, const HopArgs &a, Launch &l);
 
 }  // namespace dl

@@ -1,6 +1,6 @@
 // Host-side launchers for the kernel templates.  Each precision's Wilson-hop
 // and vector kernels are instantiated in their own translation unit
-// (hop_f64.cu, hop_f32.cu, hop_bf16.cu) so the build compiles them in parallel.
+// (hop_f64.cu; hop_f32*.cu and hop_bf16*.cu, one per R) so the build compiles them in parallel.
 #pragma once
 
 #include <cuda_runtime.h>
