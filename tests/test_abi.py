@@ -81,3 +81,10 @@ def test_struct_layouts_match_the_binding(tmp_path):
         assert got[(name, "sizeof")] == ctypes.sizeof(py), name
         for field, _ in py._fields_:
             assert got[(name, field)] == getattr(py, field).offset, (name, field)
+
+
+def test_build_compiles_every_unit():
+    """Every CUDA translation unit under csrc/ is in the build (and nothing else)."""
+    from paper_1012_5168_gb300 import build
+    units = sorted(f for f in os.listdir(build.CSRC) if f.endswith(".cu"))
+    assert sorted(build.UNITS) == units
