@@ -341,3 +341,21 @@ def test_solve_larger_lattice(lib):
         b = eta[j:j + 1].cpu().numpy()
         assert residual(U, x[j:j + 1].cpu().numpy(), b, kappa)[0] <= 1e-10
     c.close()
+
+
+def test_nan_gauge_link(lib):
+    """A NaN link: load_gauge's unitarity check rejects it; loaded without the check, every
+    solve whose sources reach it reports DL_NAN and returns (FP64 and mixed precision)."""
+    dims = (4, 4, 4, 4)
+    U = synthetic.gauge_field(dims, eps=0.45, seed=40)
+    U[1, 2, 3, 0, 2, 1, 1] = np.nan  # [T][Z][Y][X][mu][3][3]
+    c = lib.Context(dims)
+    with pytest.raises(lib.DlError):
+        c.load_gauge(U)
+    c.load_gauge(U, check_unitarity=False)
+    c.set_kappa(0.12)
+    b = synthetic.random_spinor(dims, seed=41, n=2)
+    for prec in (0, 1):
+        _, st = c.solve(to_gpu(b), lib.Params(tol=1e-10, precision=prec, batch=2), allow_fail=True)
+        assert all(s["status"] == lib.NAN for s in st), st
+    c.close()
