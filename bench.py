@@ -158,8 +158,9 @@ def oracle_iters_needed() -> int:
     raise RuntimeError("no iteration count in " + path)
 
 
-def oracle_sample(seconds: float = 20.0):
-    """Time the oracle's full-lattice BiCGStab on the workload for about `seconds`.
+def oracle_sample(seconds: float = 20.0, min_iters: int = 1):
+    """Time the oracle's full-lattice BiCGStab on the workload for about `seconds`,
+    and over at least `min_iters` iterations.
 
     Returns (solves/s, description).  The oracle runs whole BiCGStab
     iterations on one 16^3 x 32 Z2 source; solves/s = 1 / (seconds per iteration
@@ -172,7 +173,7 @@ def oracle_sample(seconds: float = 20.0):
     w = WORKLOAD
     U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
     b = noise.z2_noise(w["dims"], 1, 0)
-    n_it = 1
+    n_it = max(1, int(min_iters))
     t_iter = None
     cpu0, wall0 = time.process_time(), time.perf_counter()
     while True:
@@ -183,6 +184,8 @@ def oracle_sample(seconds: float = 20.0):
         # subtract the two extra matvecs of the true-residual checks (before and after)
         t_iter = max(dt, 1e-9) / (n_it + 1.0)
         if dt >= seconds / 4 or n_it >= 64:
+            break
+        if n_it >= min_iters and dt >= seconds / 8:
             break
         n_it = min(64, max(n_it * 2, int(seconds / max(t_iter, 1e-3))))
     cores = (time.process_time() - cpu0) / max(time.perf_counter() - wall0, 1e-9)
@@ -781,8 +784,10 @@ def reference_arm(args, rank, world):
     desc, cores = "", 1
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        rate, desc, cores = oracle_sample(8.0)
-        if s >= args.warmup:
+        # warm-up steps: one iteration; timed steps: at least 5 whole iterations each
+        timed = s >= args.warmup
+        rate, desc, cores = oracle_sample(8.0, min_iters=5 if timed else 1)
+        if timed:
             steps.append((rate, time.perf_counter() - t0))
     value = statistics.median(r for r, _ in steps)
     line = {

@@ -324,12 +324,18 @@ int dl_disconnected(dl_ctx *ctx, const double *host_loops, const unsigned char *
  *
  * Limit: n_rhs * (t_hi - t_lo) <= 16384.  Larger requests return DL_EINVAL with
  * a message (split them into several calls).  Per-block partial sums live in a
- * 4 MiB array of static device storage in the library, which every GPU that
- * loads the library holds until the process exits.  The first call on each
- * device looks up that array's device address and uploads a 4 KiB constant
- * Gamma table.  Make that first call before any stream capture.  All calls
+ * 4 MiB array of static device storage in the library's device module.  With
+ * CUDA's lazy module loading that array comes into being on a device the first
+ * time any kernel of the library is used there, and it is held until the
+ * process exits.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress, which allocates nothing); the Gamma table is a
+ * compile-time constant.  Make the first call on each device before any stream
+ * capture, so that module loading does not happen during a capture.  All calls
  * share the array: calls whose kernels may overlap on the GPU (other streams,
- * other host threads) race on it and must be serialised. */
+ * other host threads) race on it and must be serialised.
+ * Errors: DL_EINVAL for bad arguments or sizes beyond the limit; DL_ECUDA when
+ * a CUDA error from earlier work of the calling thread is pending (reported
+ * and left in place, not cleared) or when a launch fails. */
 int dl_trace_loops_noalloc(const void *dev_eta, const void *dev_phi, int n_rhs, const int dims[4], int t_lo,
                            int t_hi, void *dev_out, void *cuda_stream);
 

@@ -154,24 +154,59 @@ def n_classes(dilution: int) -> int:
             * (2 if dilution & DIL_EVENODD else 1) * (8 if dilution & DIL_CUBIC else 1))
 
 
+def _noalloc_args(eta, phi, dims, t_range, out):
+    """Check the tensors of trace_loops_noalloc before anything reaches the library:
+    the kernels index the buffers from n, V and T alone, so a wrong dtype, size or
+    layout would make them read or write past the end.  Returns (dims, n, lo, hi)."""
+    import torch
+    dims = tuple(int(d) for d in dims)
+    if len(dims) != 4 or min(dims) < 1:
+        raise ValueError("dims must be four positive extents (Lx, Ly, Lz, T)")
+    V = int(np.prod(dims))
+    T = dims[3]
+    for name, t in (("eta", eta), ("phi", phi)):
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a torch tensor")
+        if t.dtype != torch.complex128:
+            raise TypeError(f"{name} must be complex128, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if eta.numel() % (12 * V) != 0:
+        raise ValueError(f"eta holds {eta.numel()} complex values, not a multiple of 12 V = {12 * V}")
+    n = eta.numel() // (12 * V)
+    if phi.numel() != eta.numel():
+        raise ValueError(f"phi holds {phi.numel()} complex values, eta {eta.numel()}")
+    lo, hi = (0, T) if t_range is None else (int(t_range[0]), int(t_range[1]))
+    if not (0 <= lo < hi <= T):
+        raise ValueError(f"bad timeslice range [{lo}, {hi}) for T = {T}")
+    if out is not None:
+        if not isinstance(out, torch.Tensor) or out.dtype != torch.complex128 or not out.is_contiguous():
+            raise TypeError("out must be a contiguous complex128 torch tensor")
+        if tuple(out.shape) != (n, 16, T):
+            raise ValueError(f"out must have shape {(n, 16, T)}, got {tuple(out.shape)}")
+    for name, t in (("eta", eta), ("phi", phi)) + ((("out", out),) if out is not None else ()):
+        if t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device != eta.device:
+            raise ValueError(f"{name} is on {t.device}, eta on {eta.device}")
+    return dims, n, lo, hi
+
+
 def trace_loops_noalloc(eta, phi, dims, t_range=None, out=None, stream=None):
     """Local loops without a context or any allocation inside the library.
 
-    eta, phi: complex128 CUDA tensors in the canonical layout; returns (or fills)
-    a complex128 CUDA tensor [n, 16, T].  For callers that cannot allocate
-    device memory: the library keeps its partial sums in fixed static storage
-    (n * (t_hi - t_lo) <= 16384); pass a preallocated `out`.
+    eta, phi: contiguous complex128 CUDA tensors in the canonical layout, n fields
+    each; returns (or fills) a complex128 CUDA tensor [n, 16, T].  For callers
+    that cannot allocate device memory: the library keeps its partial sums in
+    fixed static storage (n * (t_hi - t_lo) <= 16384); pass a preallocated `out`.
+    Every argument is checked here before the call (dtype, layout, sizes, device).
     """
     import torch
-    dims = tuple(int(d) for d in dims)
-    V = int(np.prod(dims))
-    n = eta.numel() // (12 * V)
-    T = dims[3]
-    lo, hi = t_range if t_range is not None else (0, T)
+    dims, n, lo, hi = _noalloc_args(eta, phi, dims, t_range, out)
     if out is None:
-        out = torch.empty((n, 16, T), dtype=torch.complex128, device=eta.device)
+        out = torch.empty((n, 16, dims[3]), dtype=torch.complex128, device=eta.device)
     if stream is None:
-        stream = torch.cuda.current_stream().cuda_stream
+        stream = torch.cuda.current_stream(eta.device).cuda_stream
     _check(lib().dl_trace_loops_noalloc(ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()), n,
                                         (ctypes.c_int * 4)(*dims), lo, hi, ctypes.c_void_p(out.data_ptr()),
                                         ctypes.c_void_p(stream)))

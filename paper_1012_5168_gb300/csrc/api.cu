@@ -84,8 +84,9 @@ struct dl_ctx {
     bool smear_fp64 = false;       // smear in native FP64 instead of float-float
     float *d_gauge8_32 = nullptr;  // site-major links (staged hop)
     bf16 *d_gauge8_16 = nullptr;
-    int *h_err = nullptr;          // pinned, mapped: set by the staged hop on a wait timeout
+    int *h_err = nullptr;          // pinned, mapped [2]: set by the staged hop on a wait timeout
     int *d_err = nullptr;
+    bool poisoned = false;         // a staged hop may have left bulk copies pending: no further work
     double2 *d_gammas = nullptr;  // [16][4][4]
 
     // batch workspace, width ws_N (power of two)
@@ -187,9 +188,12 @@ static void harvest(dl_ctx *c, std::vector<TimedPair> &v, bool release) {
 static int sync(dl_ctx *c) {
     CK(cudaStreamSynchronize(c->stream));
     harvest(c, c->pending, true);
-    if (c->h_err && *(volatile int *)c->h_err) {
-        *(volatile int *)c->h_err = 0;
-        return fail(DL_ECUDA, "staged Wilson hop: a bounded wait for a bulk copy ran out");
+    if (c->h_err && (((volatile int *)c->h_err)[0] || ((volatile int *)c->h_err)[1])) {
+        if (((volatile int *)c->h_err)[1]) c->poisoned = true;
+        ((volatile int *)c->h_err)[0] = 0;
+        return fail(DL_ECUDA, c->poisoned ? "staged Wilson hop: a bounded wait ran out and bulk copies may still be "
+                                            "pending; the context takes no further work"
+                                          : "staged Wilson hop: a bounded wait for a bulk copy ran out");
     }
     return DL_OK;
 }
@@ -204,6 +208,7 @@ static void record(dl_ctx *c, cudaEvent_t e) {
 static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void *in, const void *y, const void *z,
                   const void *rhat, int p, int N, double coef, int cb0, int cb1, double2 *partials, int *nblocks,
                   int ffmt = 0) {
+    if (c->poisoned) return fail(DL_ECUDA, "context unusable: a staged hop left bulk copies pending");
     HopArgs a;
     a.out = out;
     a.in = in;
@@ -594,7 +599,6 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
         for (int i = 0; i < 4; ++i)
             for (int j = 0; j < 4; ++j) gh[(n * 4 + i) * 4 + j] = make_double2(gam[n][i][j].real(), gam[n][i][j].imag());
     int rc = DL_OK;
-    if (c->h_err) *c->h_err = 0;
     if (cudaMalloc((void **)&c->d_coords, V * sizeof(uint32_t)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_gammas, 256 * sizeof(double2)) != cudaSuccess ||
         cudaMalloc((void **)&c->d_acc, 2 * 16 * dims[3] * sizeof(double2)) != cudaSuccess ||
@@ -602,9 +606,10 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
         cudaMalloc((void **)&c->d_acc2, (size_t)64 * 2 * 16 * dims[3] * sizeof(double2)) != cudaSuccess ||
         cudaHostAlloc((void **)&c->h_count, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void **)&c->d_count, c->h_count, 0) != cudaSuccess ||
-        cudaHostAlloc((void **)&c->h_err, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostAlloc((void **)&c->h_err, 2 * sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void **)&c->d_err, c->h_err, 0) != cudaSuccess)
         rc = fail(DL_ENOMEM, "context allocation failed");
+    if (rc == DL_OK) c->h_err[0] = c->h_err[1] = 0;
     if (rc == DL_OK &&
         (cudaMemcpy(c->d_coords, coords.data(), V * sizeof(uint32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
          cudaMemcpy(c->d_gammas, gh.data(), 256 * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess))
@@ -946,6 +951,7 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
 
 static int ready(dl_ctx *c) {
     if (!c) return fail(DL_EINVAL, "null context");
+    if (c->poisoned) return fail(DL_ECUDA, "context unusable: a staged hop left bulk copies pending");
     if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
     if (!c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
     return DL_OK;
@@ -998,15 +1004,27 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
     const size_t pc = c->partials_cap / 2;
     double2 *pa = c->d_partials, *pb = c->d_partials + pc;
     int nb = 0, nb2 = 0;
-    // |b|^2 over both halves
+    // |b|^2 over both halves.  For the float-float outer loop each right-hand
+    // side is first brought to a norm in [1, 2) by an exact power of two
+    // (undone on x at the end; the relative residuals do not change), so that
+    // sources of any magnitude stay inside the float exponent range.
     {
         VecLaunch v = vec_launch(c, P_F64, N, 16);
-        CK(launch_norm2(v, be, pa));
-        nb = v.l.grid;
-        CK(launch_norm2(v, bo, pb));
-        nb2 = v.l.grid;
-        full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 0);
-        c->kernel_launches += 3;
+        for (int pass = 0; pass < (ffo ? 2 : 1); ++pass) {
+            if (pass == 1) {
+                pow2_pick_kernel<<<1, 64, 0, c->stream>>>(c->d_outer, N);
+                const long rows = 2L * Vh * 12;
+                const long grid = std::min<long>((rows * N + 255) / 256, (long)c->num_sms * 8);
+                pow2_scale_kernel<<<(int)grid, 256, 0, c->stream>>>(c->b64, (size_t)rows, N, c->d_outer, +1);
+                c->kernel_launches += 2;
+            }
+            CK(launch_norm2(v, be, pa));
+            nb = v.l.grid;
+            CK(launch_norm2(v, bo, pb));
+            nb2 = v.l.grid;
+            full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, nb2, N, 0);
+            c->kernel_launches += 3;
+        }
     }
     // bhat = b_e + kappa D_eo b_o, |bhat|^2
     if (ffo) TRY(ff_cast(c, bo, bo, half / 2, 1));
@@ -1068,9 +1086,13 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
         full_norm_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, pa, nb, pb, 0, N, 1);
         c->kernel_launches++;
     }
-    if (ffo) {  // back to FP64: the solution's odd half and the source
+    if (ffo) {  // back to FP64: the solution's odd half and the source; undo the scale on x
         TRY(ff_cast(c, xo, xo, half / 2, 0));
         TRY(ff_cast(c, bo, bo, half / 2, 0));
+        const long rows = 2L * Vh * 12;
+        const long grid = std::min<long>((rows * N + 255) / 256, (long)c->num_sms * 8);
+        pow2_scale_kernel<<<(int)grid, 256, 0, c->stream>>>(c->x64, (size_t)rows, N, c->d_outer, -1);
+        c->kernel_launches++;
     }
     CK(cudaGetLastError());
     host_os.resize(N);

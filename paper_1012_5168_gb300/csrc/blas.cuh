@@ -51,6 +51,7 @@ struct OuterState {
     int outer;        // defect-correction cycles done
     int iters;        // inner iterations summed over cycles
     double sigma;     // |r64| that scaled the current inner phase (0 before the first)
+    int scale_exp;    // the batch's fields carry the exact factor 2^scale_exp (float-float outer loop)
 };
 
 __device__ __forceinline__ bool finite2(double2 z) { return isfinite(z.x) && isfinite(z.y); }
@@ -713,6 +714,33 @@ static __global__ void outer_count_kernel(const OuterState *os, int N, int *out)
         int n = 0;
         for (int r = 0; r < N; ++r) n += os[r].active;
         *out = n;
+    }
+}
+
+// Exact power-of-two scale of each right-hand side for the float-float outer
+// loop, whose numbers keep only the float exponent range (about 1e-38 to 3e38,
+// and their low words lose bits below about 1e-31 of that range): k_r =
+// -ilogb(|b_r|), so the scaled source has a norm in [1, 2).  A zero or
+// non-finite norm keeps k_r = 0.  One thread per right-hand side.
+static __global__ void pow2_pick_kernel(OuterState *os, int N) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= N) return;
+    const double b2 = os[r].full_b2;
+    os[r].scale_exp = (b2 > 0.0 && isfinite(b2)) ? -ilogb(sqrt(b2)) : 0;
+}
+
+// f[e][r] *= 2^(sign * k_r) on a field of n_rows rows of N complex doubles
+// (scalbn: exact unless a value under- or overflows).
+static __global__ void pow2_scale_kernel(double *f, size_t n_rows, int N, const OuterState *os, int sign) {
+    const size_t total = n_rows * (size_t)N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int k = sign * os[i % N].scale_exp;
+        if (k == 0) continue;
+        double2 *z = reinterpret_cast<double2 *>(f) + i;
+        double2 v = *z;
+        v.x = scalbn(v.x, k);
+        v.y = scalbn(v.y, k);
+        *z = v;
     }
 }
 

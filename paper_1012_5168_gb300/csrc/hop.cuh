@@ -55,7 +55,7 @@ struct HopArgs {
     double c;               // coefficient of D
     Geom g;
     const void *gauge8;     // [2][Vh][8][9] complex, site-major links (staged kernel)
-    int *err;               // set to 1 by the staged kernel when a bounded wait runs out
+    int *err;               // [2]: the staged kernel sets [0] when a bounded wait runs out, [1] when a drain wait does too
     int blocked;            // direct kernel: 0 cyclic site mapping, 1 one contiguous range per block
 };
 

@@ -15,8 +15,11 @@
 // registers held for loads.
 //
 // Every wait on an mbarrier is bounded.  When a bound runs out the kernel
-// records an error in *A.err, stops computing, waits (bounded again) for the
-// copies it has in flight, and returns; the host reports DL_ECUDA.
+// records an error in A.err[0], stops computing, waits (bounded again) for the
+// copies it has in flight, and returns; the host reports DL_ECUDA.  If one of
+// those drain waits runs out too, copies may still land in shared memory after
+// the block has exited; the kernel records that in A.err[1] and the host marks
+// the context unusable (every later call returns DL_ECUDA).
 #pragma once
 
 #include "hop.cuh"
@@ -301,7 +304,12 @@ __global__ void __launch_bounds__(256) hop_kernel_tma(HopArgs A) {
         // waits) before the block releases its shared memory
         if (threadIdx.x == 0) {
             if (A.err) *(volatile int *)A.err = 1;
-            for (int kk = k; kk < issued; ++kk) mbar_wait(full + (kk % NST), (uint32_t)((kk / NST) & 1));
+            bool drained = true;
+            for (int kk = k; kk < issued; ++kk)
+                drained &= mbar_wait(full + (kk % NST), (uint32_t)((kk / NST) & 1));
+            // A drain wait that ran out leaves copies into this block's shared memory
+            // pending after it exits; the host then refuses further work on the context.
+            if (!drained && A.err) *(volatile int *)(A.err + 1) = 1;
         }
         return;
     }

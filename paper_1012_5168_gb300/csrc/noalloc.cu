@@ -11,16 +11,17 @@
 // canonical fields, and keeps its per-block partial sums in a fixed-size
 // file-scope device array.
 //
-// That array (4 MiB) is created when the library is loaded and is held by every
-// GPU that loads the library until the process exits.  All calls share it and
-// it keeps the contents of the last call; every slot a call reads is written
-// earlier in the same call, so nothing has to start at zero.  Two calls whose
-// kernels overlap on the GPU (different streams, or different host threads)
-// race on the array and give wrong results: serialise them.
+// That array (4 MiB) belongs to the library's device module.  It comes into
+// being on a device when that module is first used there (with CUDA's lazy
+// module loading: the first call of any kernel of this library on that device)
+// and is held until the process exits.  All calls share it and it keeps the
+// contents of the last call; every slot a call reads is written earlier in
+// the same call, so nothing has to start at zero.  Two calls whose kernels
+// overlap on the GPU (different streams, or different host threads) race on
+// the array and give wrong results: serialise them.
 #include <cuda_runtime.h>
 
-#include <complex>
-#include <mutex>
+#include <cstdio>
 
 #include "dloops.h"
 
@@ -28,12 +29,65 @@ namespace {
 
 constexpr int kScratchElems = 1 << 18;  // double2 entries: 4 MiB
 __device__ __align__(256) double2 g_loop_scratch[kScratchElems];
-__constant__ double2 c_gamma16[256];  // the 16 Gamma matrices, [G][row][col]
 
-constexpr int kMaxDevices = 64;
-void *g_scratch_ptr[kMaxDevices];
-bool g_ready[kMaxDevices];
-std::mutex g_mutex;
+// The 16 Gamma matrices of the library's basis and order (1, g1..g4, g5,
+// g5 g_mu, g_mu g_nu for mu < nu; chiral DeGrand-Rossi g_mu), [G][row][col]
+// as (re, im) pairs, built at compile time so that no upload is needed.
+struct Cplx {
+    double re, im;
+};
+struct Mat4 {
+    Cplx a[4][4];
+};
+struct GammaTable {
+    double v[16 * 16 * 2];
+};
+constexpr Cplx cmul(Cplx x, Cplx y) { return Cplx{x.re * y.re - x.im * y.im, x.re * y.im + x.im * y.re}; }
+constexpr Mat4 mmul(const Mat4 &x, const Mat4 &y) {
+    Mat4 r{};
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            Cplx s{0.0, 0.0};
+            for (int k = 0; k < 4; ++k) {
+                const Cplx p = cmul(x.a[i][k], y.a[k][j]);
+                s = Cplx{s.re + p.re, s.im + p.im};
+            }
+            r.a[i][j] = s;
+        }
+    return r;
+}
+constexpr Mat4 gamma_mu(int mu) {
+    const Cplx O{0, 0}, I{0, 1}, mI{0, -1}, P{1, 0}, mP{-1, 0};
+    Mat4 g{};
+    const Cplx t[4][4][4] = {
+        {{O, O, O, I}, {O, O, I, O}, {O, mI, O, O}, {mI, O, O, O}},
+        {{O, O, O, mP}, {O, O, P, O}, {O, P, O, O}, {mP, O, O, O}},
+        {{O, O, I, O}, {O, O, O, mI}, {mI, O, O, O}, {O, I, O, O}},
+        {{O, O, P, O}, {O, O, O, P}, {P, O, O, O}, {O, P, O, O}},
+    };
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) g.a[i][j] = t[mu][i][j];
+    return g;
+}
+constexpr GammaTable make_gamma_table() {
+    Mat4 m[16] = {};
+    for (int i = 0; i < 4; ++i) m[0].a[i][i] = Cplx{1.0, 0.0};
+    for (int mu = 0; mu < 4; ++mu) m[1 + mu] = gamma_mu(mu);
+    m[5] = mmul(mmul(mmul(gamma_mu(0), gamma_mu(1)), gamma_mu(2)), gamma_mu(3));
+    for (int mu = 0; mu < 4; ++mu) m[6 + mu] = mmul(m[5], gamma_mu(mu));
+    int n = 10;
+    for (int a = 0; a < 4; ++a)
+        for (int b = a + 1; b < 4; ++b) m[n++] = mmul(gamma_mu(a), gamma_mu(b));
+    GammaTable t{};
+    for (int G = 0; G < 16; ++G)
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                t.v[((G * 4 + i) * 4 + j) * 2] = m[G].a[i][j].re;
+                t.v[((G * 4 + i) * 4 + j) * 2 + 1] = m[G].a[i][j].im;
+            }
+    return t;
+}
+__constant__ GammaTable c_gamma16 = make_gamma_table();
 
 }  // namespace
 
@@ -44,62 +98,19 @@ namespace {
 
 int fail(int code, const char *msg) { return dl_record_error(code, msg); }
 
-// Same gamma basis and order as every other loop output of the library.
-void build_gammas(double2 out[256]) {
-    typedef std::complex<double> z;
-    const z I(0, 1), O(0, 0), one(1, 0);
-    const z g[4][4][4] = {
-        {{O, O, O, I}, {O, O, I, O}, {O, -I, O, O}, {-I, O, O, O}},
-        {{O, O, O, -one}, {O, O, one, O}, {O, one, O, O}, {-one, O, O, O}},
-        {{O, O, I, O}, {O, O, O, -I}, {-I, O, O, O}, {O, I, O, O}},
-        {{O, O, one, O}, {O, O, O, one}, {one, O, O, O}, {O, one, O, O}},
-    };
-    z m[16][4][4];
-    auto mul = [](const z a[4][4], const z b[4][4], z r[4][4]) {
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) {
-                z s = 0;
-                for (int k = 0; k < 4; ++k) s += a[i][k] * b[k][j];
-                r[i][j] = s;
-            }
-    };
-    for (int i = 0; i < 4; ++i)
-        for (int j = 0; j < 4; ++j) m[0][i][j] = i == j ? one : O;
-    for (int mu = 0; mu < 4; ++mu)
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) m[1 + mu][i][j] = g[mu][i][j];
-    z t1[4][4], t2[4][4];
-    mul(g[0], g[1], t1);
-    mul(t1, g[2], t2);
-    mul(t2, g[3], m[5]);
-    for (int mu = 0; mu < 4; ++mu) mul(m[5], g[mu], m[6 + mu]);
-    int n = 10;
-    for (int a = 0; a < 4; ++a)
-        for (int b = a + 1; b < 4; ++b) mul(g[a], g[b], m[n++]);
-    for (int G = 0; G < 16; ++G)
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j) out[(G * 4 + i) * 4 + j] = make_double2(m[G][i][j].real(), m[G][i][j].imag());
-}
-
-// Once per device, with that device current: the device address of the
-// scratch array (host code may not use the symbol itself) and the Gamma table.
-int setup_device(void **ptr) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return fail(DL_ECUDA, "no current CUDA device");
-    if (dev < 0 || dev >= kMaxDevices) return fail(DL_EINVAL, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_ready[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_loop_scratch) != cudaSuccess || p == nullptr)
-            return fail(DL_ECUDA, "cudaGetSymbolAddress of the loop scratch array failed");
-        double2 gam[256];
-        build_gammas(gam);
-        if (cudaMemcpyToSymbol(c_gamma16, gam, sizeof(gam)) != cudaSuccess)
-            return fail(DL_ECUDA, "uploading the Gamma table failed");
-        g_scratch_ptr[dev] = p;
-        g_ready[dev] = true;
+// The device address of the scratch array on the current device (host code
+// may not use the symbol itself: there it names a host-side stand-in).  It is
+// looked up on every call, which allocates nothing and stays valid across a
+// cudaDeviceReset or a new primary context.
+int scratch_address(void **ptr) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_loop_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        static thread_local char msg[160];
+        snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the loop scratch array failed: %s", cudaGetErrorString(e));
+        return fail(DL_ECUDA, msg);
     }
-    *ptr = g_scratch_ptr[dev];
+    *ptr = p;
     return DL_OK;
 }
 
@@ -179,7 +190,8 @@ __global__ void finish_kernel(const double2 *partials, int nbx, int nt, int t_lo
         }
         for (int al = 0; al < 4; ++al)
             for (int be = 0; be < 4; ++be) {
-                const double2 g = c_gamma16[(G * 4 + al) * 4 + be];
+                const double2 g = make_double2(c_gamma16.v[((G * 4 + al) * 4 + be) * 2],
+                                               c_gamma16.v[((G * 4 + al) * 4 + be) * 2 + 1]);
                 const double2 s = S[be * 4 + al];
                 r.x += g.x * s.x - g.y * s.y;
                 r.y += g.x * s.y + g.y * s.x;
@@ -204,8 +216,16 @@ extern "C" int dl_trace_loops_noalloc(const void *dev_eta, const void *dev_phi, 
     if ((long)n_rhs * nt * 16 > kScratchElems)
         return fail(DL_EINVAL, "n_rhs * (t_hi - t_lo) exceeds 16384, the capacity of the fixed scratch array");
     if ((long)n_rhs > 65535 || (long)n_rhs * 16 * T > (1L << 30)) return fail(DL_EINVAL, "too many right-hand sides");
+    // An error left by the caller's own earlier CUDA work is reported as such
+    // and left in place (cudaPeekAtLastError does not clear it).
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        static thread_local char msg[160];
+        snprintf(msg, sizeof(msg), "an earlier CUDA error is pending in this thread: %s", cudaGetErrorString(pending));
+        return fail(DL_ECUDA, msg);
+    }
     void *scratch = nullptr;
-    int rc = setup_device(&scratch);
+    int rc = scratch_address(&scratch);
     if (rc != DL_OK) return rc;
     const long V3 = (long)dims[0] * dims[1] * dims[2];
     const long V = V3 * T;
@@ -218,9 +238,12 @@ extern "C" int dl_trace_loops_noalloc(const void *dev_eta, const void *dev_phi, 
     dim3 grid((unsigned)nbx, (unsigned)nt, (unsigned)n_rhs);
     contract_canonical_kernel<<<grid, block, 0, s>>>((const double2 *)dev_eta, (const double2 *)dev_phi, V, V3, t_lo,
                                                      nt, (double2 *)scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(DL_ECUDA, "contraction kernel launch failed");
     const int cnt = n_rhs * 16 * T;
     finish_kernel<<<(cnt + 127) / 128, 128, 0, s>>>((const double2 *)scratch, (int)nbx, nt, t_lo, T, n_rhs,
                                                      (double2 *)dev_out);
-    if (cudaGetLastError() != cudaSuccess) return fail(DL_ECUDA, "kernel launch failed");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(DL_ECUDA, "Gamma-trace kernel launch failed");
     return DL_OK;
 }

@@ -59,7 +59,10 @@ def test_float_float_defect_correction(lib, prec, monkeypatch):
     c.load_gauge(U)
     c.set_kappa(kappa)
     b = synthetic.random_spinor(dims, seed=32, n=6)
-    b[5] *= 1e-7  # a right-hand side far from unit norm
+    b[5] *= 1e-7  # right-hand sides far from unit norm, some outside the float exponent range
+    b[4] *= 1e-35
+    b[3] *= 1e-42
+    b[2] *= 1e35
     tol = 1e-10
     sols = []
     for flag in ("1", "0"):
