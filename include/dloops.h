@@ -204,6 +204,17 @@ int dl_solve_adjoint(dl_ctx *ctx, const void *dev_b, void *dev_x, int n_rhs,
  * Mixed-precision solves use that arithmetic for their defect-correction
  * steps; the variable exposes it for testing. */
 int dl_apply_hop(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
+/* out = D in computed by the inner solver's low-precision Wilson hop (Sec. 2:
+ * the mixed-precision inversions): both halves of `in` (canonical complex128)
+ * are rounded to the storage type of `precision` (DL_PREC_F32 or DL_PREC_BF16;
+ * FP64 -> float -> storage, as the solver rounds its residual), the hop runs
+ * on the FP32/BF16 link copies with FP32 arithmetic in the kernel and launch
+ * shape the context uses for that precision and width, and the result is
+ * widened exactly to complex128 in `out`.  DL_PREC_F64 is dl_apply_hop.  It
+ * exposes the reduced-precision operator so that its error against FP64 can
+ * be measured.  Errors: DL_EINVAL (precision, sizes, pointers, in == out),
+ * DL_ESTATE (no gauge field), DL_ENOMEM, DL_ECUDA. */
+int dl_apply_hop_prec(dl_ctx *ctx, int precision, const void *dev_in, void *dev_out, int n_rhs);
 /* out = M in = in - kappa D in. */
 int dl_apply_m(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
 /* out = K in, Gaussian smearing (Sec. 2), restricted to timeslices

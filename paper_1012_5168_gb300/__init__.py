@@ -42,6 +42,7 @@ SYMBOLS = (
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
     "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
     "dl_trace_loops_noalloc", "dl_bench_fma", "dl_trace_loops_mom", "dl_meson_correlators", "dl_disconnected",
+    "dl_apply_hop_prec",
 )
 
 
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
         "dl_solve": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
         "dl_solve_adjoint": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
         "dl_apply_hop": (i, [vp, vp, vp, i]),
+        "dl_apply_hop_prec": (i, [vp, i, vp, vp, i]),
         "dl_apply_m": (i, [vp, vp, vp, i]),
         "dl_apply_smear": (i, [vp, vp, vp, i, P(Smear), i, i]),
         "dl_apply_gamma_weights": (i, [vp, vp, vp, i, vp, i, i]),
@@ -327,10 +329,16 @@ class Context:
     def solve_adjoint(self, b, params: Params | None = None, x=None, allow_fail: bool = False):
         return self._solve(lib().dl_solve_adjoint, b, params, x, allow_fail)
 
-    def apply_hop(self, x, out=None):
+    def apply_hop(self, x, out=None, precision: int | None = None):
+        """out = D x (FP64); with precision PREC_F32 or PREC_BF16, the inner solver's
+        low-precision hop on x rounded to that storage type, widened back to complex128."""
         n = self._field(x)
         out = self._torch.empty_like(x) if out is None else out
-        _check(lib().dl_apply_hop(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n))
+        if precision is None:
+            _check(lib().dl_apply_hop(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n))
+        else:
+            _check(lib().dl_apply_hop_prec(self._h, int(precision), ctypes.c_void_p(x.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), n))
         return out
 
     def apply_m(self, x, out=None):

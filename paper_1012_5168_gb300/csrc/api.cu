@@ -1241,6 +1241,43 @@ static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool 
 }
 
 extern "C" int dl_apply_hop(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, false); }
+
+// out = D in with the inner solver's low-precision hop: both halves of `in`
+// rounded to the storage type, the FP32/BF16 link copies, FP32 arithmetic, the
+// kernel and launch shape the context uses for that (precision, width); the
+// result widened back to FP64.
+extern "C" int dl_apply_hop_prec(dl_ctx *c, int precision, const void *in, void *out, int n_rhs) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (precision == DL_PREC_F64) return apply_hop_impl(c, in, out, n_rhs, false);
+    if (precision != DL_PREC_F32 && precision != DL_PREC_BF16) return fail(DL_EINVAL, "unknown precision");
+    if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (n_rhs == 0) return DL_OK;
+    if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
+    const int N = std::min(64, pow2_at_least(n_rhs));
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
+    const size_t field = (size_t)c->V * 24, half = half_elems(c, N) * 2;
+    const int Vh = (int)c->Vh;
+    const size_t nc = half / 2;  // complex values per half field
+    const int grid = (int)std::min<long>(((long)nc + 255) / 256, (long)c->num_sms * 8);
+    for (int j0 = 0; j0 < n_rhs; j0 += N) {
+        const int n = std::min(N, n_rhs - j0);
+        c->cur = c->stream;
+        TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
+        CK(launch_cast(precision, c->b64, lo_ptr(c, 0), nc, 1, grid, c->stream));
+        CK(launch_cast(precision, c->b64 + half, lo_ptr(c, 1), nc, 1, grid, c->stream));
+        TRY(do_hop(c, precision, MODE_PLAIN, RED_NONE, lo_ptr(c, 2), lo_ptr(c, 1), nullptr, nullptr, nullptr, 0, N,
+                   1.0, 0, Vh, nullptr, nullptr));
+        TRY(do_hop(c, precision, MODE_PLAIN, RED_NONE, lo_ptr(c, 3), lo_ptr(c, 0), nullptr, nullptr, nullptr, 1, N,
+                   1.0, 0, Vh, nullptr, nullptr));
+        CK(launch_cast(precision, c->x64, lo_ptr(c, 2), nc, 0, grid, c->stream));
+        CK(launch_cast(precision, c->x64 + half, lo_ptr(c, 3), nc, 0, grid, c->stream));
+        c->kernel_launches += 4;
+        TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
+    }
+    return DL_OK;
+}
 extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, true); }
 
 // Smear the EO fields at *buf (full field, width N) over cb range; returns the

@@ -778,6 +778,25 @@ static __global__ void __launch_bounds__(256) norm2_kernel(VecArgs a, const S *v
     block_reduce<R, 1, T>(red, G, a.N, partials, smem);
 }
 
+// FP64 <-> storage type S over n_complex values: to_lo = 1 rounds FP64 to S the
+// way the solver's inner phase does (to float, then to S), to_lo = 0 widens S to
+// FP64 exactly.
+template <typename S>
+static __global__ void cast_kernel(double *f64, S *lo, size_t n_complex, int to_lo) {
+    typedef typename Real<S>::type T;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_complex; i += (size_t)gridDim.x * blockDim.x) {
+        if (to_lo) {
+            const double2 v = reinterpret_cast<const double2 *>(f64)[i];
+            cx<T> z[1] = {mk((T)v.x, (T)v.y)};
+            st_pack<S, 1>(lo + 2 * i, z);
+        } else {
+            cx<T> z[1];
+            ld_pack<S, 1, false>(lo + 2 * i, z);
+            reinterpret_cast<double2 *>(f64)[i] = make_double2((double)z[0].re, (double)z[0].im);
+        }
+    }
+}
+
 // deterministic pseudo-random fill (for timing runs only)
 template <typename S>
 static __global__ void fill_kernel(S *v, size_t n_complex, uint32_t seed) {

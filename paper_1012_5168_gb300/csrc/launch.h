@@ -135,5 +135,6 @@ cudaError_t launch_cg_update(const VecLaunch &v, const RhsState *st, void *x, vo
                              double2 *partials);
 cudaError_t launch_cg_p(const VecLaunch &v, const RhsState *st, const void *u, void *p, int init);
 cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s);
+cudaError_t launch_cast(int prec, double *f64, void *lo, size_t n_complex, int to_lo, int grid, cudaStream_t s);
 
 }  // namespace dl

@@ -89,6 +89,14 @@ cudaError_t launch_cg_p(const VecLaunch &v, const RhsState *st, const void *u, v
     return cudaGetLastError();
 }
 
+cudaError_t launch_cast(int prec, double *f64, void *lo, size_t n_complex, int to_lo, int grid, cudaStream_t s) {
+    const int block = 256;
+    if (prec == P_F32) cast_kernel<float><<<grid, block, 0, s>>>(f64, (float *)lo, n_complex, to_lo);
+    else if (prec == P_BF16) cast_kernel<bf16><<<grid, block, 0, s>>>(f64, (bf16 *)lo, n_complex, to_lo);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s) {
     const int grid = 1024, block = 256;
     if (prec == P_F64) fill_kernel<double><<<grid, block, 0, s>>>((double *)x, n_complex, seed);

@@ -1,0 +1,209 @@
+"""Parity at the sizes and widths the bench runs, and configurations 3 and 4 at their stated sizes (GPU).
+
+The bench works on 16^3 x 32 with batches of 32 right-hand sides, smears 50
+times (alpha = 4) on the source timeslice and contracts local and smeared
+loops there.  These tests repeat each stage in that launch configuration and
+compare it with the oracle on sampled outputs the oracle computes one by one:
+one timeslice of the smearing is an independent 16^3 lattice (the smearing
+operator is three-dimensional), and the Wilson hop and M are applied to
+single fields.
+
+Reduced precision: the FP32 and BF16 Wilson hops of the inner solver are
+compared with the FP64 oracle hop on every site, and their error is stated.
+The bound follows from the storage: every input of the hop (spinor and link)
+is rounded once, to 24 significand bits for FP32 and 8 for BF16, and each
+output component is a sum of 48 such products (8 directions, 3 colours, 2
+spin terms), so the error relative to the largest output stays below a few
+units of 2^-24 (FP32) or 2^-8 (BF16).
+"""
+
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import loops, smear, wilson
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+W = synthetic.WORKLOADS["wilson_16x16x16x32"]
+
+
+def to_gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def loop_error(got, ref):
+    """max over Gamma of ||got_G - ref_G|| / max(||ref_G||, 1e-6 ||ref_1||) (last axis: timeslices)."""
+    floor = 1e-6 * np.linalg.norm(ref[0])
+    num = np.linalg.norm(got - ref, axis=-1)
+    den = np.maximum(np.linalg.norm(ref, axis=-1), floor)
+    return float((num / den).max())
+
+
+def hop_error(got, ref):
+    """max over fields of max|got - ref| / max|ref| (every site and component)."""
+    n = len(ref)
+    return float((np.abs(got - ref).reshape(n, -1).max(1) / np.abs(ref).reshape(n, -1).max(1)).max())
+
+
+@pytest.fixture(scope="module")
+def full(lib):
+    U = synthetic.gauge_field(W["dims"], W["eps"], W["seed"])
+    c = lib.Context(W["dims"])
+    c.load_gauge(U)
+    c.set_kappa(W["kappa"])
+    yield c, U
+    c.close()
+
+
+# FP32: a few units of 2^-24 = 6.0e-8; BF16: a few units of 2^-8 = 3.9e-3
+HOP_BOUND = {1: 1e-6, 2: 2e-2}
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_low_precision_hop_error_every_kernel(lib, prec):
+    """The inner solver's FP32 / BF16 hop, each kernel kind, against the FP64 oracle hop on every site."""
+    dims = (6, 4, 4, 8)
+    U = synthetic.gauge_field(dims, eps=0.45, seed=41)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    psi = synthetic.random_spinor(dims, seed=42, n=7)
+    ref = wilson.hop(U, psi, -1.0)
+    for kind in (0, 1, 2, 3):
+        R, B, k, _ = c.tune_hop(prec, 8, force_pf=kind)
+        assert k == kind
+        got = c.apply_hop(to_gpu(psi), precision=prec).cpu().numpy()
+        err = hop_error(got, ref)
+        print(f"hop prec {prec} kind {kind} (R {R}, block {B}): max error {err:.3e} of max|D psi|")
+        assert err < HOP_BOUND[prec]
+    exact = c.apply_hop(to_gpu(psi)).cpu().numpy()  # the FP64 hop of the same context
+    assert hop_error(exact, ref) < 1e-14
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_low_precision_hop_error_full_size(lib, full, prec):
+    """16^3 x 32 at the bench width of 32 right-hand sides, in the tuned launch shape; fields 0 and 31
+    against the FP64 oracle hop on every site."""
+    c, U = full
+    c.tune_hop(prec, 32)
+    eta = c.make_sources(seed=11, noise_first=0, n_noise=32, dilution=0)
+    got = c.apply_hop(eta, precision=prec)
+    for j in (0, 31):
+        ref = wilson.hop(U, eta[j:j + 1].cpu().numpy(), -1.0)
+        err = hop_error(got[j:j + 1].cpu().numpy(), ref)
+        print(f"full-size hop prec {prec} field {j}: max error {err:.3e} of max|D eta|")
+        assert err < HOP_BOUND[prec]
+
+
+def test_loops_local_and_smeared_full_size(lib, full):
+    """Eight fields on 16^3 x 32, time-diluted to timeslices 3 and 17 as in the bench; smearing
+    alpha = 4, 50 iterations in float-float arithmetic; local and smeared loops vs the oracle on
+    those timeslices, each smeared as an independent 16^3 lattice."""
+    c, U = full
+    n = 8
+    t_of = [3] * 4 + [17] * 4
+    eta = c.make_sources(seed=12, noise_first=0, n_noise=n, dilution=0)
+    phi = c.make_sources(seed=13, noise_first=0, n_noise=n, dilution=0)
+    got = c.trace_loops(eta, phi, lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(4.0, 50), t_of_rhs=t_of)
+    assert got.shape == (n, 2, 16, W["dims"][3])
+    worst_l = worst_s = 0.0
+    for j in range(n):
+        t = t_of[j]
+        others = [s for s in range(W["dims"][3]) if s != t]
+        assert np.all(got[j][:, :, others] == 0)
+        e = eta[j, t:t + 1].cpu().numpy()[None]  # a T = 1 lattice: [1][1][16][16][16][4][3]
+        f = phi[j, t:t + 1].cpu().numpy()[None]
+        Us = U[t:t + 1]
+        ref_l = loops.stochastic_loops(e, f)[0]  # [16][1]
+        ref_s = loops.stochastic_loops(smear.smear(Us, e, 4.0, 50), smear.smear(Us, f, 4.0, 50))[0]
+        worst_l = max(worst_l, loop_error(got[j, 0][:, t:t + 1], ref_l))
+        worst_s = max(worst_s, loop_error(got[j, 1][:, t:t + 1], ref_s))
+    print(f"full-size loops: local {worst_l:.3e}, smeared {worst_s:.3e}")
+    assert worst_l < 1e-12
+    assert worst_s < 1e-12
+
+
+def test_local_loops_all_timeslices_full_size(lib, full):
+    """Local loops of 32 fields over all 32 timeslices; fields 0 and 31 vs the oracle."""
+    c, U = full
+    eta = c.make_sources(seed=14, noise_first=0, n_noise=32, dilution=0)
+    phi = c.make_sources(seed=15, noise_first=0, n_noise=32, dilution=0)
+    got = c.trace_loops(eta, phi, lib.SINK_LOCAL)
+    for j in (0, 31):
+        ref = loops.stochastic_loops(eta[j].cpu().numpy(), phi[j].cpu().numpy())
+        err = loop_error(got[j, 0], ref)
+        print(f"full-size local loops field {j}: {err:.3e}")
+        assert err < 1e-12
+
+
+@pytest.mark.parametrize("prec, width", [(1, 64), (2, 32), (2, 64)])
+def test_solve_full_size_widths(lib, full, prec, width):
+    """FP32-inner at width 64, BF16-inner at widths 32 and 64, to 1e-10 on 16^3 x 32; every reported
+    residual within tol and the first and last checked with the oracle's FP64 M."""
+    c, U = full
+    eta = c.make_sources(seed=16, noise_first=0, n_noise=width, dilution=0)
+    x, st = c.solve(eta, lib.Params(tol=1e-10, precision=prec, batch=width))
+    assert all(s["status"] == 0 and s["true_residual"] <= 1e-10 for s in st), st
+    for j in (0, width - 1):
+        b = eta[j:j + 1].cpu().numpy()
+        r = b - wilson.apply_m(U, x[j:j + 1].cpu().numpy(), W["kappa"], -1.0)
+        res = np.linalg.norm(r) / np.linalg.norm(b)
+        print(f"prec {prec} width {width} field {j}: oracle residual {res:.3e}, reported {st[j]['true_residual']:.3e}")
+        assert res <= 1e-10
+        assert abs(res - st[j]["true_residual"]) < 1e-12 + 1e-3 * res
+
+
+def test_tsm_8x8x8x16_against_exact_loops(lib):
+    """Configuration 3: the truncated solver method on 8^3 x 16 with 500 low-precision solves (BF16
+    storage, 30 fixed BiCGStab iterations) and 50 high-precision corrections (FP32 inner, 1e-10),
+    spin x colour x time dilution, against the exact loops from all 12 V = 98,304 point sources.
+    The estimate is unbiased (Sec. 2, after Bali et al.), so |mean - exact| / sigma stays O(1):
+    below 5 for every Gamma and timeslice, median below 1.5."""
+    w = synthetic.WORKLOADS["tsm_8x8x8x16"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    c = lib.Context(w["dims"])
+    c.load_gauge(U)
+    c.set_kappa(w["kappa"])
+    V = int(np.prod(w["dims"]))
+    exact, st = c.exact_loops(0, 12 * V, lib.Params(tol=1e-10, precision=1, batch=64))
+    assert st["true_residual"] <= 1e-10
+    exact = exact[0]
+    dil = lib.DIL_SPIN | lib.DIL_COLOUR | lib.DIL_TIME
+    lp = lib.Params(precision=2, fixed_iters=30, batch=64)
+    hp = lib.Params(tol=1e-10, precision=1, batch=64)
+    mean, var = c.tsm_estimate(1, 500, 50, dil, -1, lp, hp, lib.SINK_LOCAL)
+    mean, var = mean[0], var[0]
+    sig = np.sqrt(var.real + var.imag)
+    assert np.all(sig > 0)
+    z = np.abs(mean - exact) / sig
+    print(f"TSM vs exact: median |z| {np.median(z):.2f}, max {z.max():.2f}")
+    assert z.max() < 5.0
+    assert np.median(z) < 1.5
+    c.close()
+
+
+def test_dkappa_central_difference_16x16x16x32(lib, full):
+    """Configuration 4 on the large lattice: d/dkappa of the g5 loop estimate from 32 Z2 sources,
+    through the adjoint solve, against central differences with dkappa = 1e-5 (solves to 1e-13).
+    The difference quotient divides the solve error, about 1e-13 of the loop, by 2 dkappa, and the
+    g5 loop cancels strongly between sites, so the bound is 1e-4 of the derivative."""
+    from paper_1012_5168_gb300.autograd import loop_trace
+    c, U = full
+    kappa = W["kappa"]
+    params = lib.Params(tol=1e-13, precision=1, batch=32)
+    eta = c.make_sources(seed=17, noise_first=0, n_noise=32, dilution=0)
+    k = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    L = loop_trace(eta, k, c, params)
+    loss = L[:, 5].real.sum()
+    loss.backward()
+    dk = 1e-5
+    lp = loop_trace(eta, torch.tensor(kappa + dk, dtype=torch.float64), c, params)[:, 5].real.sum()
+    lm = loop_trace(eta, torch.tensor(kappa - dk, dtype=torch.float64), c, params)[:, 5].real.sum()
+    fd = (lp - lm).item() / (2 * dk)
+    rel = abs(k.grad.item() - fd) / abs(fd)
+    print(f"d/dkappa 16^3x32: autograd {k.grad.item():.10e}, central difference {fd:.10e}, rel {rel:.2e}")
+    assert rel < 1e-4
+    c.set_kappa(kappa)
