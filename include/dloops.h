@@ -365,7 +365,9 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
  * and batch width n_rhs.  The candidates are: right-hand sides per thread R in
  * {1, 2, 4}, threads per block in {64, 128, 256}, and for FP32/BF16 the
  * kernel kind: 0 direct, 1 cp.async-prefetching, 2 bulk-copy staged, 3 direct
- * with one contiguous range of sites per (widest resident) block.  Each
+ * with one contiguous range of sites per (widest resident) block, 4 warp-staged
+ * (one site per warp with its own ring of bulk copies; only where
+ * n_rhs = 32 R, i.e. widths 32 and 64).  Each
  * candidate runs one plain and one fused hop on random fields, in two sweeps
  * over all candidates; the fastest is kept for this context.
  * force_R / force_block > 0 and force_pf >= 0 restrict the candidates.  Solves

@@ -127,7 +127,7 @@ struct dl_ctx {
     int64_t kernel_launches = 0;
     int hop_R[3][8];      // right-hand sides per thread, [prec][log2 N]
     int hop_block[3][8];  // threads per block
-    int hop_kind[3][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged
+    int hop_kind[3][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged
     bool hop_tuned[3][8];
     bool autotune = true;
 };
@@ -252,7 +252,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
         items = (long)((cb1 - cb0 + sites - 1) / sites) * block;  // one chunk per block at a time
     }
     Launch l = make_launch(c, items, block, smem, kind == 0 ? 16 : per_sm);
-    if (kind == 0 || kind == 3) l.num_sms = c->num_sms;  // direct kernels size their grid from residency
+    // the direct and warp-staged kernels size their grid from residency
+    if (kind == 0 || kind == 3 || kind == 4) l.num_sms = c->num_sms;
     const bool timed = c->timing;
     TimedPair tp;
     if (timed) {
@@ -417,7 +418,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // shape timed while the GPU was still ramping its clocks or finishing other
     // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 4); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 5); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
@@ -427,7 +428,8 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                 const int B = Bs[bi];
                 if (B % (N / R) || (force_block && B != force_block)) continue;
                 if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
-                if (pf == 3 && bi > 0) continue;  // the launcher picks the block
+                if ((pf == 3 || pf == 4) && bi > 0) continue;  // the launcher picks the block
+                if (pf == 4 && N != 32 * R) continue;          // warp-staged: one site per warp
                 if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
                 c->hop_R[prec][l] = R;
                 c->hop_block[prec][l] = B;

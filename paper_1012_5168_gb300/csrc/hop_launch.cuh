@@ -1,6 +1,7 @@
 // Launch of one Wilson-hop instantiation for a low-precision storage type S
 // (float or bf16): the kernel kind picks the direct, prefetching, staged or
-// blocked-mapping kernel.  hop_f32*.cu and hop_bf16*.cu instantiate it.  The
+// blocked-mapping or warp-staged kernel.  hop_f32*.cu and hop_bf16*.cu
+// instantiate it.  The
 // one-time settings (shared-memory opt-ins, the blocked kernel's block shape)
 // are guarded so that contexts used from several host threads can launch
 // concurrently.
@@ -8,7 +9,7 @@
 
 #include <mutex>
 
-#include "hop_tma.cuh"
+#include "hop_ws.cuh"
 #include "launch.h"
 
 namespace dl {
@@ -79,6 +80,20 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
         l.smem = per_warp * (l.block / 32);
         l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (int)((sh >> 16) & 0xff);
         direct<<<l.grid, l.block, l.smem, l.stream>>>(b);
+        return cudaGetLastError();
+    }
+    if (kind == 4) {  // warp-staged: one site per warp, so N = 32 R
+        if (a.N != 32 * R) return cudaErrorInvalidValue;
+        static size_t opted = 0;
+        static std::mutex m;
+        auto kern = hop_kernel_ws<S, R, MODE, RED>;
+        l.block = WS_WARPS * 32;
+        l.smem = WsShape<S, R>::WB * WS_WARPS;
+        const cudaError_t e = opt_in_smem(kern, l.smem, opted, m);
+        if (e != cudaSuccess) return e;
+        const int res = resident_blocks(kern, l.block, l.smem);
+        l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (res < 16 ? res : 16);
+        kern<<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
     }
     return cudaErrorInvalidValue;

@@ -97,7 +97,9 @@ cudaError_t launch_ff_cast(const double *src, double *dst, size_t n_complex, int
 // dynamic shared memory pf_stage_bytes(prec, R) * 2 * block; 2 bulk-copy
 // staged kernel, dynamic shared memory tma_smem_bytes(prec, N, block / (N/R));
 // 3 direct loads with one contiguous site range per block, the widest resident
-// block and one wave of blocks (the launcher sets block, grid and shared memory).
+// block and one wave of blocks (the launcher sets block, grid and shared memory);
+// 4 warp-staged bulk copies, one site per warp, N = 32 R only (the launcher sets
+// block, grid and shared memory; other widths return cudaErrorInvalidValue).
 cudaError_t launch_hop_f32(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 cudaError_t launch_hop_bf16(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 

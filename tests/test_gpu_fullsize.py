@@ -80,6 +80,16 @@ def test_low_precision_hop_error_every_kernel(lib, prec):
         assert err < HOP_BOUND[prec]
     exact = c.apply_hop(to_gpu(psi)).cpu().numpy()  # the FP64 hop of the same context
     assert hop_error(exact, ref) < 1e-14
+    # the warp-staged kernel serves widths 32 and 64 only
+    for n in (32, 64):
+        wide = synthetic.random_spinor(dims, seed=43, n=n)
+        ref_w = wilson.hop(U, wide[[0, n - 1]], -1.0)
+        R, B, k, _ = c.tune_hop(prec, n, force_pf=4)
+        assert k == 4
+        got = c.apply_hop(to_gpu(wide), precision=prec).cpu().numpy()[[0, n - 1]]
+        err = hop_error(got, ref_w)
+        print(f"hop prec {prec} kind 4 width {n} (R {R}): max error {err:.3e} of max|D psi|")
+        assert err < HOP_BOUND[prec]
     c.close()
 
 

@@ -190,8 +190,28 @@ def test_hop_kernel_kinds(lib, prec, kind, batch):
     c.close()
 
 
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("batch", [32, 64])
+def test_warp_staged_hop_solves(lib, prec, batch):
+    """The warp-staged hop (one site per warp, N = 32 R) at the two widths it serves, with a ragged
+    last batch, solves to tolerance."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=9)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=22, n=batch + 3)
+    R, B, k, _ = c.tune_hop(prec, batch, force_pf=4)
+    assert k == 4 and R == batch // 32
+    x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=prec, batch=batch))
+    assert all(s["status"] == 0 for s in st), st
+    res = residual(U, x.cpu().numpy(), b, kappa)
+    assert np.all(res <= 1e-11), res
+    c.close()
+
+
 def test_hop_kernel_kinds_full_size(lib):
-    """The four hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides)."""
+    """The five hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides)."""
     w = synthetic.WORKLOADS["wilson_16x16x16x32"]
     U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
     c = lib.Context(w["dims"])
@@ -199,7 +219,7 @@ def test_hop_kernel_kinds_full_size(lib):
     c.set_kappa(w["kappa"])
     eta = c.make_sources(seed=4, noise_first=0, n_noise=32, dilution=0)
     sols = []
-    for kind in (0, 1, 2, 3):
+    for kind in (0, 1, 2, 3, 4):
         c.tune_hop(1, 32, force_pf=kind)
         x, st = c.solve(eta, lib.Params(tol=1e-10, precision=1, batch=32))
         assert all(s["status"] == 0 and s["true_residual"] <= 1e-10 for s in st)
