@@ -89,8 +89,10 @@ enum { DL_METHOD_BICGSTAB = 0, DL_METHOD_CGNR = 1 };
  * timeslice; no extra inversions). */
 enum { DL_DIL_SPIN = 1, DL_DIL_COLOUR = 2, DL_DIL_EVENODD = 4, DL_DIL_CUBIC = 8, DL_DIL_TIME = 16 };
 
-/* Sink selection for loop contractions (Sec. 2: local and smeared fields). */
-enum { DL_SINK_LOCAL = 1, DL_SINK_SMEARED = 2 };
+/* Sink selection for loop contractions (Sec. 2: local and smeared fields).
+ * DL_SUM_T, or-ed into the sink mask of dl_trace_loops, sums each loop over
+ * the timeslices on the device (the total sum_x eta^dag Gamma phi). */
+enum { DL_SINK_LOCAL = 1, DL_SINK_SMEARED = 2, DL_SUM_T = 4 };
 
 typedef struct dl_ctx dl_ctx;
 
@@ -173,13 +175,20 @@ int dl_get_timing(dl_ctx *ctx, dl_timing *out, int reset);
  * index k = ((k_spin*C + k_colour)*E + k_eo)*Q + k_cubic), written to
  * dev_out[(n - noise_first)*K + k] in canonical layout (complex128).  With
  * DL_DIL_TIME only timeslice t0 is kept, or n mod T when t0 < 0.  *n_rhs
- * (may be NULL) receives n_noise*K.  dev_out must hold n_noise*K*V*12 complex. */
+ * (may be NULL) receives n_noise*K.  dev_out must hold n_noise*K*V*12 complex
+ * values in the storage of `prec`: DL_PREC_F64 complex128, DL_PREC_F32
+ * complex64 (two floats), DL_PREC_BF16 two bfloat16 (re, im); the value
+ * +-1/sqrt(2) is rounded from FP64 to nearest (through float for BF16).  The
+ * solver and the contractions take complex128 fields; the narrower outputs
+ * feed callers that keep sources in working precision.  Errors: DL_EINVAL
+ * (ranges, dilution bits, t0, precision, NULL output), DL_ECUDA. */
 int dl_make_sources(dl_ctx *ctx, uint64_t seed, int64_t noise_first, int n_noise,
-                    unsigned dilution, int t0, void *dev_out, int64_t *n_rhs);
+                    unsigned dilution, int t0, int prec, void *dev_out, int64_t *n_rhs);
 
 /* Point sources e_s with s = 12*i + 3*alpha + a for s = first .. first + n - 1
- * (Sec. 1-2: the exact all-to-all diagonal needs all 12V of them). */
-int dl_make_point_sources(dl_ctx *ctx, int64_t first, int n, void *dev_out);
+ * (Sec. 1-2: the exact all-to-all diagonal needs all 12V of them), n canonical
+ * fields in the storage of `prec` (as for dl_make_sources). */
+int dl_make_point_sources(dl_ctx *ctx, int64_t first, int n, int prec, void *dev_out);
 
 /* --- solver (Sec. 2) ------------------------------------------------------ */
 
@@ -241,7 +250,9 @@ int dl_apply_gamma_weights(dl_ctx *ctx, const void *dev_in, void *dev_out, int n
  * non-NULL.  group >= 1 must divide n_rhs: the loops of each run of `group`
  * consecutive pairs are summed (for instance the dilution classes of one noise
  * vector; group = 1 gives per-pair loops, group = n_rhs the total).
- * host_out: double [n_rhs/group][n_sinks][16][T][2] (local first). */
+ * host_out: double [n_rhs/group][n_sinks][16][T][2] (local first); with
+ * DL_SUM_T in `sink`, double [n_rhs/group][n_sinks][16][2], each value the sum
+ * over the timeslices (fixed order, FP64). */
 int dl_trace_loops(dl_ctx *ctx, const void *dev_eta, const void *dev_phi, int n_rhs, int sink,
                    const dl_smear *smear, int t_lo, int t_hi, const int *t_of_rhs, int group,
                    double *host_out);

@@ -30,7 +30,7 @@ OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, BREAKDOWN, NAN, ESTATE = range(8)
 PREC_F64, PREC_F32, PREC_BF16 = 0, 1, 2
 METHOD_BICGSTAB, METHOD_CGNR = 0, 1
 DIL_SPIN, DIL_COLOUR, DIL_EVENODD, DIL_CUBIC, DIL_TIME = 1, 2, 4, 8, 16
-SINK_LOCAL, SINK_SMEARED = 1, 2
+SINK_LOCAL, SINK_SMEARED, SUM_T = 1, 2, 4
 
 GAMMA_NAMES = ("1", "g1", "g2", "g3", "g4", "g5", "g5g1", "g5g2", "g5g3", "g5g4",
                "g1g2", "g1g3", "g1g4", "g2g3", "g2g4", "g3g4")
@@ -95,8 +95,8 @@ def lib() -> ctypes.CDLL:
         "dl_set_kappa": (i, [vp, d]),
         "dl_set_timing": (i, [vp, i]),
         "dl_get_timing": (i, [vp, P(Timing), i]),
-        "dl_make_sources": (i, [vp, u64, i64, i, ctypes.c_uint, i, vp, P(i64)]),
-        "dl_make_point_sources": (i, [vp, i64, i, vp]),
+        "dl_make_sources": (i, [vp, u64, i64, i, ctypes.c_uint, i, i, vp, P(i64)]),
+        "dl_make_point_sources": (i, [vp, i64, i, i, vp]),
         "dl_solve": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
         "dl_solve_adjoint": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
         "dl_apply_hop": (i, [vp, vp, vp, i]),
@@ -297,20 +297,41 @@ class Context:
         return dict(hop_ms=list(t.hop_ms), hop_launches=list(t.hop_launches), hop_bytes=list(t.hop_bytes),
                     kernel_launches=int(t.kernel_launches))
 
-    def make_sources(self, seed: int, noise_first: int, n_noise: int, dilution: int, t0: int = 0, out=None):
-        n_rhs = n_classes(dilution) * n_noise
+    def _source_out(self, n: int, prec: int, out, name="out"):
+        """A caller-owned output of n canonical fields in the storage of `prec`: complex128
+        (PREC_F64), complex64 (PREC_F32), or bfloat16 (re, im) pairs [n, T, Z, Y, X, 4, 3, 2]
+        (PREC_BF16)."""
+        torch = self._torch
+        lx, ly, lz, lt = self.dims
+        shape = (n, lt, lz, ly, lx, 4, 3)
+        dtype = {PREC_F64: torch.complex128, PREC_F32: torch.complex64, PREC_BF16: torch.bfloat16}.get(prec)
+        if dtype is None:
+            raise ValueError(f"unknown precision {prec}")
+        if prec == PREC_BF16:
+            shape = shape + (2,)
         if out is None:
-            out = self.new_fields(n_rhs)
-        elif self._field(out, "out") < n_rhs:
+            return torch.empty(shape, dtype=dtype, device=self.device)
+        if out.dtype != dtype or not out.is_contiguous() or out.device.type != "cuda":
+            raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+        if out.numel() < int(np.prod(shape)):
+            raise ValueError(f"{name} is too small")
+        return out
+
+    def make_sources(self, seed: int, noise_first: int, n_noise: int, dilution: int, t0: int = 0, out=None,
+                     prec: int = PREC_F64):
+        """Diluted complex Z2 sources (n_noise * classes fields), written by the library in the
+        storage of `prec` (complex128 by default; the solver takes complex128)."""
+        n_rhs = n_classes(dilution) * n_noise
+        if prec == PREC_F64 and out is not None and self._field(out, "out") < n_rhs:
             raise ValueError("out is too small")
-        _check(lib().dl_make_sources(self._h, seed, noise_first, n_noise, dilution, t0,
+        out = self._source_out(n_rhs, prec, out)
+        _check(lib().dl_make_sources(self._h, seed, noise_first, n_noise, dilution, t0, int(prec),
                                      ctypes.c_void_p(out.data_ptr()), None))
         return out
 
-    def make_point_sources(self, first: int, n: int, out=None):
-        if out is None:
-            out = self.new_fields(n)
-        _check(lib().dl_make_point_sources(self._h, first, n, ctypes.c_void_p(out.data_ptr())))
+    def make_point_sources(self, first: int, n: int, out=None, prec: int = PREC_F64):
+        out = self._source_out(n, prec, out)
+        _check(lib().dl_make_point_sources(self._h, first, n, int(prec), ctypes.c_void_p(out.data_ptr())))
         return out
 
     def _solve(self, fn, b, params, x, allow_fail):
@@ -368,11 +389,12 @@ class Context:
         return out
 
     def trace_loops(self, eta, phi, sink: int = SINK_LOCAL, smear=None, t_range=None, sum_rhs: bool = False,
-                    t_of_rhs=None, group: int | None = None):
+                    t_of_rhs=None, group: int | None = None, sum_t: bool = False):
         """Loops sum_{x in t} eta^dag Gamma phi: complex array [n/group][n_sinks][16][T].
 
         t_of_rhs: optional per-pair timeslice (time-diluted sources); group: sum
-        each run of `group` consecutive pairs (default 1, or n with sum_rhs).
+        each run of `group` consecutive pairs (default 1, or n with sum_rhs);
+        sum_t: the library sums the timeslices (last axis of length 1).
         """
         n = self._field(eta, "eta")
         if self._field(phi, "phi") != n:
@@ -382,13 +404,15 @@ class Context:
         if group is None:
             group = max(n, 1) if sum_rhs else 1
         n_sinks = (1 if sink & SINK_LOCAL else 0) + (1 if sink & SINK_SMEARED else 0)
-        out = np.zeros((max(n // group, 1) if sum_rhs else n // group, n_sinks, 16, T), dtype=np.complex128)
+        out = np.zeros((max(n // group, 1) if sum_rhs else n // group, n_sinks, 16, 1 if sum_t else T),
+                       dtype=np.complex128)
         sm = Smear(*smear) if smear is not None else None
         tarr = None
         if t_of_rhs is not None:
             tarr = (ctypes.c_int * n)(*[int(t) for t in t_of_rhs])
         _check(lib().dl_trace_loops(self._h, ctypes.c_void_p(eta.data_ptr()), ctypes.c_void_p(phi.data_ptr()), n,
-                                    sink, ctypes.byref(sm) if sm is not None else None, lo, hi, tarr, group,
+                                    sink | (SUM_T if sum_t else 0), ctypes.byref(sm) if sm is not None else None,
+                                    lo, hi, tarr, group,
                                     out.ctypes.data_as(ctypes.c_void_p)))
         return out
 

@@ -47,8 +47,8 @@ class LoopTrace(torch.autograd.Function):
         grad_kappa = None
         if fctx.needs_input_grad[1]:
             dphi = ctx.apply_hop(phi)
-            tr = ctx.trace_loops(chi, dphi, SINK_LOCAL, sum_rhs=True)
-            grad_kappa = torch.tensor(float(tr[0, 0, 0].sum().real), dtype=kappa.dtype, device=kappa.device)
+            tr = ctx.trace_loops(chi, dphi, SINK_LOCAL, sum_rhs=True, sum_t=True)  # sum_j chi_j^dag D phi_j
+            grad_kappa = torch.tensor(float(tr[0, 0, 0, 0].real), dtype=kappa.dtype, device=kappa.device)
         grad_eta = None
         if fctx.needs_input_grad[0]:
             grad_eta = ctx.apply_gamma_weights(phi, w, mode=1, out=chi, accumulate=True)

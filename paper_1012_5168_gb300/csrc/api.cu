@@ -1163,8 +1163,9 @@ extern "C" int dl_solve_adjoint(dl_ctx *c, const void *b, void *x, int n, const 
 // sources
 // ---------------------------------------------------------------------------
 extern "C" int dl_make_sources(dl_ctx *c, uint64_t seed, int64_t noise_first, int n_noise, unsigned dil, int t0,
-                               void *out, int64_t *n_rhs) {
+                               int prec, void *out, int64_t *n_rhs) {
     if (!c) return fail(DL_EINVAL, "null context");
+    if (prec < DL_PREC_F64 || prec > DL_PREC_BF16) return fail(DL_EINVAL, "unknown output precision");
     if (n_noise < 0 || noise_first < 0) return fail(DL_EINVAL, "negative noise range");
     if (dil & ~31u) return fail(DL_EINVAL, "unknown dilution bits");
     if ((dil & DL_DIL_TIME) && t0 >= c->dims[3]) return fail(DL_EINVAL, "t0 outside the lattice");
@@ -1188,20 +1189,25 @@ extern "C" int dl_make_sources(dl_ctx *c, uint64_t seed, int64_t noise_first, in
     if (!out) return fail(DL_EINVAL, "null output");
     c->cur = c->stream;
     Launch l = make_launch(c, (long)n_noise * K * c->V, 256, 0, 16);
-    z2_source_kernel<<<l.grid, l.block, 0, c->stream>>>(a, (double *)out);
+    if (prec == DL_PREC_F64) z2_source_kernel<double2><<<l.grid, l.block, 0, c->stream>>>(a, (double2 *)out);
+    else if (prec == DL_PREC_F32) z2_source_kernel<float2><<<l.grid, l.block, 0, c->stream>>>(a, (float2 *)out);
+    else z2_source_kernel<__nv_bfloat162><<<l.grid, l.block, 0, c->stream>>>(a, (__nv_bfloat162 *)out);
     c->kernel_launches++;
     CK(cudaGetLastError());
     return DL_OK;
 }
 
-extern "C" int dl_make_point_sources(dl_ctx *c, int64_t first, int n, void *out) {
+extern "C" int dl_make_point_sources(dl_ctx *c, int64_t first, int n, int prec, void *out) {
     if (!c) return fail(DL_EINVAL, "null context");
+    if (prec < DL_PREC_F64 || prec > DL_PREC_BF16) return fail(DL_EINVAL, "unknown output precision");
     if (n < 0 || first < 0 || first + n > 12 * c->V) return fail(DL_EINVAL, "point-source range outside 0..12V");
     if (n == 0) return DL_OK;
     if (!out) return fail(DL_EINVAL, "null output");
     c->cur = c->stream;
     Launch l = make_launch(c, (long)n * c->V * 12, 256, 0, 16);
-    point_source_kernel<<<l.grid, l.block, 0, c->stream>>>(first, n, c->V, (double *)out);
+    if (prec == DL_PREC_F64) point_source_kernel<double2><<<l.grid, l.block, 0, c->stream>>>(first, n, c->V, (double2 *)out);
+    else if (prec == DL_PREC_F32) point_source_kernel<float2><<<l.grid, l.block, 0, c->stream>>>(first, n, c->V, (float2 *)out);
+    else point_source_kernel<__nv_bfloat162><<<l.grid, l.block, 0, c->stream>>>(first, n, c->V, (__nv_bfloat162 *)out);
     c->kernel_launches++;
     CK(cudaGetLastError());
     return DL_OK;
@@ -1569,10 +1575,25 @@ __global__ void group_sum_kernel(const double2 *loops /* [sink][N][per] */, int 
     }
 }
 
+// out[r] = sum_t in[r][t] over T timeslices, in order (rows of [..][T])
+__global__ void sum_t_kernel(const double2 *in, int rows, int T, double2 *out) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int t = 0; t < T; ++t) {
+            const double2 v = in[(size_t)r * T + t];
+            re += v.x;
+            im += v.y;
+        }
+        out[r] = make_double2(re, im);
+    }
+}
+
 extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n_rhs, int sink, const dl_smear *sm,
                               int t_lo, int t_hi, const int *t_of_rhs, int group, double *host_out) {
     if (!c) return fail(DL_EINVAL, "null context");
     if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    const bool sum_t = (sink & DL_SUM_T) != 0;
+    sink &= ~DL_SUM_T;
     if (!(sink & (DL_SINK_LOCAL | DL_SINK_SMEARED)) || (sink & ~3)) return fail(DL_EINVAL, "bad sink mask");
     if ((sink & DL_SINK_SMEARED) && !sm) return fail(DL_EINVAL, "smeared sink needs smearing parameters");
     if ((sink & DL_SINK_SMEARED) && !c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
@@ -1586,6 +1607,7 @@ extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n
             if (t_of_rhs[j] < 0 || t_of_rhs[j] >= T) return fail(DL_EINVAL, "t_of_rhs entry outside the lattice");
     const int n_sinks = ((sink & DL_SINK_LOCAL) ? 1 : 0) + ((sink & DL_SINK_SMEARED) ? 1 : 0);
     const int per = 16 * T;
+    const int per_out = sum_t ? 16 : per;  // values per (group, sink) written to host_out
     if (n_rhs == 0) return DL_OK;
     if (!eta || !phi) return fail(DL_EINVAL, "null field pointer");
     // A batch (layout width N) holds whole groups when a group fits in 64 right-hand
@@ -1623,10 +1645,18 @@ extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n
             group_sum_kernel<<<std::max(1, (ng * n_sinks * per + 255) / 256), 256, 0, c->stream>>>(
                 c->d_loops, n, N, group, n_sinks, per, c->d_acc2);
             c->kernel_launches++;
-            CK(cudaMemcpyAsync(h.data(), c->d_acc2, sizeof(double2) * (size_t)ng * n_sinks * per,
+            const double2 *res = c->d_acc2;
+            if (sum_t) {  // d_loops is free again: it takes the timeslice sums
+                sum_t_kernel<<<std::max(1, (ng * n_sinks * 16 + 255) / 256), 256, 0, c->stream>>>(
+                    c->d_acc2, ng * n_sinks * 16, T, c->d_loops);
+                c->kernel_launches++;
+                res = c->d_loops;
+            }
+            CK(cudaMemcpyAsync(h.data(), res, sizeof(double2) * (size_t)ng * n_sinks * per_out,
                                cudaMemcpyDeviceToHost, c->stream));
             TRY(sync(c));
-            memcpy(host_out + (size_t)g_done * n_sinks * per * 2, h.data(), sizeof(double2) * (size_t)ng * n_sinks * per);
+            memcpy(host_out + (size_t)g_done * n_sinks * per_out * 2, h.data(),
+                   sizeof(double2) * (size_t)ng * n_sinks * per_out);
             g_done += ng;
         } else {
             for (int s = 0; s < n_sinks; ++s) {
@@ -1636,8 +1666,14 @@ extern "C" int dl_trace_loops(dl_ctx *c, const void *eta, const void *phi, int n
                 c->kernel_launches += 2;
             }
             if ((j0 + n) % group == 0) {  // a group is complete
-                CK(cudaMemcpyAsync(host_out + (size_t)g_done * n_sinks * per * 2, dsum,
-                                   sizeof(double2) * n_sinks * per, cudaMemcpyDeviceToHost, c->stream));
+                const double2 *res = dsum;
+                if (sum_t) {
+                    sum_t_kernel<<<1, 64, 0, c->stream>>>(dsum, n_sinks * 16, T, c->d_acc2);
+                    c->kernel_launches++;
+                    res = c->d_acc2;
+                }
+                CK(cudaMemcpyAsync(host_out + (size_t)g_done * n_sinks * per_out * 2, res,
+                                   sizeof(double2) * n_sinks * per_out, cudaMemcpyDeviceToHost, c->stream));
                 TRY(sync(c));
                 zero_kernel<<<std::max(1, (2 * per + 255) / 256), 256, 0, c->stream>>>(dsum, 2 * per);
                 ++g_done;
@@ -1831,7 +1867,7 @@ extern "C" int dl_exact_loops(dl_ctx *c, int64_t src_first, int64_t n_src, const
     std::vector<OuterState> os;
     for (int64_t s0 = src_first; s0 < src_first + n_src; s0 += N) {
         const int n = (int)std::min<int64_t>(N, src_first + n_src - s0);
-        TRY(dl_make_point_sources(c, s0, n, c->d_canon));
+        TRY(dl_make_point_sources(c, s0, n, DL_PREC_F64, c->d_canon));
         TRY(canon_to_eo(c, c->d_canon, c->b64, n, N, 0, 0, (int)c->Vh));
         TRY(solve_batch(c, n, N, P, os));
         for (int j = 0; j < n; ++j) {
@@ -1979,7 +2015,7 @@ static int tsm_pass(dl_ctx *c, uint64_t seed, int64_t first, int count, unsigned
             a.k_first = (int)(lo - nv * K);
             a.k_count = (int)(hi - lo);
             Launch l = make_launch(c, (long)a.k_count * c->V, 256, 0, 16);
-            z2_source_kernel<<<l.grid, l.block, 0, c->stream>>>(a, c->d_canon + (size_t)(lo - r0) * field);
+            z2_source_kernel<double2><<<l.grid, l.block, 0, c->stream>>>(a, (double2 *)(c->d_canon + (size_t)(lo - r0) * field));
             c->kernel_launches++;
         }
         CK(cudaGetLastError());

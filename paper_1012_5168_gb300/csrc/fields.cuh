@@ -155,7 +155,22 @@ struct SourceArgs {
 };
 
 // thread = (rhs, p, cb): one site of one diluted source, canonical output
-static __global__ void z2_source_kernel(SourceArgs a, double *out) {
+// One complex value of a canonical field in output storage O (double2: complex128,
+// float2: complex64, bf16 pairs); the value is rounded from FP64 (to float first
+// for BF16, the way the solver rounds its fields).
+template <typename O> __device__ __forceinline__ void put_cx(O *dst, double re, double im);
+template <> __device__ __forceinline__ void put_cx<double2>(double2 *dst, double re, double im) {
+    *dst = make_double2(re, im);
+}
+template <> __device__ __forceinline__ void put_cx<float2>(float2 *dst, double re, double im) {
+    *dst = make_float2((float)re, (float)im);
+}
+template <> __device__ __forceinline__ void put_cx<__nv_bfloat162>(__nv_bfloat162 *dst, double re, double im) {
+    *dst = __floats2bfloat162_rn((float)re, (float)im);
+}
+
+template <typename O>
+static __global__ void z2_source_kernel(SourceArgs a, O *out) {
     const long nsite = 2L * a.g.Vh;
     const long total = (long)a.n_noise * a.k_count * nsite;
     const double s2 = sqrt(0.5);  // 1/sqrt(2), rounded once
@@ -180,28 +195,29 @@ static __global__ void z2_source_kernel(SourceArgs a, double *out) {
             const int tn = a.t0 >= 0 ? a.t0 : (int)(n % a.g.L[3]);
             site_on &= (st.c[3] == tn);
         }
-        double2 *dst = (double2 *)(out + ((size_t)rhs * 2 * a.g.Vh + st.i) * 24);
+        O *dst = out + ((size_t)rhs * 2 * a.g.Vh + st.i) * 12;
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             const int alpha = c / 3, col = c % 3;
             const bool on = site_on && (a.dil_spin == 1 || alpha == ks) && (a.dil_colour == 1 || col == kc);
-            double2 v = make_double2(0.0, 0.0);
+            double re = 0.0, im = 0.0;
             if (on) {
-                v.x = ((w >> (2 * c)) & 1) ? -s2 : s2;
-                v.y = ((w >> (2 * c + 1)) & 1) ? -s2 : s2;
+                re = ((w >> (2 * c)) & 1) ? -s2 : s2;
+                im = ((w >> (2 * c + 1)) & 1) ? -s2 : s2;
             }
-            dst[c] = v;
+            put_cx<O>(dst + c, re, im);
         }
     }
 }
 
 // point sources e_s, s = first + j, s = 12 i + c: canonical output, n fields
-static __global__ void point_source_kernel(int64_t first, int n, long V, double *out) {
+template <typename O>
+static __global__ void point_source_kernel(int64_t first, int n, long V, O *out) {
     const long total = (long)n * V * 12;
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         const long j = idx / (V * 12);
         const long e = idx % (V * 12);
-        ((double2 *)out)[idx] = make_double2(e == first + j ? 1.0 : 0.0, 0.0);
+        put_cx<O>(out + idx, e == first + j ? 1.0 : 0.0, 0.0);
     }
 }
 

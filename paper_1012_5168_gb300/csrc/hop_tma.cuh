@@ -42,6 +42,9 @@ __device__ __forceinline__ void bulk_copy(void *dst_smem, const void *src, uint3
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(

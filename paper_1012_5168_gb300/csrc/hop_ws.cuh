@@ -204,9 +204,15 @@ __global__ void __launch_bounds__(WS_WARPS * 32) hop_kernel_ws(HopArgs A) {
         }
         __syncwarp();
     }
+    // No copy of this warp is pending now (all waited, or drained): retire its barriers.
+    __syncwarp();
+    if (lane == 0)
+        for (int i = 0; i < NST; ++i) mbar_inval(full + i);
     if (RED != RED_NONE) {
-        __syncthreads();  // every warp's copies have landed: the reduction reuses the staging memory
-        block_reduce<R, NV, T>(red, 32, N, A.partials, smem);
+        // Every warp's copies have landed: the reduction reuses warp 0's staging
+        // memory (WS_WARPS * 32 * R * NV complex, below one warp's NST * SB bytes).
+        __syncthreads();
+        block_reduce<R, NV, T>(red, 32, N, A.partials, smem + 64);
     }
 }
 

@@ -43,6 +43,13 @@ def test_trace_loops_local_and_smeared(lib, dims):
     assert np.abs(got[:, 1] - ref_s).max() < 1e-12 * np.abs(ref_s).max()
     summed = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL, sum_rhs=True)
     assert np.abs(summed[0, 0] - ref_l.sum(0)).max() < 1e-12 * np.abs(ref_l).max()
+    # the library's timeslice sums, per pair and over all pairs
+    tot = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL | lib.SINK_SMEARED, smear=(4.0, 6), sum_t=True)
+    assert tot.shape == (5, 2, 16, 1)
+    assert np.abs(tot[:, 0, :, 0] - ref_l.sum(-1)).max() < 1e-12 * np.abs(ref_l.sum(-1)).max()
+    assert np.abs(tot[:, 1, :, 0] - ref_s.sum(-1)).max() < 1e-12 * np.abs(ref_s.sum(-1)).max()
+    both = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL, sum_rhs=True, sum_t=True)
+    assert np.abs(both[0, 0, :, 0] - ref_l.sum((0, -1))).max() < 1e-12 * np.abs(ref_l.sum((0, -1))).max()
     part = c.trace_loops(to_gpu(eta), to_gpu(phi), lib.SINK_LOCAL, t_range=(1, 3))
     assert np.all(part[:, 0, :, 0] == 0) and np.abs(part[:, 0, :, 1:3] - ref_l[:, :, 1:3]).max() < 1e-12 * np.abs(ref_l).max()
     c.close()

@@ -107,7 +107,33 @@ def test_point_sources(lib):
     dims = (2, 2, 2, 4)
     c, _ = ctx_for(lib, dims)
     got = c.make_point_sources(17, 40).cpu().numpy()
-    assert np.array_equal(got, noise.point_sources(dims, 17, 40))
+    ref = noise.point_sources(dims, 17, 40)
+    assert np.array_equal(got, ref)
+    assert np.array_equal(c.make_point_sources(17, 40, prec=lib.PREC_F32).cpu().numpy(), ref.astype(np.complex64))
+    bf = c.make_point_sources(17, 40, prec=lib.PREC_BF16).float().cpu().numpy()
+    assert np.array_equal(bf[..., 0] + 1j * bf[..., 1], ref)
+    c.close()
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """float64 -> float32 (nearest) -> bfloat16 (nearest, ties to even), returned as float32."""
+    f = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    f = (f + 0x7FFF + ((f >> 16) & 1)) & 0xFFFF0000
+    return f.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("dil", [0, 1 | 2 | 4 | 16])
+def test_sources_in_working_precision(lib, dil):
+    """complex64 and bfloat16 sources are the oracle's complex128 values rounded to nearest."""
+    dims = (4, 4, 2, 6)
+    c, _ = ctx_for(lib, dims)
+    ref = noise.make_sources(dims, 77, 2, 3, dil, t0=-1)
+    f32 = c.make_sources(seed=77, noise_first=2, n_noise=3, dilution=dil, t0=-1, prec=lib.PREC_F32).cpu().numpy()
+    assert f32.dtype == np.complex64 and np.array_equal(f32, ref.astype(np.complex64))
+    bf = c.make_sources(seed=77, noise_first=2, n_noise=3, dilution=dil, t0=-1, prec=lib.PREC_BF16)
+    bf = bf.float().cpu().numpy()
+    assert np.array_equal(bf[..., 0], bf16_round(ref.real)) and np.array_equal(bf[..., 1], bf16_round(ref.imag))
+    assert set(np.unique(np.abs(bf))) <= {0.0, float(bf16_round(np.array([np.sqrt(0.5)]))[0])}
     c.close()
 
 
