@@ -84,6 +84,7 @@ struct dl_ctx {
     bool smear_fp64 = false;       // smear in native FP64 instead of float-float
     float *d_gauge8_32 = nullptr;  // site-major links (staged hop)
     bf16 *d_gauge8_16 = nullptr;
+    float4 *d_gauge8q = nullptr;   // FP32 link quads of the packed-arithmetic hop
     int *h_err = nullptr;          // pinned, mapped [2]: set by the staged hop on a wait timeout
     int *d_err = nullptr;
     bool poisoned = false;         // a staged hop may have left bulk copies pending: no further work
@@ -127,7 +128,8 @@ struct dl_ctx {
     int64_t kernel_launches = 0;
     int hop_R[3][8];      // right-hand sides per thread, [prec][log2 N]
     int hop_block[3][8];  // threads per block
-    int hop_kind[3][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged
+    int hop_kind[3][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
+                          // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic
     bool hop_tuned[3][8];
     bool autotune = true;
 };
@@ -231,6 +233,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.gauge8 = prec == P_F32 ? (const void *)c->d_gauge8_32 : (prec == P_BF16 ? (const void *)c->d_gauge8_16 : nullptr);
     a.err = c->d_err;
     a.blocked = 0;
+    a.gauge8q = c->d_gauge8q;
     int R = wide ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
@@ -253,7 +256,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     }
     Launch l = make_launch(c, items, block, smem, kind == 0 ? 16 : per_sm);
     // the direct and warp-staged kernels size their grid from residency
-    if (kind == 0 || kind == 3 || kind == 4) l.num_sms = c->num_sms;
+    if (kind == 0 || kind >= 3) l.num_sms = c->num_sms;
     const bool timed = c->timing;
     TimedPair tp;
     if (timed) {
@@ -418,7 +421,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // shape timed while the GPU was still ramping its clocks or finishing other
     // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 5); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 7); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
@@ -428,8 +431,10 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                 const int B = Bs[bi];
                 if (B % (N / R) || (force_block && B != force_block)) continue;
                 if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
-                if ((pf == 3 || pf == 4) && bi > 0) continue;  // the launcher picks the block
-                if (pf == 4 && N != 32 * R) continue;          // warp-staged: one site per warp
+                if ((pf == 3 || pf == 4 || pf == 5) && bi > 0) continue;  // the launcher picks the block
+                if ((pf == 4 || pf == 5) && N != 32 * R) continue;         // one site per warp
+                if (pf == 5 && (prec != P_BF16 || R > 2)) continue;         // tensor cores: BF16 storage
+                if (pf == 6 && (prec != P_F32 || R != 1)) continue;         // packed FP32 arithmetic
                 if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
                 c->hop_R[prec][l] = R;
                 c->hop_block[prec][l] = B;
@@ -633,7 +638,7 @@ extern "C" int dl_destroy(dl_ctx *c) {
         cudaEventDestroy(tp.a);
         cudaEventDestroy(tp.b);
     }
-    void *ptrs[] = {c->d_coords,   c->d_gauge64, c->d_gauge32,  c->d_gauge16, c->d_gauge8_32, c->d_gauge8_16,
+    void *ptrs[] = {c->d_coords,   c->d_gauge64, c->d_gauge32,  c->d_gauge16, c->d_gauge8_32, c->d_gauge8_16, c->d_gauge8q,
                     c->d_gauge_ff, c->d_gammas,  c->d_partials, c->d_acc,     c->d_noise,     c->d_w,
                     c->d_tcol,     c->d_acc2};
     for (void *p : ptrs)
@@ -675,6 +680,7 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
             cudaMalloc((void **)&c->d_gauge16, n64 * sizeof(bf16)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge8_32, 2 * n64 * sizeof(float)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge8_16, 2 * n64 * sizeof(bf16)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge8q, (size_t)c->V * 72 * sizeof(float4)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge_ff, 2 * n64 * sizeof(float)) != cudaSuccess)
             return fail(DL_ENOMEM, "gauge allocation failed");
     }
@@ -691,8 +697,9 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
         gauge_reorder_kernel<bf16><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge16);
         gauge8_kernel<float><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8_32);
         gauge8_kernel<bf16><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8_16);
+        gauge8q_kernel<<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8q);
         gauge_ff_kernel<<<grid, 256, 0, c->stream>>>(c->d_gauge64, c->d_gauge_ff, (long)n64 / 2);
-        c->kernel_launches += 6;
+        c->kernel_launches += 7;
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
             rc = fail(DL_ECUDA, "gauge reorder failed");
     }

@@ -89,6 +89,33 @@ static __global__ void gauge_reorder_kernel(const uint32_t *coords, Geom g, cons
 // gauge, site-major with all eight links of a site in one row: for site x of
 // parity p, row d = 2 mu holds U_mu(x) and row d = 2 mu + 1 holds U_mu(x - mu)
 // (not conjugated).  Out: [2][Vh][8][9] complex in S.
+// The packed-arithmetic hop's links: per output site the eight links of its
+// hop directions (d = 2 mu: U_mu(x); d = 2 mu + 1: V = U_mu(x - mu)^dag, the
+// conjugate transpose taken here), each element V[a][b] stored as the FP32
+// quad (Re V, Re V, -Im V, Im V).
+static __global__ void gauge8q_kernel(const uint32_t *coords, Geom g, const double *canon, float4 *out) {
+    const int total = 2 * g.Vh;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const Site st = decode(coords[idx], g);
+        for (int d = 0; d < 8; ++d) {
+            const int mu = d >> 1;
+            int src = st.i;
+            if (d & 1) {
+                src = st.i - g.stride[mu];
+                if (st.c[mu] == 0) src += g.L[mu] * g.stride[mu];
+            }
+            const double2 *u = (const double2 *)(canon + ((size_t)src * 4 + mu) * 18);
+            float4 *dst = out + ((size_t)idx * 8 + d) * 9;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const double2 z = (d & 1) ? make_double2(u[b * 3 + a].x, -u[b * 3 + a].y) : u[a * 3 + b];
+                    const float re = (float)z.x, im = (float)z.y;
+                    dst[a * 3 + b] = make_float4(re, re, -im, im);
+                }
+        }
+    }
+}
+
 template <typename S>
 __global__ void gauge8_kernel(const uint32_t *coords, Geom g, const double *canon, S *out) {
     typedef typename Real<S>::type T;

@@ -57,6 +57,8 @@ struct HopArgs {
     const void *gauge8;     // [2][Vh][8][9] complex, site-major links (staged kernel)
     int *err;               // [2]: the staged kernel sets [0] when a bounded wait runs out, [1] when a drain wait does too
     int blocked;            // direct kernel: 0 cyclic site mapping, 1 one contiguous range per block
+    const float4 *gauge8q;  // [2][Vh][8][9] FP32 quads (Re V, Re V, -Im V, Im V), V = U (forward) or U^dag
+                            // (backward, already conjugated): the packed-arithmetic kernel's links
 };
 
 // Load the 12 components of R right-hand sides at one neighbour site and
@@ -192,10 +194,85 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed FP32 arithmetic (sm_100 and later: one FFMA2 / FADD2 instruction does
+// two FP32 operations).  A complex value is an FP32 pair (re, im); with the
+// link element stored as the quads (Re V, Re V) and (-Im V, Im V),
+//   w += V h  is  w = ffma2((Re V, Re V), (Re h, Im h), w)
+//                 w = ffma2((-Im V, Im V), (Im h, Re h), w),
+// the same four FMAs in the same order as cmac/cjmac of the scalar kernel, so
+// the results agree bit for bit; the instruction count of the SU(3) products
+// and of the real-valued reconstructions halves.  Backward links are stored
+// already conjugated, so every direction is a plain product.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+// acc += [ w ; s X_mu^dag w ] on FP32 pairs (s = S); the i-rotations stay scalar.
+template <int MU, int S>
+__device__ __forceinline__ void reconstruct_x2(const float2 (&w)[6], float2 (&acc)[12]) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float2 w0 = w[a], w1 = w[3 + a];
+        acc[a] = __fadd2_rn(acc[a], w0);
+        acc[3 + a] = __fadd2_rn(acc[3 + a], w1);
+        float2 &l6 = acc[6 + a], &l9 = acc[9 + a];
+        if (MU == 0) {        // X^dag w = (-i w1, -i w0); -i z = (z.im, -z.re)
+            l6 = S > 0 ? make_float2(l6.x + w1.y, l6.y - w1.x) : make_float2(l6.x - w1.y, l6.y + w1.x);
+            l9 = S > 0 ? make_float2(l9.x + w0.y, l9.y - w0.x) : make_float2(l9.x - w0.y, l9.y + w0.x);
+        } else if (MU == 1) { // X^dag w = (w1, -w0)
+            l6 = S > 0 ? __fadd2_rn(l6, w1) : __ffma2_rn(m1, w1, l6);
+            l9 = S > 0 ? __ffma2_rn(m1, w0, l9) : __fadd2_rn(l9, w0);
+        } else if (MU == 2) { // X^dag w = (-i w0, i w1); i z = (-z.im, z.re)
+            l6 = S > 0 ? make_float2(l6.x + w0.y, l6.y - w0.x) : make_float2(l6.x - w0.y, l6.y + w0.x);
+            l9 = S > 0 ? make_float2(l9.x - w1.y, l9.y + w1.x) : make_float2(l9.x + w1.y, l9.y - w1.x);
+        } else {              // X^dag w = (w0, w1)
+            l6 = S > 0 ? __fadd2_rn(l6, w0) : __ffma2_rn(m1, w0, l6);
+            l9 = S > 0 ? __fadd2_rn(l9, w1) : __ffma2_rn(m1, w1, l9);
+        }
+    }
+}
+
+// One hop direction D = 2 MU (+1 backward) of the packed kernel.
+template <int MU, int SG, int NC>
+__device__ __forceinline__ void hop_dir_x2(const HopArgs &A, const Site &st, int cb, int r0, float2 (&acc)[12]) {
+    const float *in = reinterpret_cast<const float *>(A.in);
+    const size_t N = NC ? (size_t)NC : (size_t)A.N;
+    constexpr int D = 2 * MU + (SG > 0 ? 1 : 0);
+    const int nb = SG < 0 ? nbr_fwd(st, A.g, MU) : nbr_bwd(st, A.g, MU);
+    const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == (SG < 0 ? A.g.L[3] - 1 : 0));
+    const float *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;
+    cx<float> hh[1][6];
+    load_project<float, 1, MU, SG>(src, N, hh);
+    float2 h[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) h[k] = flip ? make_float2(-hh[0][k].re, -hh[0][k].im) : make_float2(hh[0][k].re, hh[0][k].im);
+    const float4 *q = A.gauge8q + (((size_t)A.p * A.g.Vh + cb) * 8 + D) * 9;
+    float2 w[6];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        float4 v[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) v[b] = __ldg(q + a * 3 + b);
+#pragma unroll
+        for (int sp = 0; sp < 2; ++sp) {
+            float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float2 hb = h[3 * sp + b];
+                acc2 = __ffma2_rn(make_float2(v[b].x, v[b].y), hb, acc2);
+                acc2 = __ffma2_rn(make_float2(v[b].z, v[b].w), swap2(hb), acc2);
+            }
+            w[3 * sp + a] = acc2;
+        }
+    }
+    reconstruct_x2<MU, SG>(w, acc);
+}
+
 // NC > 0: the number of right-hand sides in the layout is the compile-time
 // constant NC (= A.N), so component offsets fold into the load and store
 // instructions; NC = 0 reads it from A.N.
-template <typename S, int R, int MODE, int RED, int NC = 0>
+template <typename S, int R, int MODE, int RED, int NC = 0, int X2 = 0>
 __device__ __forceinline__ void hop_body(const HopArgs &A) {
     typedef typename Real<S>::type T;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
@@ -229,14 +306,30 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
         const int r0 = (idx & (G - 1)) * R;
         const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
         cx<T> acc[R][12];
+        if constexpr (X2 != 0 && sizeof(S) == 4 && R == 1) {
+            float2 a2[12];
 #pragma unroll
-        for (int r = 0; r < R; ++r)
+            for (int c = 0; c < 12; ++c) a2[c] = make_float2(0.f, 0.f);
+            hop_dir_x2<0, -1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<0, +1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<1, -1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<1, +1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<2, -1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<2, +1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<3, -1, NC>(A, st, cb, r0, a2);
+            hop_dir_x2<3, +1, NC>(A, st, cb, r0, a2);
 #pragma unroll
-            for (int c = 0; c < 12; ++c) acc[r][c] = zero<T>();
-        hop_dir<S, R, 0, NC>(A, st, cb, r0, acc);
-        hop_dir<S, R, 1, NC>(A, st, cb, r0, acc);
-        hop_dir<S, R, 2, NC>(A, st, cb, r0, acc);
-        hop_dir<S, R, 3, NC>(A, st, cb, r0, acc);
+            for (int c = 0; c < 12; ++c) acc[0][c] = mk((T)a2[c].x, (T)a2[c].y);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+                for (int c = 0; c < 12; ++c) acc[r][c] = zero<T>();
+            hop_dir<S, R, 0, NC>(A, st, cb, r0, acc);
+            hop_dir<S, R, 1, NC>(A, st, cb, r0, acc);
+            hop_dir<S, R, 2, NC>(A, st, cb, r0, acc);
+            hop_dir<S, R, 3, NC>(A, st, cb, r0, acc);
+        }
 
         const size_t base = (size_t)cb * 12 * N * 2 + (size_t)r0 * 2;
         S *out = reinterpret_cast<S *>(A.out);
@@ -310,6 +403,12 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
 template <typename S, int R, int MODE, int RED, int CAP, int NC = 0>
 __global__ void __maxnreg__(CAP) hop_kernel_cap(HopArgs A) {
     hop_body<S, R, MODE, RED, NC>(A);
+}
+
+// Packed-arithmetic direct kernel (FP32 storage, one right-hand side per thread).
+template <int MODE, int RED, int CAP, int NC = 0>
+__global__ void __maxnreg__(CAP) hop_kernel_x2(HopArgs A) {
+    hop_body<float, 1, MODE, RED, NC, 1>(A);
 }
 
 

@@ -1,7 +1,7 @@
 // Launch of one Wilson-hop instantiation for a low-precision storage type S
 // (float or bf16): the kernel kind picks the direct, prefetching, staged or
-// blocked-mapping or warp-staged kernel.  hop_f32*.cu and hop_bf16*.cu
-// instantiate it.  The
+// blocked-mapping, warp-staged or (BF16 only) tensor-core kernel.  hop_f32*.cu
+// and hop_bf16*.cu instantiate it.  The
 // one-time settings (shared-memory opt-ins, the blocked kernel's block shape)
 // are guarded so that contexts used from several host threads can launch
 // concurrently.
@@ -9,7 +9,9 @@
 
 #include <mutex>
 
-#include "hop_ws.cuh"
+#include <type_traits>
+
+#include "hop_mma.cuh"
 #include "launch.h"
 
 namespace dl {
@@ -95,6 +97,35 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
         l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (res < 16 ? res : 16);
         kern<<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
+    }
+    if (kind == 6) {  // direct loads, packed FP32 arithmetic (FP32 storage, R = 1)
+        if constexpr (std::is_same<S, float>::value && R == 1) {
+            constexpr int xcap = MODE == MODE_PLAIN ? 64 : 72;
+            if (a.N == 32) {
+                clamp_grid(l, resident_blocks(hop_kernel_x2<MODE, RED, xcap, 32>, l.block, l.smem));
+                hop_kernel_x2<MODE, RED, xcap, 32><<<l.grid, l.block, l.smem, l.stream>>>(a);
+            } else {
+                clamp_grid(l, resident_blocks(hop_kernel_x2<MODE, RED, xcap>, l.block, l.smem));
+                hop_kernel_x2<MODE, RED, xcap><<<l.grid, l.block, l.smem, l.stream>>>(a);
+            }
+            return cudaGetLastError();
+        }
+    }
+    if (kind == 5) {  // tensor cores, BF16 storage only; one site per warp, N = 32 R
+        if constexpr (std::is_same<S, bf16>::value && (R == 1 || R == 2)) {
+            if (a.N != 32 * R) return cudaErrorInvalidValue;
+            static size_t opted = 0;
+            static std::mutex m;
+            auto kern = hop_kernel_mma<R, MODE, RED>;
+            l.block = WS_WARPS * 32;
+            l.smem = MmaShape<R>::SMEM;
+            const cudaError_t e = opt_in_smem(kern, l.smem, opted, m);
+            if (e != cudaSuccess) return e;
+            const int res = resident_blocks(kern, l.block, l.smem);
+            l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (res < 16 ? res : 16);
+            kern<<<l.grid, l.block, l.smem, l.stream>>>(a);
+            return cudaGetLastError();
+        }
     }
     return cudaErrorInvalidValue;
 }

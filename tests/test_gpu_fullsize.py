@@ -80,25 +80,47 @@ def test_low_precision_hop_error_every_kernel(lib, prec):
         assert err < HOP_BOUND[prec]
     exact = c.apply_hop(to_gpu(psi)).cpu().numpy()  # the FP64 hop of the same context
     assert hop_error(exact, ref) < 1e-14
-    # the warp-staged kernel serves widths 32 and 64 only
-    for n in (32, 64):
-        wide = synthetic.random_spinor(dims, seed=43, n=n)
-        ref_w = wilson.hop(U, wide[[0, n - 1]], -1.0)
-        R, B, k, _ = c.tune_hop(prec, n, force_pf=4)
-        assert k == 4
-        got = c.apply_hop(to_gpu(wide), precision=prec).cpu().numpy()[[0, n - 1]]
-        err = hop_error(got, ref_w)
-        print(f"hop prec {prec} kind 4 width {n} (R {R}): max error {err:.3e} of max|D psi|")
-        assert err < HOP_BOUND[prec]
+    # the warp-staged kernels serve widths 32 and 64 only; kind 5 (tensor cores) BF16 only
+    for kind in ((4, 5) if prec == 2 else (4,)):
+        for n in (32, 64):
+            wide = synthetic.random_spinor(dims, seed=43, n=n)
+            ref_w = wilson.hop(U, wide, -1.0)
+            R, B, k, _ = c.tune_hop(prec, n, force_pf=kind)
+            assert k == kind
+            got = c.apply_hop(to_gpu(wide), precision=prec).cpu().numpy()
+            err = hop_error(got, ref_w)
+            print(f"hop prec {prec} kind {kind} width {n} (R {R}): max error {err:.3e} of max|D psi|")
+            assert err < HOP_BOUND[prec]
     c.close()
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_low_precision_hop_error_full_size(lib, full, prec):
-    """16^3 x 32 at the bench width of 32 right-hand sides, in the tuned launch shape; fields 0 and 31
-    against the FP64 oracle hop on every site."""
+@pytest.mark.parametrize("n", [7, 32])
+def test_packed_fp32_hop_is_bitwise_the_scalar_hop(lib, n):
+    """Kind 6 (packed FP32 pairs, FFMA2) performs the scalar kernel's FMAs in the same order, so its
+    hop equals the scalar direct kernel's (one right-hand side per thread) bit for bit, and both sit
+    within the FP32 bound of the FP64 oracle hop."""
+    dims = (6, 4, 4, 8)
+    U = synthetic.gauge_field(dims, eps=0.45, seed=44)
+    c = lib.Context(dims, t_bc=-1)
+    c.load_gauge(U)
+    psi = to_gpu(synthetic.random_spinor(dims, seed=45, n=n))
+    width = 8 if n == 7 else 32
+    c.tune_hop(1, width, force_R=1, force_pf=0)
+    scalar = c.apply_hop(psi, precision=1).cpu().numpy()
+    R, B, k, _ = c.tune_hop(1, width, force_pf=6)
+    assert k == 6 and R == 1
+    packed = c.apply_hop(psi, precision=1).cpu().numpy()
+    assert np.array_equal(packed, scalar)
+    assert hop_error(packed, wilson.hop(U, psi.cpu().numpy(), -1.0)) < HOP_BOUND[1]
+    c.close()
+
+
+@pytest.mark.parametrize("prec, kind", [(1, -1), (1, 6), (2, -1), (2, 5)])
+def test_low_precision_hop_error_full_size(lib, full, prec, kind):
+    """16^3 x 32 at the bench width of 32 right-hand sides, in the tuned launch shape (kind -1) or on
+    the tensor cores (kind 5, BF16); fields 0 and 31 against the FP64 oracle hop on every site."""
     c, U = full
-    c.tune_hop(prec, 32)
+    c.tune_hop(prec, 32, force_pf=kind)
     eta = c.make_sources(seed=11, noise_first=0, n_noise=32, dilution=0)
     got = c.apply_hop(eta, precision=prec)
     for j in (0, 31):

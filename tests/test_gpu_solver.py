@@ -190,11 +190,12 @@ def test_hop_kernel_kinds(lib, prec, kind, batch):
     c.close()
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec, kind", [(1, 4), (2, 4), (2, 5), (1, 6)])
 @pytest.mark.parametrize("batch", [32, 64])
-def test_warp_staged_hop_solves(lib, prec, batch):
-    """The warp-staged hop (one site per warp, N = 32 R) at the two widths it serves, with a ragged
-    last batch, solves to tolerance.  8^3 x 24 has more even sites (6144) than a 152-SM GPU runs warps of
+def test_warp_staged_hop_solves(lib, prec, kind, batch):
+    """The warp-staged hops (one site per warp, N = 32 R: kind 4 on the CUDA cores, kind 5 on the
+    tensor cores for BF16) and the packed-FP32 direct hop (kind 6) at widths 32 and 64, with a ragged
+    last batch, solve to tolerance.  8^3 x 24 has more even sites (6144) than a 152-SM GPU runs warps of
     this kernel (at most 2432), so every warp walks several sites and reuses its stages and link rows."""
     dims, kappa = (8, 8, 8, 24), 0.12
     U = synthetic.gauge_field(dims, eps=0.45, seed=9)
@@ -203,8 +204,8 @@ def test_warp_staged_hop_solves(lib, prec, batch):
     c.set_kappa(kappa)
     b = synthetic.random_spinor(dims, seed=22, n=batch + 3)
     k = [0, batch - 1, batch, batch + 2]  # fields checked with the oracle's M
-    R, B, kind, _ = c.tune_hop(prec, batch, force_pf=4)
-    assert kind == 4 and R == batch // 32
+    R, B, got_kind, _ = c.tune_hop(prec, batch, force_pf=kind)
+    assert got_kind == kind and R == (1 if kind == 6 else batch // 32)
     x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=prec, batch=batch))
     assert all(s["status"] == 0 and s["true_residual"] <= 1e-11 for s in st), st
     res = residual(U, x.cpu().numpy()[k], b[k], kappa)
