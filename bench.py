@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--workload", default="stochastic",
                     choices=["stochastic", "exact_4x4x4x4", "single_rhs_16x16x16x32", "tsm_8x8x8x16",
                              "autograd", "correlators_16x16x16x32", "dilution_8x8x8x16",
-                             "batch_scan_16x16x16x32"],
+                             "batch_scan_16x16x16x32", "tsm_16x16x16x32"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--smear-profile", metavar="N", type=int, default=None,
@@ -458,6 +458,58 @@ def workload_tsm():
     print(json.dumps(out), flush=True)
 
 
+def workload_tsm_paper():
+    """The truncated solver method at the paper's sizes (Sec. 2): 5000 low-precision solves
+    (single-precision CG on the normal equations, tolerance 1e-6) and 500 high-precision corrections
+    (FP32 inner with FP64 defect correction, 1e-10) on 16^3 x 32, complex Z2 noise, time dilution by
+    translation (t0 = n mod T; the paper states no dilution for this ensemble).  No exact loops exist
+    at this volume (12V = 1.57 million solves), so the report is the estimate per Gamma with its
+    error, the share of the variance from the low-precision ensemble and from the correction, and
+    the bias the correction removed (<L_HP - L_LP> against its error)."""
+    import numpy as np
+    import torch
+    import paper_1012_5168_gb300 as dl
+    ctx, U, w = _ctx(dl, "wilson_16x16x16x32")
+    T = w["dims"][3]
+    n_lp, n_hp = 5000, 500
+    lp = dl.Params(tol=1e-6, delta=1e-6, precision=dl.PREC_F32, batch=32, method=dl.METHOD_CGNR)
+    hp = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=32)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    t0 = time.perf_counter()
+    mean, var, pn = ctx.tsm_estimate(1, n_lp, n_hp, dl.DIL_TIME, -1, lp, hp, dl.SINK_LOCAL, per_noise=True)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    clk = clocks.stop()
+    mean, var = mean[0], var[0]
+    lp_l, hp_l, lph_l = pn[:n_lp, 0], pn[n_lp:n_lp + n_hp, 0], pn[n_lp + n_hp:, 0]
+    cover_lp = np.array([[(i % T) == t for t in range(T)] for i in range(n_lp)])
+    cover_hp = np.array([[((n_lp + i) % T) == t for t in range(T)] for i in range(n_hp)])
+
+    def mv(a, cov):
+        cnt = cov.sum(0)
+        m = (a * cov[:, None, :]).sum(0) / cnt
+        d = (a - m[None]) * cov[:, None, :]
+        return m, (np.abs(d) ** 2).sum(0) / (cnt - 1) / cnt
+
+    m_lp, v_lp = mv(lp_l, cover_lp)
+    m_d, v_d = mv(hp_l - lph_l, cover_hp)
+    names = dl.GAMMA_NAMES
+    out = {"workload": "tsm_16x16x16x32", "n_lp": n_lp, "n_hp": n_hp, "dilution": "time",
+           "lp": "FP32 CGNR to 1e-6", "hp": "FP32 inner + FP64 defect correction to 1e-10",
+           "seconds": round(el, 2), "solves": n_lp + 2 * n_hp,
+           "solves_per_s": round((n_lp + 2 * n_hp) / el, 1), "clocks": clk, "per_gamma": {}}
+    for g in range(16):
+        err = float(np.sqrt((var[g].real + var[g].imag).mean()))
+        out["per_gamma"][names[g]] = {
+            "estimate_sum_t": [float(mean[g].sum().real), float(mean[g].sum().imag)],
+            "error_per_t": err,
+            "lp_variance_share": float((v_lp[g].real + v_lp[g].imag).sum() / max((var[g].real + var[g].imag).sum(), 1e-300)),
+            "correction_per_t": float(np.abs(m_d[g]).mean()),
+            "correction_error_per_t": float(np.sqrt(v_d[g].mean()))}
+    print(json.dumps(out), flush=True)
+
+
 def workload_correlators():
     """Sec. 3 two-point functions on 16^3 x 32 (kappa 0.140): the connected pion from one point source
     (12 solves) and the disconnected function of 16 spin x colour x even-odd diluted noise vectors
@@ -506,16 +558,16 @@ def workload_correlators():
 def workload_dilution():
     """Stochastic error per inversion for each dilution scheme (the study of Sec. 3, Figs. 3-4, without
     the gauge-noise line, which needs an ensemble).  8^3 x 16 (kappa 0.140, eps 0.45), time dilution by
-    translation in every scheme, exact loops from all 12V point sources as the reference.  Each noise
-    vector n (K inversions, one per dilution class) gives one estimate of L_Gamma(t0 = n mod T); with
-    sigma^2 the mean squared deviation of those estimates from the exact loops, the error of an estimate
-    that costs N_inv inversions is sqrt(sigma^2 K / N_inv).  Reported: sqrt(sigma^2 K) per Gamma."""
+    translation in every scheme, exact loops from all 12V point sources as the reference.  The library
+    (dl_dilution_error) solves each noise vector's K diluted sources, forms its loop estimate on the
+    source timeslice t0 = n mod T and returns sigma^2, the mean squared deviation of those estimates from
+    the exact loops; an estimate that costs N_inv inversions has the error sqrt(sigma^2 K / N_inv).
+    Reported per Gamma: sqrt(sigma^2 K), the error per unit inversion, with clocks per scheme."""
     import numpy as np
     import torch
     import paper_1012_5168_gb300 as dl
     ctx, U, w = _ctx(dl, "tsm_8x8x8x16")
     V = int(np.prod(w["dims"]))
-    T = w["dims"][3]
     p = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=64)
     t0 = time.perf_counter()
     exact, _ = ctx.exact_loops(0, 12 * V, p)
@@ -531,18 +583,13 @@ def workload_dilution():
     for label, dil in schemes.items():
         K = dl.n_classes(dil)
         n_noise = max(16, 3072 // K)
-        eta = ctx.make_sources(seed=11, noise_first=0, n_noise=n_noise, dilution=dil, t0=-1)
         torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
         t1 = time.perf_counter()
-        phi, _ = ctx.solve(eta, p)
-        t_of = [(j // K) % T for j in range(n_noise * K)]
-        L = ctx.trace_loops(eta, phi, dl.SINK_LOCAL, t_of_rhs=t_of, group=K)[:, 0]  # [n_noise][16][T]
-        torch.cuda.synchronize()
+        sigma2 = ctx.dilution_error(11, n_noise, dil, -1, p, exact)
         el = time.perf_counter() - t1
-        dev = np.array([L[n, :, n % T] - exact[:, n % T] for n in range(n_noise)])  # [n_noise][16]
-        sigma2 = (np.abs(dev) ** 2).mean(0)
         out["schemes"][label] = {
-            "classes": K, "noise_vectors": n_noise, "seconds": round(el, 3),
+            "classes": K, "noise_vectors": n_noise, "seconds": round(el, 3), "clocks": clocks.stop(),
             "error_per_unit_inversion": {names[g]: float(np.sqrt(sigma2[g] * K)) for g in range(16)}}
     print(json.dumps(out), flush=True)
 
@@ -605,7 +652,7 @@ def main():
         return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
                 "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,
                 "correlators_16x16x16x32": workload_correlators,
-                "dilution_8x8x8x16": workload_dilution, "batch_scan_16x16x16x32": workload_batch_scan}[args.workload]()
+                "dilution_8x8x8x16": workload_dilution, "tsm_16x16x16x32": workload_tsm_paper, "batch_scan_16x16x16x32": workload_batch_scan}[args.workload]()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 

@@ -281,6 +281,24 @@ int dl_tsm_estimate(dl_ctx *ctx, uint64_t seed, int n_lp, int n_hp, unsigned dil
                     int sink, const dl_smear *smear,
                     double *mean_out, double *var_out, double *per_noise_out);
 
+/* Dilution study (Sec. 3, Figs. 3-4): the stochastic error of the loop
+ * estimate of one diluted noise vector.  Noise vectors n = 0 .. n_noise-1 of
+ * `seed` are diluted by `dilution` (K classes) and solved with *params; each
+ * gives the estimate L_n[Gamma][t] = sum over its classes of
+ * sum_{x in t} eta^dag Gamma phi (local sink).  With host_exact the exact loops
+ * (double [16][T][2], e.g. from dl_exact_loops),
+ *   sigma2[Gamma] = mean over n of |L_n[Gamma][t_n] - exact[Gamma][t_n]|^2
+ * on the source timeslice t_n (t0, or n mod T when t0 < 0) for DL_DIL_TIME,
+ * else the mean over n and all timeslices.  An estimate that costs N_inv
+ * inversions then has the error sqrt(sigma2 K / N_inv) (the quantity plotted
+ * against the number of inversions per scheme).  host_sigma2: double [16];
+ * per_noise_out (may be NULL): double [n_noise][16][T][2].  The per-noise
+ * loops and the mean run on the device in a fixed order.  Errors: DL_EINVAL,
+ * DL_ESTATE, DL_ENOMEM, DL_ECUDA; the status of the worst solve otherwise. */
+int dl_dilution_error(dl_ctx *ctx, uint64_t seed, int n_noise, unsigned dilution, int t0,
+                      const dl_solve_params *params, const double *host_exact, double *host_sigma2,
+                      double *per_noise_out);
+
 /* --- two-point functions (Sec. 3, Eqs. 1 and 3) --------------------------- */
 
 /* Momentum-projected loops.  Sec. 3 puts the momentum phases inside the

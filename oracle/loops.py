@@ -141,6 +141,21 @@ def tsm_estimate(lp: np.ndarray, hp: np.ndarray, lp_on_hp: np.ndarray,
     return m_lp + m_d, v_lp + v_d
 
 
+def dilution_sigma2(per_noise: np.ndarray, exact: np.ndarray, t_of=None) -> np.ndarray:
+    """Stochastic error of one noise vector's loop estimate (the dilution study of Sec. 3, Figs. 3-4).
+
+    per_noise: [n, 16, T] loop estimates, each summed over the dilution classes of one noise
+    vector; exact: [16, T] exact loops; t_of: [n] source timeslice of each time-diluted vector
+    (None: every timeslice of every vector counts).  Returns, per Gamma, the mean of
+    |L_n(t) - exact(t)|^2 over the vectors (and timeslices) that estimate it.  With K classes per
+    vector, an estimate costing N_inv inversions has the error sqrt(sigma2 K / N_inv).
+    """
+    dev = np.abs(per_noise - exact[None]) ** 2  # [n, 16, T]
+    if t_of is None:
+        return dev.mean(axis=(0, 2))
+    return np.array([dev[i, :, t] for i, t in enumerate(t_of)]).mean(axis=0)
+
+
 def loop_gradients(U, kappa, eta, gamma_index: int, g: np.ndarray, t_bc=-1.0, tol=1e-13):
     """Gradients of a real loss through L(t) = sum_{x in t} eta^dag Gamma M^{-1} eta.
 

@@ -42,7 +42,7 @@ SYMBOLS = (
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
     "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
     "dl_trace_loops_noalloc", "dl_bench_fma", "dl_trace_loops_mom", "dl_meson_correlators", "dl_disconnected",
-    "dl_apply_hop_prec",
+    "dl_apply_hop_prec", "dl_dilution_error",
 )
 
 
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
         "dl_solve_adjoint": (i, [vp, vp, vp, i, P(SolveParams), P(SolveStats)]),
         "dl_apply_hop": (i, [vp, vp, vp, i]),
         "dl_apply_hop_prec": (i, [vp, i, vp, vp, i]),
+        "dl_dilution_error": (i, [vp, u64, i, ctypes.c_uint, i, P(SolveParams), vp, vp, vp]),
         "dl_apply_m": (i, [vp, vp, vp, i]),
         "dl_apply_smear": (i, [vp, vp, vp, i, P(Smear), i, i]),
         "dl_apply_gamma_weights": (i, [vp, vp, vp, i, vp, i, i]),
@@ -493,6 +494,22 @@ class Context:
                                      mean.ctypes.data_as(ctypes.c_void_p), var.ctypes.data_as(ctypes.c_void_p),
                                      pn.ctypes.data_as(ctypes.c_void_p) if pn is not None else None))
         return (mean, var, pn) if per_noise else (mean, var)
+
+    def dilution_error(self, seed: int, n_noise: int, dilution: int, t0: int, params: Params, exact: np.ndarray,
+                       per_noise: bool = False):
+        """Dilution study: per Gamma, the mean squared deviation of one noise vector's loop
+        estimate from the exact loops `exact` [16][T] (dl_dilution_error).  Returns sigma2 [16]
+        (and the per-noise loops [n_noise][16][T] with per_noise=True)."""
+        T = self.dims[3]
+        ex = np.ascontiguousarray(np.asarray(exact, dtype=np.complex128).reshape(16, T))
+        sig = np.zeros(16, dtype=np.float64)
+        pn = np.zeros((n_noise, 16, T), dtype=np.complex128) if per_noise else None
+        p = params.c()
+        rc = lib().dl_dilution_error(self._h, seed, n_noise, dilution, t0, ctypes.byref(p),
+                                     ex.ctypes.data_as(ctypes.c_void_p), sig.ctypes.data_as(ctypes.c_void_p),
+                                     pn.ctypes.data_as(ctypes.c_void_p) if pn is not None else None)
+        _check(rc)
+        return (sig, pn) if per_noise else sig
 
     def bench_hop(self, precision: int, n_rhs: int, fused: int = 0, reps: int = 20):
         """Time one hop kind alone (fused: 0 plain, 1 XPAY + <rhat, v>, 2 XPAY + five reductions)."""

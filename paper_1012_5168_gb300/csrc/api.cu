@@ -2107,6 +2107,75 @@ extern "C" int dl_tsm_estimate(dl_ctx *c, uint64_t seed, int n_lp, int n_hp, uns
 }
 
 // ---------------------------------------------------------------------------
+// dilution study
+// ---------------------------------------------------------------------------
+// sigma2[G] = mean over noise vectors n (and, without time dilution, over the
+// timeslices t) of |L_n[G][t] - exact[G][t]|^2, with t = t_n on the source
+// timeslice of a time-diluted vector; fixed summation order.
+__global__ void dilution_error_kernel(const double2 *noise /* [n][16][T] */, int n, int T, int timed, int t0,
+                                      const double2 *exact /* [16][T] */, double *sigma2) {
+    const int G = threadIdx.x;
+    if (G >= 16) return;
+    double acc = 0.0, cnt = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int t = 0; t < T; ++t) {
+            if (timed && t != (t0 >= 0 ? t0 : i % T)) continue;
+            const double2 v = noise[((size_t)i * 16 + G) * T + t], e = exact[G * T + t];
+            const double dr = v.x - e.x, di = v.y - e.y;
+            acc += dr * dr + di * di;
+            cnt += 1.0;
+        }
+    sigma2[G] = cnt > 0 ? acc / cnt : 0.0;
+}
+
+extern "C" int dl_dilution_error(dl_ctx *c, uint64_t seed, int n_noise, unsigned dil, int t0,
+                                 const dl_solve_params *params, const double *host_exact, double *host_sigma2,
+                                 double *per_noise_out) {
+    TRY(ready(c));
+    if (n_noise < 1) return fail(DL_EINVAL, "need at least one noise vector");
+    if (dil & ~31u) return fail(DL_EINVAL, "unknown dilution bits");
+    if ((dil & DL_DIL_TIME) && t0 >= c->dims[3]) return fail(DL_EINVAL, "t0 outside the lattice");
+    if (!host_exact || !host_sigma2) return fail(DL_EINVAL, "null argument");
+    SolveCfg P;
+    TRY(read_params(params, &P));
+    const int T = c->dims[3];
+    const int per = 16 * T;
+    const int N = P.batch;
+    TRY(ensure_ws(c, N));
+    TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
+    TRY(maybe_tune(c, P.prec, N));
+    TRY(maybe_tune(c, P_F64, N));
+    // per-noise loops, the exact loops and the 16 results (as doubles) in the noise buffer
+    const size_t need = (size_t)per * n_noise + per + 8;
+    if (c->noise_cap < need) {
+        TRY(sync(c));
+        if (c->d_noise) cudaFree(c->d_noise);
+        c->d_noise = nullptr;
+        if (cudaMalloc((void **)&c->d_noise, need * sizeof(double2)) != cudaSuccess)
+            return fail(DL_ENOMEM, "dilution-study buffers");
+        c->noise_cap = need;
+    }
+    double2 *d_loops = c->d_noise, *d_exact = d_loops + (size_t)per * n_noise;
+    double *d_sig = reinterpret_cast<double *>(d_exact + per);
+    c->cur = c->stream;
+    const int cnt = per * n_noise;
+    zero_kernel<<<std::max(1, std::min(4096, (cnt + 255) / 256)), 256, 0, c->stream>>>(d_loops, cnt);
+    CK(cudaMemcpyAsync(d_exact, host_exact, per * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    int worst = DL_OK;
+    TRY(tsm_pass(c, seed, 0, n_noise, dil, t0, P, DL_SINK_LOCAL, nullptr, 1, d_loops, &worst));
+    dilution_error_kernel<<<1, 32, 0, c->stream>>>(d_loops, n_noise, T, (dil & DL_DIL_TIME) ? 1 : 0, t0, d_exact,
+                                                   d_sig);
+    c->kernel_launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_sigma2, d_sig, 16 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (per_noise_out)
+        CK(cudaMemcpyAsync(per_noise_out, d_loops, (size_t)cnt * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    TRY(sync(c));
+    if (worst != DL_OK) fail(worst, "some solves of the dilution study did not converge");
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
 // measurement
 // ---------------------------------------------------------------------------
 extern "C" int dl_bench_hop(dl_ctx *c, int precision, int n_rhs, int fused, int reps, double *ms, double *bytes) {

@@ -180,3 +180,41 @@ def test_tsm_time_diluted_smeared(lib):
     assert loop_error(pn[4:6, 0].reshape(-1, 4), ref_l.reshape(-1, 4)) < 1e-8
     assert loop_error(pn[4:6, 1].reshape(-1, 4), ref_s.reshape(-1, 4)) < 1e-8
     c.close()
+
+
+def golden_exact_4x4x4x4():
+    """The oracle's exact loops of the 4^4 workload (tests/golden, written by make_golden.py)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "exact_loops_4x4x4x4.txt")
+    out = np.zeros((16, 4), dtype=np.complex128)
+    for g, t, re, im in np.loadtxt(path):
+        out[int(g), int(t)] = re + 1j * im
+    return out
+
+
+@pytest.mark.parametrize("dil, n_noise", [(16, 12), (1 | 16, 6), (1 | 2 | 4 | 16, 4)])
+def test_dilution_error_matches_oracle(lib, dil, n_noise):
+    """The dilution study (Sec. 3, Figs. 3-4) on the 4^4 workload: per-noise loop estimates and the
+    per-Gamma mean squared deviation from the exact loops, GPU (FP32 inner, 1e-12) against the
+    oracle's estimator on the same noise vectors (bit-identical sources, oracle solves to 1e-13)."""
+    w = synthetic.WORKLOADS["exact_4x4x4x4"]
+    dims, kappa = w["dims"], w["kappa"]
+    U = synthetic.gauge_field(dims, w["eps"], w["seed"])
+    exact = golden_exact_4x4x4x4()
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    sig, per = c.dilution_error(9, n_noise, dil, -1, lib.Params(tol=1e-12, precision=1, batch=32), exact,
+                                per_noise=True)
+    t_of = [n % dims[3] for n in range(n_noise)]
+    ref_per = []
+    for n in range(n_noise):
+        eta = noise.make_sources(dims, 9, n, 1, dil, t0=-1)
+        phi = np.stack([wilson.solve(U, e, kappa, -1.0, tol=1e-13)[0] for e in eta])
+        ref_per.append(loops.stochastic_loops(eta, phi).sum(0))
+    ref_per = np.array(ref_per)
+    ref_sig = loops.dilution_sigma2(ref_per, exact, t_of)
+    for n in range(n_noise):
+        assert loop_error(per[n], ref_per[n]) < 1e-9
+    assert np.all(np.abs(sig - ref_sig) <= 1e-8 * ref_sig + 1e-12 * np.abs(exact).max() ** 2), (sig, ref_sig)
+    c.close()

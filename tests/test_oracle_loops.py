@@ -210,3 +210,39 @@ def test_loop_gradients_match_torch_autograd():
     ge, gk = loops.loop_gradients(u, kappa, eta, gidx, g, TBC)
     assert np.allclose(ge.reshape(-1), e.grad.numpy(), atol=1e-10)
     assert abs(gk - k.grad.item()) < 1e-9 * max(1.0, abs(gk))
+
+
+def test_dilution_sigma2_pins():
+    """The dilution-study statistic: (a) with the exact loops replaced by the sample means it is
+    numpy's variance (mean |x - mean|^2) of the estimates, weighted by the vectors per timeslice;
+    (b) offsets c_n common to every Gamma give sigma2 = mean |c_n|^2."""
+    rng = np.random.default_rng(7)
+    n, T = 12, 4
+    L = rng.standard_normal((n, 16, T)) + 1j * rng.standard_normal((n, 16, T))
+    t_of = [i % T for i in range(n)]
+    means = np.stack([L[[i for i in range(n) if t_of[i] == t], :, t].mean(0) for t in range(T)], axis=-1)
+    got = loops.dilution_sigma2(L, means, t_of)
+    ref = sum(np.var(L[[i for i in range(n) if t_of[i] == t], :, t], axis=0) * t_of.count(t) for t in range(T)) / n
+    assert np.allclose(got, ref, rtol=1e-13)
+    assert np.allclose(loops.dilution_sigma2(L, L.mean(0), None), np.var(L, axis=0).mean(-1), rtol=1e-13)
+    c = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    exact = rng.standard_normal((16, T)) + 1j * rng.standard_normal((16, T))
+    shifted = exact[None] + c[:, None, None]
+    assert np.allclose(loops.dilution_sigma2(shifted, exact, t_of), np.mean(np.abs(c) ** 2), rtol=1e-13)
+
+
+def test_full_dilution_has_no_stochastic_error():
+    """On a 2x2x2x4 lattice, spin x colour x cubic x time dilution puts every class on one site,
+    spin and colour: each noise vector's estimate is the exact loop on its timeslice, so the
+    dilution-study statistic vanishes (to solver tolerance)."""
+    dims, kappa = (2, 2, 2, 4), 0.11
+    U = synthetic.gauge_field(dims, eps=0.45, seed=8)
+    exact = loops.exact_loops_dense(U, kappa, -1.0)
+    dil = noise.SPIN | noise.COLOUR | noise.CUBIC | noise.TIME
+    per = []
+    for n in range(3):
+        eta = noise.make_sources(dims, 5, n, 1, dil, t0=-1)
+        phi = np.stack([wilson.solve(U, e, kappa, -1.0, tol=1e-13)[0] for e in eta])
+        per.append(loops.stochastic_loops(eta, phi).sum(0))
+    sig = loops.dilution_sigma2(np.array(per), exact, [n % 4 for n in range(3)])
+    assert sig.max() < 1e-20 * np.abs(exact).max() ** 2 + 1e-22
