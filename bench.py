@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--workload", default="stochastic",
                     choices=["stochastic", "exact_4x4x4x4", "single_rhs_16x16x16x32", "tsm_8x8x8x16",
                              "autograd", "correlators_16x16x16x32", "dilution_8x8x8x16",
-                             "batch_scan_16x16x16x32", "tsm_16x16x16x32"],
+                             "batch_scan_16x16x16x32", "tsm_16x16x16x32", "mixed_16x16x16x32"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--smear-profile", metavar="N", type=int, default=None,
@@ -458,6 +458,55 @@ def workload_tsm():
     print(json.dumps(out), flush=True)
 
 
+def workload_mixed():
+    """Batches whose right-hand sides stop at different iterations, on 16^3 x 32 (kappa 0.157, eps 0.60:
+    the kappa-literal variant), FP32 inner to 1e-10, width 32: (a) 16 point sources and 16 complex Z2
+    sources; (b) a ragged last batch of 17 Z2 sources, whose 15 padding columns never take part.  The
+    direct Wilson-hop kernels skip the loads and stores of right-hand sides that have stopped;
+    DLOOPS_HOP_SKIP=0 keeps them streaming.  Reported: iterations and the solve time both ways (each
+    the best of three, after a warm-up solve)."""
+    import numpy as np
+    import torch
+    import paper_1012_5168_gb300 as dl
+    import synthetic
+    w = synthetic.WORKLOADS["wilson_16x16x16x32_k157"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    out = {"workload": "mixed_16x16x16x32", "kappa": w["kappa"], "eps": w["eps"], "batch": 32, "cases": {}}
+    for case in ("point_and_z2", "ragged_17_of_32"):
+        runs = {}
+        for skip in ("1", "0"):
+            os.environ["DLOOPS_HOP_SKIP"] = skip
+            ctx = dl.Context(w["dims"], t_bc=-1)
+            ctx.load_gauge(U)
+            ctx.set_kappa(w["kappa"])
+            V = int(np.prod(w["dims"]))
+            if case == "point_and_z2":
+                b = torch.cat([ctx.make_point_sources(12 * (V // 3), 16),
+                               ctx.make_sources(seed=5, noise_first=0, n_noise=16, dilution=0)]).contiguous()
+            else:  # a last batch of 17 sources: 15 padding columns of the width-32 layout never run
+                b = ctx.make_sources(seed=5, noise_first=0, n_noise=17, dilution=0)
+            p = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=32)
+            ctx.solve(b, p)
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                clocks = ClockSampler(torch.cuda.current_device())
+                t0 = time.perf_counter()
+                _, st = ctx.solve(b, p)
+                torch.cuda.synchronize()
+                times.append((time.perf_counter() - t0, clocks.stop()))
+            best = min(times, key=lambda x: x[0])
+            runs["skip" if skip == "1" else "no_skip"] = {
+                "seconds": round(best[0], 4), "clocks": best[1], "iters": [s["iters"] for s in st],
+                "outer": sorted(set(s["outer"] for s in st)),
+                "max_true_residual": max(s["true_residual"] for s in st)}
+            ctx.close()
+        os.environ.pop("DLOOPS_HOP_SKIP", None)
+        runs["speedup"] = round(runs["no_skip"]["seconds"] / runs["skip"]["seconds"], 3)
+        out["cases"][case] = runs
+    print(json.dumps(out), flush=True)
+
+
 def workload_tsm_paper():
     """The truncated solver method at the paper's sizes (Sec. 2): 5000 low-precision solves
     (single-precision CG on the normal equations, tolerance 1e-6) and 500 high-precision corrections
@@ -652,7 +701,8 @@ def main():
         return {"exact_4x4x4x4": workload_exact, "single_rhs_16x16x16x32": workload_single_rhs,
                 "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,
                 "correlators_16x16x16x32": workload_correlators,
-                "dilution_8x8x8x16": workload_dilution, "tsm_16x16x16x32": workload_tsm_paper, "batch_scan_16x16x16x32": workload_batch_scan}[args.workload]()
+                "dilution_8x8x8x16": workload_dilution, "tsm_16x16x16x32": workload_tsm_paper,
+                "mixed_16x16x16x32": workload_mixed, "batch_scan_16x16x16x32": workload_batch_scan}[args.workload]()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 

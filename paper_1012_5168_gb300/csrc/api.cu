@@ -88,6 +88,7 @@ struct dl_ctx {
     int *h_err = nullptr;          // pinned, mapped [2]: set by the staged hop on a wait timeout
     int *d_err = nullptr;
     bool poisoned = false;         // a staged hop may have left bulk copies pending: no further work
+    bool skip_inactive = true;     // direct hops skip right-hand sides that stopped (DLOOPS_HOP_SKIP=0: off)
     double2 *d_gammas = nullptr;  // [16][4][4]
 
     // batch workspace, width ws_N (power of two)
@@ -209,7 +210,7 @@ static void record(dl_ctx *c, cudaEvent_t e) {
 // P_DFF: `in` is float-float; ffmt flags FF_Y / FF_OUT give the formats of y and out.
 static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void *in, const void *y, const void *z,
                   const void *rhat, int p, int N, double coef, int cb0, int cb1, double2 *partials, int *nblocks,
-                  int ffmt = 0) {
+                  int ffmt = 0, const RhsState *act = nullptr) {
     if (c->poisoned) return fail(DL_ECUDA, "context unusable: a staged hop left bulk copies pending");
     HopArgs a;
     a.out = out;
@@ -234,6 +235,9 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.err = c->d_err;
     a.blocked = 0;
     a.gauge8q = c->d_gauge8q;
+    // per-RHS participation flags (BiCGStab inner iterations): next_active holds for the whole iteration
+    a.act = act && c->skip_inactive ? &act[0].next_active : nullptr;
+    a.act_stride = (int)(sizeof(RhsState) / sizeof(int));
     int R = wide ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
@@ -562,6 +566,8 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     {
         const char *e = getenv("DLOOPS_SMEAR_FP64");
         c->smear_fp64 = e && e[0] == '1';
+        const char *k = getenv("DLOOPS_HOP_SKIP");
+        c->skip_inactive = !(k && k[0] == '0');
     }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     c->stream = (cudaStream_t)cuda_stream;
@@ -786,17 +792,18 @@ static int enqueue_iteration(dl_ctx *c, int prec, int N) {
     const int Vh = (int)c->Vh;
     double2 *part = c->d_partials;
     int nb = 0;
+    const RhsState *act = c->d_rhs;  // right-hand sides that stopped skip the direct hops' loads and stores
     TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
-               Vh, nullptr, nullptr));
+               Vh, nullptr, nullptr, 0, act));
     TRY(do_hop(c, prec, MODE_XPAY, RED_R0DOT, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr,
-               lo_ptr(c, LRH), 0, N, -k2, 0, Vh, part, &nb));
+               lo_ptr(c, LRH), 0, N, -k2, 0, Vh, part, &nb, 0, act));
     scalar_alpha_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, part, nb, N);
     VecLaunch v = vec_launch(c, prec, N, 0);
     CK(launch_axpy_s(v, c->d_rhs, lo_ptr(c, LR), lo_ptr(c, LV), lo_ptr(c, LS)));
     TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
-               Vh, nullptr, nullptr));
+               Vh, nullptr, nullptr, 0, act));
     TRY(do_hop(c, prec, MODE_XPAY, RED_BICG, lo_ptr(c, LT), lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, lo_ptr(c, LRH),
-               0, N, -k2, 0, Vh, part, &nb));
+               0, N, -k2, 0, Vh, part, &nb, 0, act));
     scalar_omega_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, part, nb, N);
     CK(launch_update(v, c->d_rhs, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LP), lo_ptr(c, LS), lo_ptr(c, LT),
                      lo_ptr(c, LV)));

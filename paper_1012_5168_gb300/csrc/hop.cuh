@@ -59,6 +59,8 @@ struct HopArgs {
     int blocked;            // direct kernel: 0 cyclic site mapping, 1 one contiguous range per block
     const float4 *gauge8q;  // [2][Vh][8][9] FP32 quads (Re V, Re V, -Im V, Im V), V = U (forward) or U^dag
                             // (backward, already conjugated): the packed-arithmetic kernel's links
+    const int *act;         // per right-hand side r: act[r * act_stride] != 0 if it takes part in this
+    int act_stride;         // iteration; NULL: all do.  The direct kernels skip the others' loads and stores.
 };
 
 // Load the 12 components of R right-hand sides at one neighbour site and
@@ -304,6 +306,12 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
     for (; idx < idx_end; idx += stride) {
         const int cb = A.cb_begin + (idx >> lgG);
         const int r0 = (idx & (G - 1)) * R;
+        if (A.act) {  // right-hand sides that have converged (or stopped) need no hop
+            bool any = false;
+#pragma unroll
+            for (int r = 0; r < R; ++r) any |= __ldg(A.act + (size_t)(r0 + r) * A.act_stride) != 0;
+            if (!any) continue;
+        }
         const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
         cx<T> acc[R][12];
         if constexpr (X2 != 0 && sizeof(S) == 4 && R == 1) {

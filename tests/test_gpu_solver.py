@@ -385,3 +385,30 @@ def test_nan_gauge_link(lib):
         _, st = c.solve(to_gpu(b), lib.Params(tol=1e-10, precision=prec, batch=2), allow_fail=True)
         assert all(s["status"] == lib.NAN for s in st), st
     c.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_skipping_stopped_rhs_changes_nothing(lib, prec, monkeypatch):
+    """The direct hops skip the loads and stores of right-hand sides that have stopped; the
+    others' arithmetic is untouched and a stopped one's vectors stay frozen either way, so the
+    solutions are bitwise the same with the skip switched off (DLOOPS_HOP_SKIP=0).  Point sources
+    and Z2 sources in one batch stop at different iterations."""
+    dims, kappa = (4, 4, 4, 8), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=12)
+    sols = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("DLOOPS_HOP_SKIP", flag)
+        c = lib.Context(dims)
+        c.load_gauge(U)
+        c.set_kappa(kappa)
+        c.tune_hop(prec, 16, force_pf=0)
+        b = torch.cat([c.make_point_sources(12 * 37, 8), c.make_sources(seed=6, noise_first=0, n_noise=8,
+                                                                          dilution=0)]).contiguous()
+        x, st = c.solve(b, lib.Params(tol=1e-11, precision=prec, batch=16))
+        assert all(s["status"] == 0 for s in st), st
+        sols[flag] = (x.cpu().numpy(), [s["iters"] for s in st])
+        c.close()
+    monkeypatch.delenv("DLOOPS_HOP_SKIP")
+    assert np.array_equal(sols["1"][0], sols["0"][0])
+    assert sols["1"][1] == sols["0"][1]
+    assert len(set(sols["1"][1])) > 1  # the batch really held right-hand sides that stopped early
