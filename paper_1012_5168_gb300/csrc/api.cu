@@ -1030,7 +1030,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
             if (pass == 1) {
                 pow2_pick_kernel<<<1, 64, 0, c->stream>>>(c->d_outer, N);
                 const long rows = 2L * Vh * 12;
-                const long grid = std::min<long>((rows * N + 255) / 256, (long)c->num_sms * 8);
+                const long grid = std::min<long>((rows * N + 255) / 256, (long)c->num_sms * 8);  // stride: a multiple of N
                 pow2_scale_kernel<<<(int)grid, 256, 0, c->stream>>>(c->b64, (size_t)rows, N, c->d_outer, +1);
                 c->kernel_launches += 2;
             }

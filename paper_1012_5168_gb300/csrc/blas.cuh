@@ -729,18 +729,26 @@ static __global__ void pow2_pick_kernel(OuterState *os, int N) {
     os[r].scale_exp = (b2 > 0.0 && isfinite(b2)) ? -ilogb(sqrt(b2)) : 0;
 }
 
-// f[e][r] *= 2^(sign * k_r) on a field of n_rows rows of N complex doubles
-// (scalbn: exact unless a value under- or overflows).
+// 2^e as a double for e in [-1022, 1023] (built from its bits, exact).
+__device__ __forceinline__ double pow2_exact(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+
+// f[e][r] *= 2^(sign * k_r) on a field of n_rows rows of N complex doubles (N a
+// power of two dividing the block size, so a thread always meets the same
+// right-hand side r = index mod N).  2^k is applied as two factors 2^(k/2) and
+// 2^(k - k/2), each a normal double for |k| <= 2046; the products are exact
+// unless a value under- or overflows.
 static __global__ void pow2_scale_kernel(double *f, size_t n_rows, int N, const OuterState *os, int sign) {
+    const size_t first = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    const int k = sign * os[first & (size_t)(N - 1)].scale_exp;
+    if (k == 0) return;
+    const double f1 = pow2_exact(k / 2), f2 = pow2_exact(k - k / 2);
+    double2 *z = reinterpret_cast<double2 *>(f);
     const size_t total = n_rows * (size_t)N;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int k = sign * os[i % N].scale_exp;
-        if (k == 0) continue;
-        double2 *z = reinterpret_cast<double2 *>(f) + i;
-        double2 v = *z;
-        v.x = scalbn(v.x, k);
-        v.y = scalbn(v.y, k);
-        *z = v;
+    for (size_t i = first; i < total; i += stride) {
+        double2 v = z[i];
+        v.x = v.x * f1 * f2;
+        v.y = v.y * f1 * f2;
+        z[i] = v;
     }
 }
 

@@ -86,13 +86,11 @@ static __global__ void gauge_reorder_kernel(const uint32_t *coords, Geom g, cons
     }
 }
 
-// gauge, site-major with all eight links of a site in one row: for site x of
-// parity p, row d = 2 mu holds U_mu(x) and row d = 2 mu + 1 holds U_mu(x - mu)
-// (not conjugated).  Out: [2][Vh][8][9] complex in S.
 // The packed-arithmetic hop's links: per output site the eight links of its
 // hop directions (d = 2 mu: U_mu(x); d = 2 mu + 1: V = U_mu(x - mu)^dag, the
 // conjugate transpose taken here), each element V[a][b] stored as the FP32
-// quad (Re V, Re V, -Im V, Im V).
+// quad (Re V, Re V, -Im V, Im V), with the time boundary factor t_bc folded
+// into the links of the hops that cross t = T-1 <-> 0.
 static __global__ void gauge8q_kernel(const uint32_t *coords, Geom g, const double *canon, float4 *out) {
     const int total = 2 * g.Vh;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -106,16 +104,21 @@ static __global__ void gauge8q_kernel(const uint32_t *coords, Geom g, const doub
             }
             const double2 *u = (const double2 *)(canon + ((size_t)src * 4 + mu) * 18);
             float4 *dst = out + ((size_t)idx * 8 + d) * 9;
+            const double sg = (mu == 3 && g.t_bc < 0 && st.c[3] == ((d & 1) ? 0 : g.L[3] - 1)) ? -1.0 : 1.0;
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b) {
                     const double2 z = (d & 1) ? make_double2(u[b * 3 + a].x, -u[b * 3 + a].y) : u[a * 3 + b];
-                    const float re = (float)z.x, im = (float)z.y;
+                    const float re = (float)(sg * z.x), im = (float)(sg * z.y);
                     dst[a * 3 + b] = make_float4(re, re, -im, im);
                 }
         }
     }
 }
 
+// gauge, site-major with all eight links of a site in one row: for site x of
+// parity p, row d = 2 mu holds U_mu(x) and row d = 2 mu + 1 holds U_mu(x - mu)
+// (not conjugated), the time boundary factor t_bc folded into the links of
+// the hops that cross t = T-1 <-> 0.  Out: [2][Vh][8][9] complex in S.
 template <typename S>
 __global__ void gauge8_kernel(const uint32_t *coords, Geom g, const double *canon, S *out) {
     typedef typename Real<S>::type T;
@@ -131,9 +134,11 @@ __global__ void gauge8_kernel(const uint32_t *coords, Geom g, const double *cano
             }
             const double2 *u = (const double2 *)(canon + ((size_t)src * 4 + mu) * 18);
             S *dst = out + ((size_t)idx * 8 + d) * 18;
+            // the time boundary factor of the quark fields rides on the link of the hop that crosses it
+            const double sg = (mu == 3 && g.t_bc < 0 && st.c[3] == ((d & 1) ? 0 : g.L[3] - 1)) ? -1.0 : 1.0;
             for (int k = 0; k < 9; ++k) {
                 cx<T> z[1];
-                z[0] = mk((T)u[k].x, (T)u[k].y);
+                z[0] = mk((T)(sg * u[k].x), (T)(sg * u[k].y));
                 st_pack<S, 1>(dst + 2 * k, z);
             }
         }

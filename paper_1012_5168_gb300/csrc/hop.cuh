@@ -148,7 +148,8 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
     // ---- forward: (1 - g_mu) U_mu(x) psi(x + mu)
     {
         const int nb = nbr_fwd(st, A.g, MU);
-        const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == A.g.L[3] - 1);
+        // the low-precision link rows carry the time boundary factor already
+        const bool flip = !G8 && (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == A.g.L[3] - 1);
         cx<T> u[9];
         // low precision: site-major rows (all eight links of the output site together)
         const S *up = G8 ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU) * 18
@@ -173,7 +174,7 @@ __device__ __forceinline__ void hop_dir(const HopArgs &A, const Site &st, int cb
     // ---- backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
     {
         const int nb = nbr_bwd(st, A.g, MU);
-        const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == 0);
+        const bool flip = !G8 && (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == 0);
         cx<T> u[9];
         const S *up = G8 ? reinterpret_cast<const S *>(A.gauge8) + (((size_t)A.p * A.g.Vh + cb) * 8 + 2 * MU + 1) * 18
                          : gauge + (((size_t)(1 - A.p) * A.g.Vh + nb) * 4 + MU) * 18;
@@ -242,13 +243,12 @@ __device__ __forceinline__ void hop_dir_x2(const HopArgs &A, const Site &st, int
     const size_t N = NC ? (size_t)NC : (size_t)A.N;
     constexpr int D = 2 * MU + (SG > 0 ? 1 : 0);
     const int nb = SG < 0 ? nbr_fwd(st, A.g, MU) : nbr_bwd(st, A.g, MU);
-    const bool flip = (MU == 3) && (A.g.t_bc < 0) && (st.c[3] == (SG < 0 ? A.g.L[3] - 1 : 0));
     const float *src = in + (size_t)nb * 12 * N * 2 + (size_t)r0 * 2;
     cx<float> hh[1][6];
     load_project<float, 1, MU, SG>(src, N, hh);
-    float2 h[6];
+    float2 h[6];  // (the link quads carry the time boundary factor)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) h[k] = flip ? make_float2(-hh[0][k].re, -hh[0][k].im) : make_float2(hh[0][k].re, hh[0][k].im);
+    for (int k = 0; k < 6; ++k) h[k] = make_float2(hh[0][k].re, hh[0][k].im);
     const float4 *q = A.gauge8q + (((size_t)A.p * A.g.Vh + cb) * 8 + D) * 9;
     float2 w[6];
 #pragma unroll

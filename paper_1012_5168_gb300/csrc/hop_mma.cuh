@@ -162,9 +162,7 @@ __global__ void __launch_bounds__(WS_WARPS * 32, R == 1 ? 4 : 2) hop_kernel_mma(
     int k = 0;
     for (int j = 0; j < nmy && ok; ++j) {
         const int cb = A.cb_begin + gw + j * tw;
-        const int tcoord = (int)((__ldg(A.coords + (size_t)A.p * A.g.Vh + cb) >> 24) & 0xffu);
-        const bool flip_f = (A.g.t_bc < 0) && (tcoord == A.g.L[3] - 1);
-        const bool flip_b = (A.g.t_bc < 0) && (tcoord == 0);
+        // (the link rows carry the time boundary factor)
         const unsigned char *lrow = lnk + (size_t)(j & 1) * W::LB;
         float acc[2][NT][4];
 #pragma unroll
@@ -179,7 +177,7 @@ __global__ void __launch_bounds__(WS_WARPS * 32, R == 1 ? 4 : 2) hop_kernel_mma(
             ok = __all_sync(0xffffffffu, mbar_wait(full + slot, (uint32_t)((k / NST) & 1)));           \
             if (ok) {                                                                                  \
                 mma_dir<R, D>(stg + (size_t)slot * W::SB, lrow, tcode, lane,                           \
-                              (D == 6) ? flip_f : ((D == 7) ? flip_b : false), acc);                   \
+                              false, acc);                   \
                 __syncwarp();                                                                          \
                 if (k + NST < nsteps) {                                                                \
                     issue(k + NST);                                                                    \

@@ -230,10 +230,7 @@ __global__ void __launch_bounds__(256) hop_kernel_tma(HopArgs A) {
         const int ns = min(SITES, A.cb_end - cb0);
         const bool active = s_me < ns;
         const int cb = cb0 + s_me;
-        int tcoord = 0;
-        if (active) tcoord = (__ldg(A.coords + (size_t)A.p * A.g.Vh + cb) >> 24) & 0xff;
-        const bool flip_f = (A.g.t_bc < 0) && (tcoord == A.g.L[3] - 1);
-        const bool flip_b = (A.g.t_bc < 0) && (tcoord == 0);
+        // (the link rows carry the time boundary factor)
         const unsigned char *lrow = lnk + (size_t)(j & 1) * SITES * LB + (size_t)s_me * LB;
         cx<T> acc[R][12];
 #pragma unroll
@@ -246,7 +243,7 @@ __global__ void __launch_bounds__(256) hop_kernel_tma(HopArgs A) {
             const bool landed = mbar_wait(full + slot, (uint32_t)((k / NST) & 1));                     \
             if (landed && active)                                                                      \
                 tma_compute<S, R, D>(stg + (size_t)slot * SITES * SB + (size_t)s_me * SB, lrow, A.N, r0, \
-                                     (D == 6) ? flip_f : ((D == 7) ? flip_b : false), acc);            \
+                                     false, acc);            \
             ok = __syncthreads_and(landed) != 0; /* block-uniform; the slot is free */                 \
             if (ok) {                                                                                  \
                 if (warp == 0 && k + NST < nsteps) issue(k + NST);                                     \
