@@ -159,6 +159,28 @@ int dl_load_gauge(dl_ctx *ctx, const double *host_U, int check_unitarity);
 /* Set the hopping parameter kappa of M = 1 - kappa D (Sec. 2: kappa = 0.157). */
 int dl_set_kappa(dl_ctx *ctx, double kappa);
 
+/* Clover (Sheikholeslami-Wohlert) improvement, an extension: the paper's
+ * inversions use plain Wilson fermions (Sec. 2), which c_sw = 0 (the default)
+ * keeps.  With c_sw != 0 the operator becomes M = A - kappa D with the
+ * site-local, hermitian, gamma_5-commuting
+ *   A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x),
+ *   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu],
+ *   F_{mu nu} = (Q_{mu nu} - Q_{mu nu}^dag)/(8i),
+ * Q_{mu nu}(x) the sum of the four plaquettes of the mu-nu plane that start
+ * and end at x, each traversed mu first.  A and its inverse (two 6 x 6 blocks
+ * per site in the chiral basis; A in FP64, A^-1 in FP64, FP32 and BF16:
+ * 3168 bytes of device memory per site) are built from the FP64 links before the next call that
+ * needs them, after any change of links, kappa or c_sw.  dl_apply_m, the
+ * solvers and every solve inside the loop estimators then use M; dl_apply_hop
+ * is still D alone.  The even-odd solve uses the asymmetric Schur system
+ * A_ee^-1 (A_ee - kappa^2 D_eo A_oo^-1 D_oe) with A^-1 applied in the inner
+ * hops; the residual and tolerance remain those of b - M x.  BiCGStab only:
+ * a solve with DL_METHOD_CGNR fails with DL_EINVAL, and mixed-precision clover
+ * solves run their defect-correction steps in FP64.  Errors: DL_EINVAL
+ * (non-finite c_sw), DL_ECUDA; an allocation failure (DL_ENOMEM) is reported
+ * by the call that builds the blocks. */
+int dl_set_clover(dl_ctx *ctx, double c_sw);
+
 /* Enable (1) or disable (0) CUDA-event timing of Wilson-hop launches; read and
  * reset with dl_get_timing. */
 int dl_set_timing(dl_ctx *ctx, int enable);
@@ -224,8 +246,19 @@ int dl_apply_hop(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
  * be measured.  Errors: DL_EINVAL (precision, sizes, pointers, in == out),
  * DL_ESTATE (no gauge field), DL_ENOMEM, DL_ECUDA. */
 int dl_apply_hop_prec(dl_ctx *ctx, int precision, const void *dev_in, void *dev_out, int n_rhs);
-/* out = M in = in - kappa D in. */
+/* out = M in = in - kappa D in (with clover: A in - kappa D in, dl_set_clover). */
 int dl_apply_m(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
+/* out = -dM/dkappa in = D in (+ c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu} in with
+ * clover, formed as (in - A in)/kappa in FP64): the derivative that the
+ * kappa-gradient of a loop needs (Sec. 3's loops as functions of kappa:
+ * dM^-1/dkappa = M^-1 (-dM/dkappa) M^-1).  Errors as dl_apply_m, and
+ * DL_EINVAL for kappa = 0 with clover. */
+int dl_apply_dm_dkappa(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs);
+/* out = A in (inverse = 0) or A^-1 in (inverse != 0), site by site in FP64:
+ * the clover blocks of dl_set_clover (a copy of in without clover).  Canonical
+ * complex128 fields as dl_apply_m.  Errors: DL_EINVAL (sizes, pointers,
+ * in == out), DL_ESTATE (no gauge field or kappa), DL_ENOMEM, DL_ECUDA. */
+int dl_apply_clover(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs, int inverse);
 /* out = K in, Gaussian smearing (Sec. 2), restricted to timeslices
  * [t_lo, t_hi) (other timeslices of out are set to zero). */
 int dl_apply_smear(dl_ctx *ctx, const void *dev_in, void *dev_out, int n_rhs,

@@ -37,9 +37,9 @@ GAMMA_NAMES = ("1", "g1", "g2", "g3", "g4", "g5", "g5g1", "g5g2", "g5g3", "g5g4"
 
 # every entry point of the C ABI, as declared in include/dloops.h
 SYMBOLS = (
-    "dl_create", "dl_destroy", "dl_last_error", "dl_status_string", "dl_load_gauge", "dl_set_kappa",
+    "dl_create", "dl_destroy", "dl_last_error", "dl_status_string", "dl_load_gauge", "dl_set_kappa", "dl_set_clover",
     "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
-    "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_smear", "dl_apply_gamma_weights",
+    "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_dm_dkappa", "dl_apply_clover", "dl_apply_smear", "dl_apply_gamma_weights",
     "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop",
     "dl_trace_loops_noalloc", "dl_bench_fma", "dl_trace_loops_mom", "dl_meson_correlators", "dl_disconnected",
     "dl_apply_hop_prec", "dl_dilution_error",
@@ -93,6 +93,7 @@ def lib() -> ctypes.CDLL:
         "dl_status_string": (ctypes.c_char_p, [i]),
         "dl_load_gauge": (i, [vp, vp, i]),
         "dl_set_kappa": (i, [vp, d]),
+        "dl_set_clover": (i, [vp, d]),
         "dl_set_timing": (i, [vp, i]),
         "dl_get_timing": (i, [vp, P(Timing), i]),
         "dl_make_sources": (i, [vp, u64, i64, i, ctypes.c_uint, i, i, vp, P(i64)]),
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
         "dl_apply_hop_prec": (i, [vp, i, vp, vp, i]),
         "dl_dilution_error": (i, [vp, u64, i, ctypes.c_uint, i, P(SolveParams), vp, vp, vp]),
         "dl_apply_m": (i, [vp, vp, vp, i]),
+        "dl_apply_dm_dkappa": (i, [vp, vp, vp, i]),
+        "dl_apply_clover": (i, [vp, vp, vp, i, i]),
         "dl_apply_smear": (i, [vp, vp, vp, i, P(Smear), i, i]),
         "dl_apply_gamma_weights": (i, [vp, vp, vp, i, vp, i, i]),
         "dl_trace_loops": (i, [vp, vp, vp, i, i, P(Smear), i, i, P(i), i, vp]),
@@ -289,6 +292,10 @@ class Context:
     def set_kappa(self, kappa: float):
         _check(lib().dl_set_kappa(self._h, float(kappa)))
 
+    def set_clover(self, c_sw: float):
+        """Clover coefficient c_sw of M = A - kappa D (0: plain Wilson, the default)."""
+        _check(lib().dl_set_clover(self._h, float(c_sw)))
+
     def set_timing(self, enable: bool):
         _check(lib().dl_set_timing(self._h, int(enable)))
 
@@ -367,6 +374,21 @@ class Context:
         n = self._field(x)
         out = self._torch.empty_like(x) if out is None else out
         _check(lib().dl_apply_m(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n))
+        return out
+
+    def apply_dm_dkappa(self, x, out=None):
+        """-dM/dkappa x: D x, plus the clover term c_sw sum sigma F x when c_sw != 0."""
+        n = self._field(x)
+        out = self._torch.empty_like(x) if out is None else out
+        _check(lib().dl_apply_dm_dkappa(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n))
+        return out
+
+    def apply_clover(self, x, inverse: bool = False, out=None):
+        """A x or A^-1 x (the clover blocks; the identity when c_sw = 0)."""
+        n = self._field(x)
+        out = self._torch.empty_like(x) if out is None else out
+        _check(lib().dl_apply_clover(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
+                                     int(inverse)))
         return out
 
     def apply_smear(self, x, alpha: float, n_iter: int, t_range=None, out=None):

@@ -7,10 +7,13 @@ right-hand side, with M^dagger = gamma_5 M gamma_5:
   with g = dloss/dconj(L) (PyTorch's convention for complex outputs),
   chi    = M^{-dagger} sum_{Gamma,t} g_{Gamma,t} Gamma^dagger P_t eta,
   grad_eta   = chi + sum_{Gamma,t} conj(g_{Gamma,t}) Gamma P_t phi,
-  grad_kappa = Re sum_j chi_j^dagger D phi_j        (dM^{-1}/dkappa = M^{-1} D M^{-1}).
+  grad_kappa = Re sum_j chi_j^dagger (-dM/dkappa) phi_j   (dM^{-1}/dkappa = -M^{-1} (dM/dkappa) M^{-1}),
+
+with -dM/dkappa = D for the Wilson matrix and D + c_sw sum sigma F with the
+clover term.
 
 Every arithmetic step runs in the library's kernels (solve, adjoint solve,
-Gamma-weighted spin matrices, Wilson hop, contraction); this module only
+Gamma-weighted spin matrices, -dM/dkappa, contraction); this module only
 passes tensors between them.
 """
 
@@ -46,8 +49,8 @@ class LoopTrace(torch.autograd.Function):
         chi, _ = ctx.solve_adjoint(src, fctx.params)
         grad_kappa = None
         if fctx.needs_input_grad[1]:
-            dphi = ctx.apply_hop(phi)
-            tr = ctx.trace_loops(chi, dphi, SINK_LOCAL, sum_rhs=True, sum_t=True)  # sum_j chi_j^dag D phi_j
+            dphi = ctx.apply_dm_dkappa(phi)
+            tr = ctx.trace_loops(chi, dphi, SINK_LOCAL, sum_rhs=True, sum_t=True)  # sum_j chi_j^dag (-dM/dk) phi_j
             grad_kappa = torch.tensor(float(tr[0, 0, 0, 0].real), dtype=kappa.dtype, device=kappa.device)
         grad_eta = None
         if fctx.needs_input_grad[0]:

@@ -90,6 +90,13 @@ struct dl_ctx {
     bool poisoned = false;         // a staged hop may have left bulk copies pending: no further work
     bool skip_inactive = true;     // direct hops skip right-hand sides that stopped (DLOOPS_HOP_SKIP=0: off)
     double2 *d_gammas = nullptr;  // [16][4][4]
+    // clover term (c_sw != 0): A and A^-1 per site, [2][Vh][2 blocks][6][6] complex
+    double csw = 0.0;
+    bool clover_stale = true;        // rebuild before the next use (links, kappa or c_sw changed)
+    double2 *d_clov64 = nullptr;     // A (FP64)
+    double2 *d_clovinv64 = nullptr;  // A^-1 in FP64, FP32 and BF16
+    float2 *d_clovinv32 = nullptr;
+    bf16 *d_clovinv16 = nullptr;
 
     // batch workspace, width ws_N (power of two)
     int ws_N = 0;
@@ -208,10 +215,13 @@ static void record(dl_ctx *c, cudaEvent_t e) {
 
 // Wilson hop launch.  kind >= 0 marks launches timed with CUDA events.
 // P_DFF: `in` is float-float; ffmt flags FF_Y / FF_OUT give the formats of y and out.
+// clov: the clover solve's inner hop A^-1 D (A^-1 of the output parity p in the epilogue;
+// FP64, FP32 or BF16 storage, the direct kernel with one right-hand side per thread).
 static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void *in, const void *y, const void *z,
                   const void *rhat, int p, int N, double coef, int cb0, int cb1, double2 *partials, int *nblocks,
-                  int ffmt = 0, const RhsState *act = nullptr) {
+                  int ffmt = 0, const RhsState *act = nullptr, bool clov = false) {
     if (c->poisoned) return fail(DL_ECUDA, "context unusable: a staged hop left bulk copies pending");
+    if (clov && (prec == P_DFF || !c->d_clovinv64)) return fail(DL_EINVAL, "clover hop: no A^-1 for this storage");
     HopArgs a;
     a.out = out;
     a.in = in;
@@ -238,14 +248,18 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     // per-RHS participation flags (BiCGStab inner iterations): next_active holds for the whole iteration
     a.act = act && c->skip_inactive ? &act[0].next_active : nullptr;
     a.act_stride = (int)(sizeof(RhsState) / sizeof(int));
-    int R = wide ? 1 : c->hop_R[prec][ilog2(N)];
+    a.clovinv = !clov ? nullptr
+                : prec == P_F64 ? (const void *)c->d_clovinv64
+                : prec == P_F32 ? (const void *)c->d_clovinv32
+                                : (const void *)c->d_clovinv16;
+    int R = (wide || clov) ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
     const int G = N / R;
     int block = prec == P_DFF ? 192 : c->hop_block[prec][ilog2(N)];  // P_DFF: a multiple of 3 N
     if (block % G) block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G * (prec == P_DFF ? 3 : 1);
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
-    const int kind = wide ? 0 : c->hop_kind[prec][ilog2(N)];
+    const int kind = (wide || clov) ? 0 : c->hop_kind[prec][ilog2(N)];
     size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (wide ? 16 : 8) : 0;
     int per_sm = wide ? 4 : 8;
     long items = total;
@@ -646,7 +660,7 @@ extern "C" int dl_destroy(dl_ctx *c) {
     }
     void *ptrs[] = {c->d_coords,   c->d_gauge64, c->d_gauge32,  c->d_gauge16, c->d_gauge8_32, c->d_gauge8_16, c->d_gauge8q,
                     c->d_gauge_ff, c->d_gammas,  c->d_partials, c->d_acc,     c->d_noise,     c->d_w,
-                    c->d_tcol,     c->d_acc2};
+                    c->d_tcol,     c->d_acc2,    c->d_clov64,   c->d_clovinv64, c->d_clovinv32, c->d_clovinv16};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (dl_ctx::Scratch *sc : {&c->s_phase, &c->s_site, &c->s_msum, &c->s_mloops, &c->s_mgroup, &c->s_mom,
@@ -711,15 +725,89 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
     }
     cudaFree(tmp);
     if (rc == DL_OK) c->have_gauge = true;
+    c->clover_stale = true;
     return rc;
 }
 
 extern "C" int dl_set_kappa(dl_ctx *c, double kappa) {
     if (!c) return fail(DL_EINVAL, "null context");
     if (!std::isfinite(kappa)) return fail(DL_EINVAL, "kappa must be finite");
-    if (kappa != c->kappa) invalidate_graphs(c);
+    if (kappa != c->kappa) {
+        invalidate_graphs(c);
+        c->clover_stale = true;
+    }
     c->kappa = kappa;
     c->have_kappa = true;
+    return DL_OK;
+}
+
+// Clover term: A = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu} per site,
+// built from the FP64 links before the next operation that needs it.
+extern "C" int dl_set_clover(dl_ctx *c, double c_sw) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!std::isfinite(c_sw)) return fail(DL_EINVAL, "c_sw must be finite");
+    if (c_sw != c->csw) {
+        CK(cudaStreamSynchronize(c->stream));
+        invalidate_graphs(c);  // the inner hops change kernel
+        c->clover_stale = true;
+    }
+    c->csw = c_sw;
+    return DL_OK;
+}
+
+// The clover blocks for the current links, kappa and c_sw (no-op without clover or
+// when they are current).  sigma_{mu nu} = (i/2)[g_mu, g_nu] from the context's
+// chiral gamma matrices, whose 2 x 2 spin blocks are all it keeps.
+static int ensure_clover(dl_ctx *c) {
+    if (c->csw == 0.0 || !c->clover_stale) return DL_OK;
+    const size_t n = (size_t)c->V * 72;  // complex entries
+    if (!c->d_clov64) {
+        if (cudaMalloc((void **)&c->d_clov64, n * sizeof(double2)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_clovinv64, n * sizeof(double2)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_clovinv32, n * sizeof(float2)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_clovinv16, n * 2 * sizeof(bf16)) != cudaSuccess)
+            return fail(DL_ENOMEM, "clover allocation failed");
+    }
+    zc gam[16][4][4];
+    gamma_basis(gam);
+    SigmaBlocks sig;
+    int plane = 0;
+    for (int mu = 0; mu < 4; ++mu)
+        for (int nu = mu + 1; nu < 4; ++nu, ++plane) {
+            zc sg[4][4];
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    zc v = 0;
+                    for (int k = 0; k < 4; ++k) v += gam[1 + mu][i][k] * gam[1 + nu][k][j] - gam[1 + nu][i][k] * gam[1 + mu][k][j];
+                    sg[i][j] = zc(0, 0.5) * v;
+                }
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
+                    if (i / 2 != j / 2 && std::abs(sg[i][j]) > 1e-12)
+                        return fail(DL_EINVAL, "clover: sigma_{mu nu} is not block-diagonal in this gamma basis");
+            for (int b = 0; b < 2; ++b)
+                for (int s1 = 0; s1 < 2; ++s1)
+                    for (int s2 = 0; s2 < 2; ++s2) {
+                        const zc v = sg[2 * b + s1][2 * b + s2];
+                        sig.s[plane][b][s1][s2] = make_double2(v.real(), v.imag());
+                    }
+        }
+    const int grid = (int)std::max<long>(1, std::min<long>((c->V + 127) / 128, (long)c->num_sms * 4));
+    CK(launch_clover_build(c->d_gauge64, c->g, sig, c->kappa * c->csw, c->d_clov64, c->d_clovinv64, c->d_clovinv32,
+                           reinterpret_cast<__nv_bfloat162 *>(c->d_clovinv16), grid, c->stream));
+    c->kernel_launches++;
+    c->clover_stale = false;
+    return DL_OK;
+}
+
+// out = mat in on the half field of parity p (width N; in place allowed); with
+// acc_s != 0, out += acc_s (in - mat in).
+static int clover_mul(dl_ctx *c, const double2 *mat, int p, int N, const double *in, double *out,
+                      double acc_s = 0.0) {
+    const long items = c->Vh * 2L * N;
+    const int grid = (int)std::max<long>(1, std::min<long>((items + 255) / 256, (long)c->num_sms * 8));
+    CK(launch_clover_mul(mat, p, (int)c->Vh, N, in, out, acc_s, grid, c->cur));
+    c->kernel_launches++;
     return DL_OK;
 }
 
@@ -793,17 +881,18 @@ static int enqueue_iteration(dl_ctx *c, int prec, int N) {
     double2 *part = c->d_partials;
     int nb = 0;
     const RhsState *act = c->d_rhs;  // right-hand sides that stopped skip the direct hops' loads and stores
+    const bool cl = c->csw != 0.0;   // clover: Mhat = 1 - kappa^2 A_ee^-1 D_eo A_oo^-1 D_oe
     TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
-               Vh, nullptr, nullptr, 0, act));
+               Vh, nullptr, nullptr, 0, act, cl));
     TRY(do_hop(c, prec, MODE_XPAY, RED_R0DOT, lo_ptr(c, LV), lo_ptr(c, LTMP), lo_ptr(c, LP), nullptr,
-               lo_ptr(c, LRH), 0, N, -k2, 0, Vh, part, &nb, 0, act));
+               lo_ptr(c, LRH), 0, N, -k2, 0, Vh, part, &nb, 0, act, cl));
     scalar_alpha_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, part, nb, N);
     VecLaunch v = vec_launch(c, prec, N, 0);
     CK(launch_axpy_s(v, c->d_rhs, lo_ptr(c, LR), lo_ptr(c, LV), lo_ptr(c, LS)));
     TRY(do_hop(c, prec, MODE_PLAIN, RED_NONE, lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, nullptr, nullptr, 1, N, 1.0, 0,
-               Vh, nullptr, nullptr, 0, act));
+               Vh, nullptr, nullptr, 0, act, cl));
     TRY(do_hop(c, prec, MODE_XPAY, RED_BICG, lo_ptr(c, LT), lo_ptr(c, LTMP), lo_ptr(c, LS), nullptr, lo_ptr(c, LRH),
-               0, N, -k2, 0, Vh, part, &nb, 0, act));
+               0, N, -k2, 0, Vh, part, &nb, 0, act, cl));
     scalar_omega_kernel<<<N, kScalarThreads, 0, c->cur>>>(c->d_rhs, part, nb, N);
     CK(launch_update(v, c->d_rhs, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LP), lo_ptr(c, LS), lo_ptr(c, LT),
                      lo_ptr(c, LV)));
@@ -965,12 +1054,13 @@ static int read_params(const dl_solve_params *p, SolveCfg *s) {
     return DL_OK;
 }
 
+// State check before a solve; brings the clover blocks up to date.
 static int ready(dl_ctx *c) {
     if (!c) return fail(DL_EINVAL, "null context");
     if (c->poisoned) return fail(DL_ECUDA, "context unusable: a staged hop left bulk copies pending");
     if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
     if (!c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
-    return DL_OK;
+    return ensure_clover(c);
 }
 
 // FP64 <-> float-float copy of n_complex values (in place when dst == src).
@@ -988,10 +1078,18 @@ static int ff_cast(dl_ctx *c, const double *src, double *dst, size_t n_complex, 
 // the next cycle and the full-lattice residual; the final solution needs no
 // further hop.  op = P_DFF: b_o is float-float, x_o is left float-float and x_e
 // is first copied to float-float in c->bh64.
+// Clover (op = P_F64): x_o = t + kappa A_oo^-1 D_oe x_e with t = A_oo^-1 b_o held in
+// c->t64, and r = b_e - A_ee x_e + kappa D_eo x_o with A_ee x_e formed in c->bh64.
 static int outer_residual(dl_ctx *c, int op, int N, const double *be, const double *bo, const double *xe,
                           double *xo, double2 *pa, int *nb) {
     const double k = c->kappa;
     const int Vh = (int)c->Vh;
+    if (c->csw != 0.0) {
+        TRY(do_hop(c, P_F64, MODE_XPAY, RED_NONE, xo, xe, c->t64, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr,
+                   0, nullptr, true));
+        TRY(clover_mul(c, c->d_clov64, 0, N, xe, c->bh64));
+        return do_hop(c, P_F64, MODE_RESID, RED_NORM, c->r64, xo, c->bh64, be, nullptr, 0, N, -k, 0, Vh, pa, nb);
+    }
     if (op == P_DFF) {
         TRY(ff_cast(c, xe, c->bh64, half_elems(c, N), 1));
         TRY(do_hop(c, op, MODE_XPAY, RED_NONE, xo, c->bh64, bo, nullptr, nullptr, 1, N, k, 0, Vh, nullptr, nullptr,
@@ -1011,7 +1109,10 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
     // rounding (~1e-14 relative), else in FP64.  In float-float, b_o and x_o are
     // held as float-float fields until the batch ends and x_e is copied to that
     // format (into the bhat buffer, free once r = bhat) before each residual.
-    const int op = (P.prec != P_F64 && P.outer_dff && P.tol >= kFFMinTol) ? P_DFF : P_F64;
+    const bool clov = c->csw != 0.0;
+    if (clov && P.method == DL_METHOD_CGNR)  // A_ee^-1 Mhat is not gamma_5-hermitian: CGNR's gamma_5 trick fails
+        return fail(DL_EINVAL, "the clover operator is solved with BiCGStab only");
+    const int op = (!clov && P.prec != P_F64 && P.outer_dff && P.tol >= kFFMinTol) ? P_DFF : P_F64;
     const bool ffo = op == P_DFF;
     const int Vh = (int)c->Vh;
     const size_t half = half_elems(c, N) * 2;  // doubles
@@ -1042,9 +1143,10 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
             c->kernel_launches += 3;
         }
     }
-    // bhat = b_e + kappa D_eo b_o, |bhat|^2
+    // bhat = b_e + kappa D_eo b_o, |bhat|^2 (clover: b_o replaced by t = A_oo^-1 b_o, kept in c->t64)
     if (ffo) TRY(ff_cast(c, bo, bo, half / 2, 1));
-    TRY(do_hop(c, op, MODE_XPAY, RED_NORM, c->bh64, bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
+    if (clov) TRY(clover_mul(c, c->d_clovinv64, 1, N, bo, c->t64));
+    TRY(do_hop(c, op, MODE_XPAY, RED_NORM, c->bh64, clov ? c->t64 : bo, be, nullptr, nullptr, 0, N, k, 0, Vh, pa, &nb));
     outer_update_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_outer, c->d_rhs, pa, nb, N, 0, P.tol, P.max_outer, P.max_iter);
     c->kernel_launches++;
     CK(cudaMemcpyAsync(c->r64, c->bh64, half * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -1070,9 +1172,11 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
             CK(launch_cg_p(vec_launch(c, prec, N, 0), c->d_rhs, lo_ptr(c, LRH), lo_ptr(c, LP), 1));
             c->kernel_launches += 3;
         } else {
+            // clover: the inner system is A_ee^-1 Mhat, its source A_ee^-1 r (in c->bh64)
+            if (clov) TRY(clover_mul(c, c->d_clovinv64, 0, N, c->r64, c->bh64));
             VecLaunch v = vec_launch(c, prec, N, 2 * (prec == P_F64 ? 16 : 8));
-            CK(launch_inner_init(v, c->d_outer, c->d_rhs, c->r64, lo_ptr(c, LX), lo_ptr(c, LR), lo_ptr(c, LRH),
-                                 lo_ptr(c, LP), pa, (cycle == 0 || P.restart) ? 1 : 0));
+            CK(launch_inner_init(v, c->d_outer, c->d_rhs, clov ? c->bh64 : c->r64, lo_ptr(c, LX), lo_ptr(c, LR),
+                                 lo_ptr(c, LRH), lo_ptr(c, LP), pa, (cycle == 0 || P.restart) ? 1 : 0));
             inner_start_kernel<<<N, kScalarThreads, 0, c->stream>>>(c->d_rhs, c->d_outer, pa, v.l.grid, N, P.delta, target,
                                                         P.max_iter, P.fixed_iters > 0 ? 1 : 0);
             c->kernel_launches += 2;
@@ -1230,10 +1334,16 @@ extern "C" int dl_make_point_sources(dl_ctx *c, int64_t first, int n, int prec, 
 // ---------------------------------------------------------------------------
 // operators on canonical fields
 // ---------------------------------------------------------------------------
-static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool with_m) {
+enum { OP_D = 0, OP_M = 1, OP_DMDK = 2 };  // D, M, -dM/dkappa
+
+static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, int what) {
     if (!c) return fail(DL_EINVAL, "null context");
     if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
-    if (with_m && !c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
+    const bool with_m = what == OP_M;
+    if (what != OP_D && !c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
+    // -dM/dkappa = D + c_sw sum sigma F = D + (1 - A) / kappa
+    const bool dmdk_clov = what == OP_DMDK && c->csw != 0.0;
+    if (dmdk_clov && c->kappa == 0.0) return fail(DL_EINVAL, "dM/dkappa with clover needs kappa != 0");
     if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
     if (n_rhs == 0) return DL_OK;
     if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
@@ -1245,11 +1355,33 @@ static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool 
     const int mode = with_m ? MODE_XPAY : MODE_PLAIN;
     const double coef = with_m ? -c->kappa : 1.0;
     const char *ar = getenv("DLOOPS_HOP_ARITH");
-    const int op = (ar && std::string(ar) == "dff") ? P_DFF : P_F64;
+    const bool clov = with_m && c->csw != 0.0;  // M = A - kappa D: y = A in (c->s64a), FP64
+    const int op = (!clov && !dmdk_clov && ar && std::string(ar) == "dff") ? P_DFF : P_F64;
+    if (clov || dmdk_clov) TRY(ensure_clover(c));
     for (int j0 = 0; j0 < n_rhs; j0 += N) {
         const int n = std::min(N, n_rhs - j0);
         c->cur = c->stream;
         TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
+        if (clov) {
+            TRY(clover_mul(c, c->d_clov64, 0, N, c->b64, c->s64a));
+            TRY(clover_mul(c, c->d_clov64, 1, N, c->b64 + half, c->s64a + half));
+            TRY(do_hop(c, op, mode, RED_NONE, c->x64, c->b64 + half, c->s64a, nullptr, nullptr, 0, N, coef, 0, Vh,
+                       nullptr, nullptr));
+            TRY(do_hop(c, op, mode, RED_NONE, c->x64 + half, c->b64, c->s64a + half, nullptr, nullptr, 1, N, coef, 0,
+                       Vh, nullptr, nullptr));
+            TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
+            continue;
+        }
+        if (dmdk_clov) {  // D in, then += (in - A in) / kappa on each half
+            TRY(do_hop(c, op, MODE_PLAIN, RED_NONE, c->x64, c->b64 + half, nullptr, nullptr, nullptr, 0, N, 1.0, 0, Vh,
+                       nullptr, nullptr));
+            TRY(do_hop(c, op, MODE_PLAIN, RED_NONE, c->x64 + half, c->b64, nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh,
+                       nullptr, nullptr));
+            TRY(clover_mul(c, c->d_clov64, 0, N, c->b64, c->x64, 1.0 / c->kappa));
+            TRY(clover_mul(c, c->d_clov64, 1, N, c->b64 + half, c->x64 + half, 1.0 / c->kappa));
+            TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
+            continue;
+        }
         // float-float: each half is converted in place before it is gathered
         if (op == P_DFF) TRY(ff_cast(c, c->b64 + half, c->b64 + half, half / 2, 1));
         TRY(do_hop(c, op, mode, RED_NONE, c->x64, c->b64 + half, c->b64, nullptr, nullptr, 0, N, coef, 0, Vh,
@@ -1262,7 +1394,7 @@ static int apply_hop_impl(dl_ctx *c, const void *in, void *out, int n_rhs, bool 
     return DL_OK;
 }
 
-extern "C" int dl_apply_hop(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, false); }
+extern "C" int dl_apply_hop(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, OP_D); }
 
 // out = D in with the inner solver's low-precision hop: both halves of `in`
 // rounded to the storage type, the FP32/BF16 link copies, FP32 arithmetic, the
@@ -1270,7 +1402,7 @@ extern "C" int dl_apply_hop(dl_ctx *c, const void *in, void *out, int n) { retur
 // result widened back to FP64.
 extern "C" int dl_apply_hop_prec(dl_ctx *c, int precision, const void *in, void *out, int n_rhs) {
     if (!c) return fail(DL_EINVAL, "null context");
-    if (precision == DL_PREC_F64) return apply_hop_impl(c, in, out, n_rhs, false);
+    if (precision == DL_PREC_F64) return apply_hop_impl(c, in, out, n_rhs, OP_D);
     if (precision != DL_PREC_F32 && precision != DL_PREC_BF16) return fail(DL_EINVAL, "unknown precision");
     if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
     if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
@@ -1300,7 +1432,40 @@ extern "C" int dl_apply_hop_prec(dl_ctx *c, int precision, const void *in, void 
     }
     return DL_OK;
 }
-extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, true); }
+extern "C" int dl_apply_m(dl_ctx *c, const void *in, void *out, int n) { return apply_hop_impl(c, in, out, n, OP_M); }
+extern "C" int dl_apply_dm_dkappa(dl_ctx *c, const void *in, void *out, int n) {
+    return apply_hop_impl(c, in, out, n, OP_DMDK);
+}
+
+// out = A in or A^-1 in, site by site (the identity without clover).
+extern "C" int dl_apply_clover(dl_ctx *c, const void *in, void *out, int n_rhs, int inverse) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (!c->have_gauge) return fail(DL_ESTATE, "load_gauge has not been called");
+    if (!c->have_kappa) return fail(DL_ESTATE, "set_kappa has not been called");
+    if (n_rhs < 0) return fail(DL_EINVAL, "n_rhs < 0");
+    if (n_rhs == 0) return DL_OK;
+    if (!in || !out || in == out) return fail(DL_EINVAL, "bad field pointers");
+    const size_t field = (size_t)c->V * 24;
+    c->cur = c->stream;
+    if (c->csw == 0.0) {
+        CK(cudaMemcpyAsync(out, in, (size_t)n_rhs * field * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        return DL_OK;
+    }
+    TRY(ensure_clover(c));
+    const int N = std::min(64, pow2_at_least(n_rhs));
+    TRY(ensure_ws(c, N));
+    const size_t half = half_elems(c, N) * 2;
+    const int Vh = (int)c->Vh;
+    const double2 *mat = inverse ? c->d_clovinv64 : c->d_clov64;
+    for (int j0 = 0; j0 < n_rhs; j0 += N) {
+        const int n = std::min(N, n_rhs - j0);
+        TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
+        TRY(clover_mul(c, mat, 0, N, c->b64, c->x64));
+        TRY(clover_mul(c, mat, 1, N, c->b64 + half, c->x64 + half));
+        TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
+    }
+    return DL_OK;
+}
 
 // Smear the EO fields at *buf (full field, width N) over cb range; returns the
 // buffer holding the result (ping-pong with `spare`).

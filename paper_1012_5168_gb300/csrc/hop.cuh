@@ -28,6 +28,7 @@
 //   NORM: <out, out>   (<a, b> = sum conj(a) b).
 #pragma once
 
+#include "clover.cuh"
 #include "common.cuh"
 
 namespace dl {
@@ -61,6 +62,8 @@ struct HopArgs {
                             // (backward, already conjugated): the packed-arithmetic kernel's links
     const int *act;         // per right-hand side r: act[r * act_stride] != 0 if it takes part in this
     int act_stride;         // iteration; NULL: all do.  The direct kernels skip the others' loads and stores.
+    const void *clovinv;    // clover: A^-1 of the output sites in the storage type ([2][Vh][2][6][6]
+                            // complex), applied to D in before the epilogue; NULL: no clover term
 };
 
 // Load the 12 components of R right-hand sides at one neighbour site and
@@ -274,7 +277,7 @@ __device__ __forceinline__ void hop_dir_x2(const HopArgs &A, const Site &st, int
 // NC > 0: the number of right-hand sides in the layout is the compile-time
 // constant NC (= A.N), so component offsets fold into the load and store
 // instructions; NC = 0 reads it from A.N.
-template <typename S, int R, int MODE, int RED, int NC = 0, int X2 = 0>
+template <typename S, int R, int MODE, int RED, int NC = 0, int X2 = 0, int CLOV = 0>
 __device__ __forceinline__ void hop_body(const HopArgs &A) {
     typedef typename Real<S>::type T;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
@@ -337,6 +340,9 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
             hop_dir<S, R, 1, NC>(A, st, cb, r0, acc);
             hop_dir<S, R, 2, NC>(A, st, cb, r0, acc);
             hop_dir<S, R, 3, NC>(A, st, cb, r0, acc);
+            if constexpr (CLOV != 0 && R == 1)  // clover: A^-1 of the output site on D in
+                clover_inv_apply<S, T>(reinterpret_cast<const S *>(A.clovinv) + ((size_t)A.p * A.g.Vh + cb) * 72 * 2,
+                                       acc[0]);
         }
 
         const size_t base = (size_t)cb * 12 * N * 2 + (size_t)r0 * 2;
@@ -411,6 +417,13 @@ __global__ void __launch_bounds__(256) hop_kernel(HopArgs A) {
 template <typename S, int R, int MODE, int RED, int CAP, int NC = 0>
 __global__ void __maxnreg__(CAP) hop_kernel_cap(HopArgs A) {
     hop_body<S, R, MODE, RED, NC>(A);
+}
+
+// Clover direct kernel (one right-hand side per thread): the inner hops of the
+// clover operator's asymmetric Schur system, A^-1 D.
+template <typename S, int MODE, int RED>
+__global__ void __launch_bounds__(256) hop_kernel_clov(HopArgs A) {
+    hop_body<S, 1, MODE, RED, 0, 0, 1>(A);
 }
 
 // Packed-arithmetic direct kernel (FP32 storage, one right-hand side per thread).

@@ -7,6 +7,11 @@ namespace dl {
 
 template <int R, int MODE, int RED>
 static cudaError_t go(const HopArgs &a, Launch &l) {
+    if (a.clovinv) {  // clover: A^-1 of the output site in the epilogue
+        clamp_grid(l, resident_blocks(hop_kernel_clov<double, MODE, RED>, l.block, l.smem));
+        hop_kernel_clov<double, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+        return cudaGetLastError();
+    }
     clamp_grid(l, resident_blocks(hop_kernel<double, R, MODE, RED>, l.block, l.smem));
     hop_kernel<double, R, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
     return cudaGetLastError();

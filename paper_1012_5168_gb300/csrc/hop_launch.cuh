@@ -30,6 +30,14 @@ inline cudaError_t opt_in_smem(K kernel, size_t smem, size_t &opted, std::mutex 
 
 template <typename S, int R, int MODE, int RED>
 cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
+    if (a.clovinv) {  // clover: the direct kernel with A^-1 in the epilogue, one right-hand side per thread
+        if constexpr (R == 1) {
+            clamp_grid(l, resident_blocks(hop_kernel_clov<S, MODE, RED>, l.block, l.smem));
+            hop_kernel_clov<S, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     constexpr int cap = HopRegCap<S, R, MODE, RED>::n;
     auto direct = [] {
         if constexpr (cap > 0) return hop_kernel_cap<S, R, MODE, RED, cap>;

@@ -138,5 +138,13 @@ cudaError_t launch_cg_update(const VecLaunch &v, const RhsState *st, void *x, vo
 cudaError_t launch_cg_p(const VecLaunch &v, const RhsState *st, const void *u, void *p, int init);
 cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cudaStream_t s);
 cudaError_t launch_cast(int prec, double *f64, void *lo, size_t n_complex, int to_lo, int grid, cudaStream_t s);
+// Clover term (clover.cu): the blocks A = 1 - kappa c_sw sum sigma F and their inverses
+// from the FP64 links (kcsw = kappa c_sw), and out = mat x in on one parity's half field
+// ([Vh][12][N] complex doubles; in place allowed), or, for acc_s != 0,
+// out += acc_s (in - mat x in).
+cudaError_t launch_clover_build(const double *g64, const Geom &g, const SigmaBlocks &sig, double kcsw, double2 *a64,
+                               double2 *ainv64, float2 *ainv32, __nv_bfloat162 *ainv16, int grid, cudaStream_t s);
+cudaError_t launch_clover_mul(const double2 *mat, int p, int Vh, int N, const double *in, double *out, double acc_s,
+                             int grid, cudaStream_t s);
 
 }  // namespace dl
