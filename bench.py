@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--workload", default="stochastic",
                     choices=["stochastic", "exact_4x4x4x4", "single_rhs_16x16x16x32", "tsm_8x8x8x16",
                              "autograd", "correlators_16x16x16x32", "dilution_8x8x8x16",
-                             "batch_scan_16x16x16x32", "tsm_16x16x16x32", "mixed_16x16x16x32"],
+                             "batch_scan_16x16x16x32", "tsm_16x16x16x32", "mixed_16x16x16x32",
+                             "clover_16x16x16x32"],
                     help="stochastic: the benchmark line (default); the others measure the remaining "
                          "configurations and print one JSON line each")
     ap.add_argument("--smear-profile", metavar="N", type=int, default=None,
@@ -511,6 +512,56 @@ def workload_mixed():
     print(json.dumps(out), flush=True)
 
 
+def workload_clover():
+    """The clover-improved operator M = A - kappa D against the Wilson matrix on the benchmark lattice
+    (16^3 x 32, eps 0.45 links), kappa 0.13, c_sw 1.0: 32 time-diluted complex Z2 sources, FP32 inner
+    solve with FP64 defect correction to 1e-10, width 32.  Each operator: a warm-up solve, then the best
+    of three timed solves, the iterations, and the inner hops' CUDA-event timing (the clover hops also
+    stream A^-1 of every output site: 576 B in FP32)."""
+    import torch
+    import paper_1012_5168_gb300 as dl
+    import synthetic
+    w = synthetic.WORKLOADS["wilson_16x16x16x32"]
+    U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
+    peak, src = read_peaks()
+    kappa, csw = 0.13, 1.0
+    out = {"workload": "clover_16x16x16x32", "kappa": kappa, "c_sw": csw, "eps": w["eps"], "batch": 32,
+           "tol": 1e-10, "runs": {}}
+    for name, c_sw in (("wilson", 0.0), ("clover", csw)):
+        ctx = dl.Context(w["dims"], t_bc=-1)
+        ctx.load_gauge(U)
+        ctx.set_kappa(kappa)
+        ctx.set_clover(c_sw)
+        b = ctx.make_sources(seed=9, noise_first=0, n_noise=32, dilution=dl.DIL_TIME, t0=-1)
+        p = dl.Params(tol=1e-10, precision=dl.PREC_F32, batch=32)
+        ctx.solve(b, p)
+        ctx.set_timing(True)
+        times = []
+        for _ in range(3):
+            ctx.get_timing(reset=True)
+            torch.cuda.synchronize()
+            clocks = ClockSampler(torch.cuda.current_device())
+            t0 = time.perf_counter()
+            _, st = ctx.solve(b, p)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t0, clocks.stop(), ctx.get_timing(), st))
+        el, clk, tim, st = min(times, key=lambda x: x[0])
+        fused_ms = tim["hop_ms"][1] / max(1, tim["hop_launches"][1])
+        fused_gbs = tim["hop_bytes"][1] / max(1e-30, tim["hop_ms"][1] * 1e-3) / 1e9
+        out["runs"][name] = {
+            "seconds": round(el, 4), "solves_per_s": round(len(st) / el, 2), "clocks": clk,
+            "iters_max": max(s["iters"] for s in st), "iters_mean": round(sum(s["iters"] for s in st) / len(st), 1),
+            "outer": sorted(set(s["outer"] for s in st)), "max_true_residual": max(s["true_residual"] for s in st),
+            "status": sorted(set(s["status"] for s in st)),
+            "inner_fused_hop": {"ms_per_launch": round(fused_ms, 5), "GB/s": round(fused_gbs, 1),
+                                "frac_of_hbm_peak": round(fused_gbs / peak, 4), "peak_source": src + " hbm_gbs"}}
+        ctx.close()
+    r = out["runs"]
+    out["clover_cost_per_iteration"] = round((r["clover"]["seconds"] / r["clover"]["iters_max"]) /
+                                             (r["wilson"]["seconds"] / r["wilson"]["iters_max"]), 3)
+    print(json.dumps(out), flush=True)
+
+
 def workload_tsm_paper():
     """The truncated solver method at the paper's sizes (Sec. 2): 5000 low-precision solves
     (single-precision CG on the normal equations, tolerance 1e-6) and 500 high-precision corrections
@@ -706,7 +757,8 @@ def main():
                 "tsm_8x8x8x16": workload_tsm, "autograd": workload_autograd,
                 "correlators_16x16x16x32": workload_correlators,
                 "dilution_8x8x8x16": workload_dilution, "tsm_16x16x16x32": workload_tsm_paper,
-                "mixed_16x16x16x32": workload_mixed, "batch_scan_16x16x16x32": workload_batch_scan}[args.workload]()
+                "mixed_16x16x16x32": workload_mixed, "batch_scan_16x16x16x32": workload_batch_scan,
+                "clover_16x16x16x32": workload_clover}[args.workload]()
     if args.impl == "reference":
         return reference_arm(args, rank, world)
 
