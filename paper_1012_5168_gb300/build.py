@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libdloops.so")
 UNITS = ["api.cu", "hop_f64.cu", "hop_f32.cu", "hop_f32_r2.cu", "hop_f32_r4.cu", "hop_bf16.cu", "hop_bf16_r2.cu",
-         "hop_bf16_r4.cu", "vec.cu", "noalloc.cu", "peak.cu", "clover.cu"]
+         "hop_bf16_r4.cu", "vec.cu", "noalloc.cu", "peak.cu", "clover.cu", "hop_f32p.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -85,6 +85,8 @@ struct dl_ctx {
     float *d_gauge8_32 = nullptr;  // site-major links (staged hop)
     bf16 *d_gauge8_16 = nullptr;
     float4 *d_gauge8q = nullptr;   // FP32 link quads of the packed-arithmetic hop
+    float4 *d_gauge8d = nullptr;   // FP32 link quads (Re, Re, Im, Im) of the paired-layout hop
+    bool f32_pairs = false;        // FP32 inner fields of even width in the paired layout (DLOOPS_F32_PAIRS=1)
     int *h_err = nullptr;          // pinned, mapped [2]: set by the staged hop on a wait timeout
     int *d_err = nullptr;
     bool poisoned = false;         // a staged hop may have left bulk copies pending: no further work
@@ -134,11 +136,13 @@ struct dl_ctx {
     std::vector<cudaEvent_t> event_pool;
     dl_timing tim;
     int64_t kernel_launches = 0;
-    int hop_R[3][8];      // right-hand sides per thread, [prec][log2 N]
-    int hop_block[3][8];  // threads per block
-    int hop_kind[3][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
-                          // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic
-    bool hop_tuned[3][8];
+    int hop_R[5][8];      // right-hand sides per thread, [prec][log2 N]
+    int hop_block[5][8];  // threads per block
+    int hop_kind[5][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
+                          // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic, 7 paired layout with
+                          // packed FP32 arithmetic, 8 the same under a 128-register cap, 9 paired and
+                          // warp-staged
+    bool hop_tuned[5][8];
     bool autotune = true;
 };
 
@@ -166,7 +170,15 @@ static Launch make_launch(dl_ctx *c, long items, int block, size_t smem, int per
 
 static size_t half_elems(dl_ctx *c, int N) { return (size_t)c->Vh * 12 * N; }  // complex per half field
 
-static int storage_bytes(int prec) { return (prec == P_F64 || prec == P_DFF) ? 8 : (prec == P_F32 ? 4 : 2); }
+static int storage_bytes(int prec) {
+    return (prec == P_F64 || prec == P_DFF) ? 8 : ((prec == P_F32 || prec == P_F32P) ? 4 : 2);
+}
+
+// The storage of a solve's inner fields: FP32 of even width in the paired layout
+// (two right-hand sides per 16-byte group) when the context uses it.
+static int inner_prec(const dl_ctx *c, int prec, int N) {
+    return (prec == P_F32 && c->f32_pairs && N >= 2) ? P_F32P : prec;
+}
 
 static cudaEvent_t get_event(dl_ctx *c) {
     if (!c->event_pool.empty()) {
@@ -229,9 +241,10 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.z = z;
     a.rhat = rhat;
     const bool wide = prec == P_F64 || prec == P_DFF;  // FP64 fields, one right-hand side per thread
+    const bool f32 = prec == P_F32 || prec == P_F32P;
     a.gauge = prec == P_F64   ? (const void *)c->d_gauge64
               : prec == P_DFF ? (const void *)c->d_gauge_ff
-              : prec == P_F32 ? (const void *)c->d_gauge32
+              : f32           ? (const void *)c->d_gauge32
                               : (const void *)c->d_gauge16;
     a.coords = c->d_coords;
     a.partials = partials;
@@ -241,7 +254,8 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.cb_end = cb1;
     a.c = coef;
     a.g = c->g;
-    a.gauge8 = prec == P_F32 ? (const void *)c->d_gauge8_32 : (prec == P_BF16 ? (const void *)c->d_gauge8_16 : nullptr);
+    a.gauge8 = f32 ? (const void *)c->d_gauge8_32 : (prec == P_BF16 ? (const void *)c->d_gauge8_16 : nullptr);
+    a.gauge8d = c->d_gauge8d;
     a.err = c->d_err;
     a.blocked = 0;
     a.gauge8q = c->d_gauge8q;
@@ -250,7 +264,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
     a.act_stride = (int)(sizeof(RhsState) / sizeof(int));
     a.clovinv = !clov ? nullptr
                 : prec == P_F64 ? (const void *)c->d_clovinv64
-                : prec == P_F32 ? (const void *)c->d_clovinv32
+                : f32           ? (const void *)c->d_clovinv32
                                 : (const void *)c->d_clovinv16;
     int R = (wide || clov) ? 1 : c->hop_R[prec][ilog2(N)];
     if (R > N) R = N;
@@ -286,12 +300,14 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
                       ((red == RED_R0DOT || red == RED_BICG) ? 1 : 0);
         if (red == RED_BICG && mode == MODE_PLAIN) streams += 1;
         tp.bytes = (double)(cb1 - cb0) * (8.0 * L + (double)N * streams * S);
+        if (clov) tp.bytes += (double)(cb1 - cb0) * 72.0 * 2.0 * storage_bytes(prec);  // A^-1 of each output site
         record(c, tp.a);
     }
     cudaError_t e;
     if (prec == P_F64) e = launch_hop_f64(R, mode, red, a, l);
     else if (prec == P_DFF) e = launch_hop_ff(mode, red, ffmt, a, l);
     else if (prec == P_F32) e = launch_hop_f32(R, mode, red, kind, a, l);
+    else if (prec == P_F32P) e = launch_hop_f32p(R, mode, red, kind, a, l);
     else e = launch_hop_bf16(R, mode, red, kind, a, l);
     if (e != cudaSuccess) return fail(DL_ECUDA, std::string("hop launch: ") + cudaGetErrorString(e));
     if (nblocks) *nblocks = l.grid;
@@ -439,8 +455,9 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // shape timed while the GPU was still ramping its clocks or finishing other
     // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 7); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 10); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
+        if (prec == P_F32P ? (pf != 0 && pf < 7) : pf >= 7) continue;  // the paired layout: kinds 0, 7, 8, 9
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
             if (prec == P_F64 && R != 1) continue;
@@ -453,6 +470,8 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                 if ((pf == 4 || pf == 5) && N != 32 * R) continue;         // one site per warp
                 if (pf == 5 && (prec != P_BF16 || R > 2)) continue;         // tensor cores: BF16 storage
                 if (pf == 6 && (prec != P_F32 || R != 1)) continue;         // packed FP32 arithmetic
+                if (pf >= 7 && R != 2) continue;                            // paired layout: two per thread
+                if (pf == 9 && (bi > 0 || (N != 32 && N != 64))) continue;  // warp-staged pairs: N = 32, 64
                 if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
                 c->hop_R[prec][l] = R;
                 c->hop_block[prec][l] = B;
@@ -483,20 +502,24 @@ extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int
     if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
     if (force_R < 0 || force_block < 0) return fail(DL_EINVAL, "bad forced shape");
     const int N = pow2_at_least(n_rhs);
-    TRY(tune_hop(c, precision, N, force_R, force_block, force_pf));
+    const int ip = inner_prec(c, precision, N);
+    if (force_pf >= 0 && (ip == P_F32P ? (force_pf != 0 && force_pf < 7) : force_pf >= 7))
+        return fail(DL_EINVAL, "kernel kind not available for this storage layout");
+    TRY(tune_hop(c, ip, N, force_R, force_block, force_pf));
     const int l = ilog2(N);
-    if (R_out) *R_out = c->hop_R[precision][l];
-    if (block_out) *block_out = c->hop_block[precision][l];
-    if (pf_out) *pf_out = c->hop_kind[precision][l];
+    if (R_out) *R_out = c->hop_R[ip][l];
+    if (block_out) *block_out = c->hop_block[ip][l];
+    if (pf_out) *pf_out = c->hop_kind[ip][l];
     if (ms_out) {
         float ms = 0.f;
-        TRY(time_hops(c, precision, N, 10, &ms));
+        TRY(time_hops(c, ip, N, 10, &ms));
         *ms_out = ms;
     }
     return DL_OK;
 }
 
 static int maybe_tune(dl_ctx *c, int prec, int N) {
+    prec = inner_prec(c, prec, N);
     if (!c->autotune || c->hop_tuned[prec][ilog2(N)]) return DL_OK;
     return tune_hop(c, prec, N, 0, 0, -1);
 }
@@ -582,6 +605,8 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
         c->smear_fp64 = e && e[0] == '1';
         const char *k = getenv("DLOOPS_HOP_SKIP");
         c->skip_inactive = !(k && k[0] == '0');
+        const char *pr = getenv("DLOOPS_F32_PAIRS");
+        c->f32_pairs = pr && pr[0] == '1';
     }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     c->stream = (cudaStream_t)cuda_stream;
@@ -601,7 +626,7 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     c->g.V3h = dims[0] * dims[1] * dims[2] / 2;
     c->g.t_bc = t_bc;
     memset(&c->tim, 0, sizeof(c->tim));
-    for (int p = 0; p < 3; ++p)
+    for (int p = 0; p < 5; ++p)
         for (int l = 0; l < 8; ++l) {
             c->hop_R[p][l] = 2;
             c->hop_block[p][l] = 128;
@@ -659,6 +684,7 @@ extern "C" int dl_destroy(dl_ctx *c) {
         cudaEventDestroy(tp.b);
     }
     void *ptrs[] = {c->d_coords,   c->d_gauge64, c->d_gauge32,  c->d_gauge16, c->d_gauge8_32, c->d_gauge8_16, c->d_gauge8q,
+                    c->d_gauge8d,
                     c->d_gauge_ff, c->d_gammas,  c->d_partials, c->d_acc,     c->d_noise,     c->d_w,
                     c->d_tcol,     c->d_acc2,    c->d_clov64,   c->d_clovinv64, c->d_clovinv32, c->d_clovinv16};
     for (void *p : ptrs)
@@ -701,6 +727,7 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
             cudaMalloc((void **)&c->d_gauge8_32, 2 * n64 * sizeof(float)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge8_16, 2 * n64 * sizeof(bf16)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge8q, (size_t)c->V * 72 * sizeof(float4)) != cudaSuccess ||
+            cudaMalloc((void **)&c->d_gauge8d, (size_t)c->V * 72 * sizeof(float4)) != cudaSuccess ||
             cudaMalloc((void **)&c->d_gauge_ff, 2 * n64 * sizeof(float)) != cudaSuccess)
             return fail(DL_ENOMEM, "gauge allocation failed");
     }
@@ -718,8 +745,9 @@ extern "C" int dl_load_gauge(dl_ctx *c, const double *U, int check) {
         gauge8_kernel<float><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8_32);
         gauge8_kernel<bf16><<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8_16);
         gauge8q_kernel<<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8q);
+        gauge8d_kernel<<<grid, 256, 0, c->stream>>>(c->d_coords, c->g, tmp, c->d_gauge8d);
         gauge_ff_kernel<<<grid, 256, 0, c->stream>>>(c->d_gauge64, c->d_gauge_ff, (long)n64 / 2);
-        c->kernel_launches += 7;
+        c->kernel_launches += 8;
         if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
             rc = fail(DL_ECUDA, "gauge reorder failed");
     }
@@ -1152,7 +1180,7 @@ static int solve_batch(dl_ctx *c, int n, int N, const SolveCfg &P, std::vector<O
     CK(cudaMemcpyAsync(c->r64, c->bh64, half * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     CK(cudaMemsetAsync(xe, 0, half * sizeof(double), c->stream));
     bool residual_current = false;  // c->r64 and x_o belong to the current x_e
-    const int prec = P.prec;
+    const int prec = inner_prec(c, P.prec, N);
     for (int cycle = 0; cycle < P.max_outer; ++cycle) {
         outer_count_kernel<<<1, 1, 0, c->stream>>>(c->d_outer, N, c->d_count);
         c->kernel_launches++;
@@ -1415,18 +1443,19 @@ extern "C" int dl_apply_hop_prec(dl_ctx *c, int precision, const void *in, void 
     const int Vh = (int)c->Vh;
     const size_t nc = half / 2;  // complex values per half field
     const int grid = (int)std::min<long>(((long)nc + 255) / 256, (long)c->num_sms * 8);
+    const int ip = inner_prec(c, precision, N);  // storage layout the solver's inner fields use at this width
     for (int j0 = 0; j0 < n_rhs; j0 += N) {
         const int n = std::min(N, n_rhs - j0);
         c->cur = c->stream;
         TRY(canon_to_eo(c, (const double *)in + j0 * field, c->b64, n, N, 0, 0, Vh));
-        CK(launch_cast(precision, c->b64, lo_ptr(c, 0), nc, 1, grid, c->stream));
-        CK(launch_cast(precision, c->b64 + half, lo_ptr(c, 1), nc, 1, grid, c->stream));
-        TRY(do_hop(c, precision, MODE_PLAIN, RED_NONE, lo_ptr(c, 2), lo_ptr(c, 1), nullptr, nullptr, nullptr, 0, N,
+        CK(launch_cast(ip, c->b64, lo_ptr(c, 0), nc, 1, grid, c->stream));
+        CK(launch_cast(ip, c->b64 + half, lo_ptr(c, 1), nc, 1, grid, c->stream));
+        TRY(do_hop(c, ip, MODE_PLAIN, RED_NONE, lo_ptr(c, 2), lo_ptr(c, 1), nullptr, nullptr, nullptr, 0, N,
                    1.0, 0, Vh, nullptr, nullptr));
-        TRY(do_hop(c, precision, MODE_PLAIN, RED_NONE, lo_ptr(c, 3), lo_ptr(c, 0), nullptr, nullptr, nullptr, 1, N,
+        TRY(do_hop(c, ip, MODE_PLAIN, RED_NONE, lo_ptr(c, 3), lo_ptr(c, 0), nullptr, nullptr, nullptr, 1, N,
                    1.0, 0, Vh, nullptr, nullptr));
-        CK(launch_cast(precision, c->x64, lo_ptr(c, 2), nc, 0, grid, c->stream));
-        CK(launch_cast(precision, c->x64 + half, lo_ptr(c, 3), nc, 0, grid, c->stream));
+        CK(launch_cast(ip, c->x64, lo_ptr(c, 2), nc, 0, grid, c->stream));
+        CK(launch_cast(ip, c->x64 + half, lo_ptr(c, 3), nc, 0, grid, c->stream));
         c->kernel_launches += 4;
         TRY(eo_to_canon(c, c->x64, (double *)out + j0 * field, n, N, 0, 0, Vh));
     }
@@ -2355,6 +2384,7 @@ extern "C" int dl_bench_hop(dl_ctx *c, int precision, int n_rhs, int fused, int 
     if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64 || reps < 1 || !ms || !bytes)
         return fail(DL_EINVAL, "bad arguments");
     const int N = pow2_at_least(n_rhs);
+    precision = inner_prec(c, precision, N);
     TRY(ensure_ws(c, N));
     TRY(ensure_partials(c, (size_t)2 * c->num_sms * 16 * N * 16));
     c->cur = c->stream;

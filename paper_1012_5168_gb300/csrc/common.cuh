@@ -276,6 +276,22 @@ template <> struct Real<double> { typedef double type; };
 template <> struct Real<float> { typedef float type; };
 template <> struct Real<bf16> { typedef float type; };
 
+// FP32 storage with the right-hand sides of a field interleaved in pairs: each
+// 16-byte group holds (re_r, re_r+1, im_r, im_r+1) for the two right-hand
+// sides r = 2k, 2k+1 of one field element (N even).  An element's address is
+// the one it has in the plain FP32 layout (re, im pairs of floats), so the
+// kernels' offsets do not change: only the order inside each group does.
+// Groups start on 16-byte boundaries (field bases are), so bit 3 of an
+// element's address tells which member of its pair it is.  One 16-byte load
+// gives the real parts of two right-hand sides as one FP32 pair and their
+// imaginary parts as another: the operands of the packed FP32 instructions.
+struct f32p {
+    float v;
+};
+template <> struct Real<f32p> { typedef float type; };
+template <typename S> struct IsPaired { static constexpr bool v = false; };
+template <> struct IsPaired<f32p> { static constexpr bool v = true; };
+
 template <typename S>
 __host__ __device__ constexpr int cbytes() { return 2 * (int)sizeof(S); }
 
@@ -361,6 +377,7 @@ template <> struct Conv<float> {
         w[0] = __float_as_uint(z.re); w[1] = __float_as_uint(z.im);
     }
 };
+template <> struct Conv<f32p> : Conv<float> {};  // unpaired data (links) in f32p-typed buffers
 template <> struct Conv<bf16> {
     static constexpr int W = 1;
     __device__ __forceinline__ static cx<float> get(const uint32_t *w) {
@@ -374,9 +391,47 @@ template <> struct Conv<bf16> {
     }
 };
 
+// Paired FP32 layout (f32p): R = 1 reads or writes its own member of a group
+// (two 4-byte accesses), even R whole groups (16-byte accesses; the first
+// right-hand side must be even).
+template <int R, bool NC>
+__device__ __forceinline__ void ld_paired(const float *p, cx<float> (&v)[R]) {
+    if constexpr (R == 1) {
+        const int m = (int)((reinterpret_cast<uintptr_t>(p) >> 3) & 1);
+        const float *g = p - 2 * m;
+        v[0] = NC ? mk(__ldg(g + m), __ldg(g + 2 + m)) : mk(g[m], g[2 + m]);
+    } else {
+        static_assert(R % 2 == 0, "paired layout: R = 1 or even");
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) {
+            const float4 q = NC ? __ldg(reinterpret_cast<const float4 *>(p) + k) : reinterpret_cast<const float4 *>(p)[k];
+            v[2 * k] = mk(q.x, q.z);
+            v[2 * k + 1] = mk(q.y, q.w);
+        }
+    }
+}
+template <int R>
+__device__ __forceinline__ void st_paired(float *p, const cx<float> (&v)[R]) {
+    if constexpr (R == 1) {
+        const int m = (int)((reinterpret_cast<uintptr_t>(p) >> 3) & 1);
+        float *g = p - 2 * m;
+        g[m] = v[0].re;
+        g[2 + m] = v[0].im;
+    } else {
+        static_assert(R % 2 == 0, "paired layout: R = 1 or even");
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k)
+            reinterpret_cast<float4 *>(p)[k] = make_float4(v[2 * k].re, v[2 * k + 1].re, v[2 * k].im, v[2 * k + 1].im);
+    }
+}
+
 // Load / store R consecutive complex values of storage type S.
 template <typename S, int R, bool NC>
 __device__ __forceinline__ void ld_pack(const S *p, cx<typename Real<S>::type> (&v)[R]) {
+    if constexpr (IsPaired<S>::v) {
+        ld_paired<R, NC>(reinterpret_cast<const float *>(p), v);
+        return;
+    }
     constexpr int NB = R * cbytes<S>();
     uint32_t w[NB / 4];
     RawLd<NB, NC>::ld(p, w);
@@ -385,6 +440,10 @@ __device__ __forceinline__ void ld_pack(const S *p, cx<typename Real<S>::type> (
 }
 template <typename S, int R>
 __device__ __forceinline__ void st_pack(S *p, const cx<typename Real<S>::type> (&v)[R]) {
+    if constexpr (IsPaired<S>::v) {
+        st_paired<R>(reinterpret_cast<float *>(p), v);
+        return;
+    }
     constexpr int NB = R * cbytes<S>();
     uint32_t w[NB / 4];
 #pragma unroll

@@ -145,6 +145,32 @@ __global__ void gauge8_kernel(const uint32_t *coords, Geom g, const double *cano
     }
 }
 
+// The paired-layout hop's links (kind 7): the site-major rows of gauge8_kernel
+// (U_mu(x) for d = 2 mu, U_mu(x - mu) for d = 2 mu + 1, time boundary factor
+// folded in) with every FP32 element stored as the quad (Re U, Re U, Im U, Im U),
+// so that each half is an FP32 pair operand for two right-hand sides at once.
+static __global__ void gauge8d_kernel(const uint32_t *coords, Geom g, const double *canon, float4 *out) {
+    const int total = 2 * g.Vh;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const Site st = decode(coords[idx], g);
+        for (int d = 0; d < 8; ++d) {
+            const int mu = d >> 1;
+            int src = st.i;
+            if (d & 1) {
+                src = st.i - g.stride[mu];
+                if (st.c[mu] == 0) src += g.L[mu] * g.stride[mu];
+            }
+            const double2 *u = (const double2 *)(canon + ((size_t)src * 4 + mu) * 18);
+            float4 *dst = out + ((size_t)idx * 8 + d) * 9;
+            const double sg = (mu == 3 && g.t_bc < 0 && st.c[3] == ((d & 1) ? 0 : g.L[3] - 1)) ? -1.0 : 1.0;
+            for (int k = 0; k < 9; ++k) {
+                const float re = (float)(sg * u[k].x), im = (float)(sg * u[k].y);
+                dst[k] = make_float4(re, re, im, im);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Philox4x64-10 (Salmon et al., SC'11) and complex Z2 sources
 // ---------------------------------------------------------------------------

@@ -62,6 +62,8 @@ struct HopArgs {
                             // (backward, already conjugated): the packed-arithmetic kernel's links
     const int *act;         // per right-hand side r: act[r * act_stride] != 0 if it takes part in this
     int act_stride;         // iteration; NULL: all do.  The direct kernels skip the others' loads and stores.
+    const float4 *gauge8d;  // [2][Vh][8][9] FP32 quads (Re U, Re U, Im U, Im U) of the site-major rows:
+                            // the paired-layout kernel's links
     const void *clovinv;    // clover: A^-1 of the output sites in the storage type ([2][Vh][2][6][6]
                             // complex), applied to D in before the epilogue; NULL: no clover term
 };

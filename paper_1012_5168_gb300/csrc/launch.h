@@ -19,7 +19,9 @@ namespace dl {
 
 // Storage precisions.  P_DFF is internal to the Wilson hop: FP64 storage
 // (float-float gathered field), float-float arithmetic (defect correction).
-enum { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_DFF = 3 };
+// P_F32P: FP32 storage in the paired layout (f32p, common.cuh), the inner
+// fields of FP32 solves of even width when the context uses it.
+enum { P_F64 = 0, P_F32 = 1, P_BF16 = 2, P_DFF = 3, P_F32P = 4 };
 
 struct Launch {
     int grid;
@@ -101,6 +103,7 @@ cudaError_t launch_ff_cast(const double *src, double *dst, size_t n_complex, int
 // 4 warp-staged bulk copies, one site per warp, N = 32 R only (the launcher sets
 // block, grid and shared memory; other widths return cudaErrorInvalidValue).
 cudaError_t launch_hop_f32(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
+cudaError_t launch_hop_f32p(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 cudaError_t launch_hop_bf16(int R, int mode, int red, int kind, const HopArgs &a, Launch &l);
 
 // TMA_STAGES stages of `sites` neighbour blocks [12][N], two link rows and two

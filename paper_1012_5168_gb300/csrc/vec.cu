@@ -10,6 +10,9 @@ namespace dl {
         else if (PREC == P_F32 && R == 1) { typedef float S; CALL(S, 1); } \
         else if (PREC == P_F32 && R == 2) { typedef float S; CALL(S, 2); } \
         else if (PREC == P_F32 && R == 4) { typedef float S; CALL(S, 4); } \
+        else if (PREC == P_F32P && R == 1) { typedef f32p S; CALL(S, 1); } \
+        else if (PREC == P_F32P && R == 2) { typedef f32p S; CALL(S, 2); } \
+        else if (PREC == P_F32P && R == 4) { typedef f32p S; CALL(S, 4); } \
         else if (PREC == P_BF16 && R == 1) { typedef bf16 S; CALL(S, 1); } \
         else if (PREC == P_BF16 && R == 2) { typedef bf16 S; CALL(S, 2); } \
         else if (PREC == P_BF16 && R == 4) { typedef bf16 S; CALL(S, 4); } \
@@ -92,6 +95,7 @@ cudaError_t launch_cg_p(const VecLaunch &v, const RhsState *st, const void *u, v
 cudaError_t launch_cast(int prec, double *f64, void *lo, size_t n_complex, int to_lo, int grid, cudaStream_t s) {
     const int block = 256;
     if (prec == P_F32) cast_kernel<float><<<grid, block, 0, s>>>(f64, (float *)lo, n_complex, to_lo);
+    else if (prec == P_F32P) cast_kernel<f32p><<<grid, block, 0, s>>>(f64, (f32p *)lo, n_complex, to_lo);
     else if (prec == P_BF16) cast_kernel<bf16><<<grid, block, 0, s>>>(f64, (bf16 *)lo, n_complex, to_lo);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -101,6 +105,7 @@ cudaError_t launch_fill(int prec, void *x, size_t n_complex, uint32_t seed, cuda
     const int grid = 1024, block = 256;
     if (prec == P_F64) fill_kernel<double><<<grid, block, 0, s>>>((double *)x, n_complex, seed);
     else if (prec == P_F32) fill_kernel<float><<<grid, block, 0, s>>>((float *)x, n_complex, seed);
+    else if (prec == P_F32P) fill_kernel<f32p><<<grid, block, 0, s>>>((f32p *)x, n_complex, seed);
     else if (prec == P_BF16) fill_kernel<bf16><<<grid, block, 0, s>>>((bf16 *)x, n_complex, seed);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();

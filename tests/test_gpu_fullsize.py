@@ -62,16 +62,19 @@ def full(lib):
 HOP_BOUND = {1: 1e-6, 2: 2e-2}
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_low_precision_hop_error_every_kernel(lib, prec):
-    """The inner solver's FP32 / BF16 hop, each kernel kind, against the FP64 oracle hop on every site."""
+@pytest.mark.parametrize("prec, pairs", [(1, "0"), (1, "1"), (2, "1")])
+def test_low_precision_hop_error_every_kernel(lib, prec, pairs, monkeypatch):
+    """The inner solver's FP32 / BF16 hop, each kernel kind, against the FP64 oracle hop on every site.
+    FP32 runs in both field layouts: plain (kinds 0-4, 6) and paired (kinds 0, 7, 8)."""
+    monkeypatch.setenv("DLOOPS_F32_PAIRS", pairs)
+    paired = prec == 1 and pairs == "1"
     dims = (6, 4, 4, 8)
     U = synthetic.gauge_field(dims, eps=0.45, seed=41)
     c = lib.Context(dims)
     c.load_gauge(U)
     psi = synthetic.random_spinor(dims, seed=42, n=7)
     ref = wilson.hop(U, psi, -1.0)
-    for kind in (0, 1, 2, 3):
+    for kind in ((0, 7, 8) if paired else (0, 1, 2, 3)):
         R, B, k, _ = c.tune_hop(prec, 8, force_pf=kind)
         assert k == kind
         got = c.apply_hop(to_gpu(psi), precision=prec).cpu().numpy()
@@ -81,7 +84,7 @@ def test_low_precision_hop_error_every_kernel(lib, prec):
     exact = c.apply_hop(to_gpu(psi)).cpu().numpy()  # the FP64 hop of the same context
     assert hop_error(exact, ref) < 1e-14
     # the warp-staged kernels serve widths 32 and 64 only; kind 5 (tensor cores) BF16 only
-    for kind in ((4, 5) if prec == 2 else (4,)):
+    for kind in ((7, 8, 9) if paired else ((4, 5) if prec == 2 else (4, 6))):
         for n in (32, 64):
             wide = synthetic.random_spinor(dims, seed=43, n=n)
             ref_w = wilson.hop(U, wide, -1.0)
@@ -94,11 +97,18 @@ def test_low_precision_hop_error_every_kernel(lib, prec):
     c.close()
 
 
+@pytest.mark.parametrize("kind", [6, 7, 8, 9])
 @pytest.mark.parametrize("n", [7, 32])
-def test_packed_fp32_hop_is_bitwise_the_scalar_hop(lib, n):
-    """Kind 6 (packed FP32 pairs, FFMA2) performs the scalar kernel's FMAs in the same order, so its
-    hop equals the scalar direct kernel's (one right-hand side per thread) bit for bit, and both sit
-    within the FP32 bound of the FP64 oracle hop."""
+def test_packed_fp32_hop_is_bitwise_the_scalar_hop(lib, n, kind, monkeypatch):
+    """The packed FP32 kernels perform the scalar kernel's operations in the same order: kind 6 (one
+    right-hand side per thread, (re, im) pairs, plain layout) and kinds 7, 8 (two right-hand sides per
+    thread in the paired layout, their real parts one pair and their imaginary parts another; kind 9
+    the same arithmetic on operands staged in shared memory).  So the
+    hop equals the scalar direct kernel's (one right-hand side per thread, same layout) bit for bit, and
+    both sit within the FP32 bound of the FP64 oracle hop."""
+    if kind == 9 and n == 7:
+        pytest.skip("the warp-staged paired hop serves widths 32 and 64")
+    monkeypatch.setenv("DLOOPS_F32_PAIRS", "0" if kind == 6 else "1")
     dims = (6, 4, 4, 8)
     U = synthetic.gauge_field(dims, eps=0.45, seed=44)
     c = lib.Context(dims, t_bc=-1)
@@ -107,27 +117,36 @@ def test_packed_fp32_hop_is_bitwise_the_scalar_hop(lib, n):
     width = 8 if n == 7 else 32
     c.tune_hop(1, width, force_R=1, force_pf=0)
     scalar = c.apply_hop(psi, precision=1).cpu().numpy()
-    R, B, k, _ = c.tune_hop(1, width, force_pf=6)
-    assert k == 6 and R == 1
+    R, B, k, _ = c.tune_hop(1, width, force_pf=kind)
+    assert k == kind and R == (1 if kind == 6 else 2)
     packed = c.apply_hop(psi, precision=1).cpu().numpy()
     assert np.array_equal(packed, scalar)
     assert hop_error(packed, wilson.hop(U, psi.cpu().numpy(), -1.0)) < HOP_BOUND[1]
     c.close()
 
 
-@pytest.mark.parametrize("prec, kind", [(1, -1), (1, 6), (2, -1), (2, 5)])
-def test_low_precision_hop_error_full_size(lib, full, prec, kind):
-    """16^3 x 32 at the bench width of 32 right-hand sides, in the tuned launch shape (kind -1) or on
-    the tensor cores (kind 5, BF16); fields 0 and 31 against the FP64 oracle hop on every site."""
+@pytest.mark.parametrize("prec, kind", [(1, -1), (1, 7), (1, 8), (1, 9), (2, -1), (2, 5)])
+def test_low_precision_hop_error_full_size(lib, full, prec, kind, monkeypatch):
+    """16^3 x 32 at the bench width of 32 right-hand sides, in the tuned launch shape (kind -1), on
+    the tensor cores (kind 5, BF16) or in the paired FP32 layout (kinds 7-9, a context of its own);
+    fields 0 and 31 against the FP64 oracle hop on every site."""
     c, U = full
+    own = None
+    if kind >= 7:
+        monkeypatch.setenv("DLOOPS_F32_PAIRS", "1")
+        c = own = lib.Context(W["dims"])
+        c.load_gauge(U)
+        c.set_kappa(W["kappa"])
     c.tune_hop(prec, 32, force_pf=kind)
     eta = c.make_sources(seed=11, noise_first=0, n_noise=32, dilution=0)
     got = c.apply_hop(eta, precision=prec)
     for j in (0, 31):
         ref = wilson.hop(U, eta[j:j + 1].cpu().numpy(), -1.0)
         err = hop_error(got[j:j + 1].cpu().numpy(), ref)
-        print(f"full-size hop prec {prec} field {j}: max error {err:.3e} of max|D eta|")
+        print(f"full-size hop prec {prec} kind {kind} field {j}: max error {err:.3e} of max|D eta|")
         assert err < HOP_BOUND[prec]
+    if own is not None:
+        own.close()
 
 
 def test_loops_local_and_smeared_full_size(lib, full):

@@ -168,11 +168,22 @@ def test_solve_full_size(lib, prec):
     c.close()
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def plain_f32_layout(monkeypatch, prec, kind):
+    """FP32 fields of the contexts made now: paired for kinds 7-9, which read that layout only."""
+    if prec == 1 and kind >= 7:
+        monkeypatch.setenv("DLOOPS_F32_PAIRS", "1")
+
+
+@pytest.mark.parametrize("prec, kind", [(p, k) for p in (1, 2) for k in (0, 1, 2, 3)] + [(1, 7), (1, 8), (1, 9)])
 @pytest.mark.parametrize("batch", [1, 4, 16, 64])
-def test_hop_kernel_kinds(lib, prec, kind, batch):
-    """Direct, cp.async-prefetching, bulk-copy-staged and blocked-mapping hops all solve to tolerance."""
+def test_hop_kernel_kinds(lib, prec, kind, batch, monkeypatch):
+    """Direct, cp.async-prefetching, bulk-copy-staged and blocked-mapping hops, and the paired-layout
+    packed-FP32 hops (kinds 7, 8: FP32 of even width), all solve to tolerance."""
+    if kind >= 7 and batch == 1:
+        pytest.skip("the paired layout holds two right-hand sides per group: even widths only")
+    if kind == 9 and batch != 64:
+        pytest.skip("the warp-staged paired hop serves widths 32 and 64")
+    plain_f32_layout(monkeypatch, prec, kind)
     dims, kappa = (4, 4, 4, 8), 0.12
     U = synthetic.gauge_field(dims, eps=0.45, seed=8)
     c = lib.Context(dims)
@@ -190,13 +201,16 @@ def test_hop_kernel_kinds(lib, prec, kind, batch):
     c.close()
 
 
-@pytest.mark.parametrize("prec, kind", [(1, 4), (2, 4), (2, 5), (1, 6)])
+@pytest.mark.parametrize("prec, kind", [(1, 4), (2, 4), (2, 5), (1, 6), (1, 7), (1, 8), (1, 9)])
 @pytest.mark.parametrize("batch", [32, 64])
-def test_warp_staged_hop_solves(lib, prec, kind, batch):
+def test_warp_staged_hop_solves(lib, prec, kind, batch, monkeypatch):
     """The warp-staged hops (one site per warp, N = 32 R: kind 4 on the CUDA cores, kind 5 on the
     tensor cores for BF16) and the packed-FP32 direct hop (kind 6) at widths 32 and 64, with a ragged
     last batch, solve to tolerance.  8^3 x 24 has more even sites (6144) than a 152-SM GPU runs warps of
-    this kernel (at most 2432), so every warp walks several sites and reuses its stages and link rows."""
+    this kernel (at most 2432), so every warp walks several sites and reuses its stages and link rows.
+    Kinds 7 and 8 (paired layout, two right-hand sides per thread) and kind 9 (paired and
+    warp-staged, 64 / N sites per warp) run at the same widths."""
+    plain_f32_layout(monkeypatch, prec, kind)
     dims, kappa = (8, 8, 8, 24), 0.12
     U = synthetic.gauge_field(dims, eps=0.45, seed=9)
     c = lib.Context(dims)
@@ -205,7 +219,7 @@ def test_warp_staged_hop_solves(lib, prec, kind, batch):
     b = synthetic.random_spinor(dims, seed=22, n=batch + 3)
     k = [0, batch - 1, batch, batch + 2]  # fields checked with the oracle's M
     R, B, got_kind, _ = c.tune_hop(prec, batch, force_pf=kind)
-    assert got_kind == kind and R == (1 if kind == 6 else batch // 32)
+    assert got_kind == kind and R == {6: 1, 7: 2, 8: 2, 9: 2}.get(kind, batch // 32)
     x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=prec, batch=batch))
     assert all(s["status"] == 0 and s["true_residual"] <= 1e-11 for s in st), st
     res = residual(U, x.cpu().numpy()[k], b[k], kappa)
@@ -213,23 +227,26 @@ def test_warp_staged_hop_solves(lib, prec, kind, batch):
     c.close()
 
 
-def test_hop_kernel_kinds_full_size(lib):
-    """The five hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides)."""
+def test_hop_kernel_kinds_full_size(lib, monkeypatch):
+    """The FP32 hop kernels give the same Schur solve on the 16^3 x 32 lattice (32 right-hand sides):
+    kinds 0-4 on the plain layout, kinds 0, 7, 8, 9 on the paired one."""
     w = synthetic.WORKLOADS["wilson_16x16x16x32"]
     U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
-    c = lib.Context(w["dims"])
-    c.load_gauge(U)
-    c.set_kappa(w["kappa"])
-    eta = c.make_sources(seed=4, noise_first=0, n_noise=32, dilution=0)
     sols = []
-    for kind in (0, 1, 2, 3, 4):
-        c.tune_hop(1, 32, force_pf=kind)
-        x, st = c.solve(eta, lib.Params(tol=1e-10, precision=1, batch=32))
-        assert all(s["status"] == 0 and s["true_residual"] <= 1e-10 for s in st)
-        sols.append(x)
+    for pairs, kinds in (("0", (0, 1, 2, 3, 4)), ("1", (0, 7, 8, 9))):
+        monkeypatch.setenv("DLOOPS_F32_PAIRS", pairs)
+        c = lib.Context(w["dims"])
+        c.load_gauge(U)
+        c.set_kappa(w["kappa"])
+        eta = c.make_sources(seed=4, noise_first=0, n_noise=32, dilution=0)
+        for kind in kinds:
+            c.tune_hop(1, 32, force_pf=kind)
+            x, st = c.solve(eta, lib.Params(tol=1e-10, precision=1, batch=32))
+            assert all(s["status"] == 0 and s["true_residual"] <= 1e-10 for s in st)
+            sols.append(x)
+        c.close()
     for x in sols[1:]:
         assert (torch.linalg.vector_norm(x - sols[0]) / torch.linalg.vector_norm(sols[0])).item() < 1e-9
-    c.close()
 
 
 @pytest.mark.parametrize("method", [0, 1])
@@ -387,8 +404,8 @@ def test_nan_gauge_link(lib):
     c.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
-def test_skipping_stopped_rhs_changes_nothing(lib, prec, monkeypatch):
+@pytest.mark.parametrize("prec, kind", [(0, 0), (1, 0), (1, 7)])
+def test_skipping_stopped_rhs_changes_nothing(lib, prec, kind, monkeypatch):
     """The direct hops skip the loads and stores of right-hand sides that have stopped; the
     others' arithmetic is untouched and a stopped one's vectors stay frozen either way, so the
     solutions are bitwise the same with the skip switched off (DLOOPS_HOP_SKIP=0).  Point sources
@@ -396,12 +413,13 @@ def test_skipping_stopped_rhs_changes_nothing(lib, prec, monkeypatch):
     dims, kappa = (4, 4, 4, 8), 0.12
     U = synthetic.gauge_field(dims, eps=0.45, seed=12)
     sols = {}
+    plain_f32_layout(monkeypatch, prec, kind)
     for flag in ("1", "0"):
         monkeypatch.setenv("DLOOPS_HOP_SKIP", flag)
         c = lib.Context(dims)
         c.load_gauge(U)
         c.set_kappa(kappa)
-        c.tune_hop(prec, 16, force_pf=0)
+        c.tune_hop(prec, 16, force_pf=kind)
         b = torch.cat([c.make_point_sources(12 * 37, 8), c.make_sources(seed=6, noise_first=0, n_noise=8,
                                                                           dilution=0)]).contiguous()
         x, st = c.solve(b, lib.Params(tol=1e-11, precision=prec, batch=16))
