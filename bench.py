@@ -39,6 +39,12 @@ WORKLOAD = dict(name="stochastic_loops_16x16x16x32", dims=(16, 16, 16, 32), kapp
 # The paper's kappa = 0.157 on links rough enough to keep M subcritical (eps 0.60, plaquette ~0.37)
 WORKLOAD_K157 = dict(WORKLOAD, name="stochastic_loops_16x16x16x32_k157", kappa=0.157, eps=0.60)
 CHUNK_NOISE = 4  # noise vectors per solve call (96 right-hand sides)
+# the Wilson-hop kernel kinds of the autotuner (dl_tune_hop)
+HOP_KIND_NAMES = {0: "hop_kernel_cap (direct)", 1: "hop_kernel_pf (cp.async prefetch)",
+                  2: "hop_kernel_tma (block-staged)", 3: "hop_kernel (blocked order)",
+                  4: "hop_kernel_ws (warp-staged)", 5: "hop_kernel_mma (tensor cores)",
+                  6: "hop_kernel_x2 (packed FP32)", 7: "hop_kernel_pair (paired layout)",
+                  8: "hop_kernel_pair_cap (paired layout)", 9: "hop_kernel_ws_pair (paired, warp-staged)"}
 
 
 def parse():
@@ -50,6 +56,9 @@ def parse():
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hop-kind", type=int, default=-1,
+                    help="Wilson-hop kernel kind for the benchmark line (default -1: the autotuner's choice); "
+                         "lets a profiler run use the kernel the timed run chose, whose kind the line records")
     ap.add_argument("--kappa-literal", action="store_true",
                     help="the benchmark workload at kappa 0.157 on eps 0.60 links instead of kappa 0.140 on eps 0.45")
     ap.add_argument("--workload", default="stochastic",
@@ -795,8 +804,9 @@ def main():
         tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
         return float(t.item())
 
-    # ---- warm-up (autotunes the hop, captures the CUDA graphs with their
-    # timing events, fills caches)
+    # ---- the hop's launch shape for this width (the tuner the solver would run), then warm-up
+    # (captures the CUDA graphs with their timing events, fills caches)
+    hop_R, hop_block, hop_kind, _ = ctx.tune_hop(prec, args.batch, force_pf=args.hop_kind)
     ctx.set_timing(True)
     for s in range(args.warmup):
         run_step(ctx, dl, 1000 + s, noise0, params, store)
@@ -869,10 +879,12 @@ def main():
     per_launch_ms = tim["hop_ms"][dom] / max(tim["hop_launches"][dom], 1)
     per_launch_bytes = tim["hop_bytes"][dom] / max(tim["hop_launches"][dom], 1)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = read_traffic(kinds[dom])
+    traffic = read_traffic(kinds[dom]) if hop_kind == 0 and args.batch == 32 and args.precision == "f32" else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": f"hop_kernel {kinds[dom]} ({args.precision} storage, batch {args.batch})",
+                "kernel": f"{HOP_KIND_NAMES.get(hop_kind, hop_kind)} {kinds[dom]} ({args.precision} storage, "
+                          f"batch {args.batch}, {hop_R} right-hand side(s) per thread, block {hop_block})",
+                "hop_kind": hop_kind,
                 "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": per_launch_bytes,
                 "launches": tim["hop_launches"][dom], "ms_per_launch": round(per_launch_ms, 5),
                 "hop_share_of_step": round(sum(tim["hop_ms"]) / ms, 3) if ms > 0 else None}
