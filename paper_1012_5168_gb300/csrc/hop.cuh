@@ -308,15 +308,19 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
         idx_end = min(total, (int)(blockIdx.x + 1) * per);
         stride = blockDim.x;
     }
+    // A thread keeps its right-hand sides for the whole launch (the stride is a
+    // multiple of G), so those that have converged (or stopped) are read once:
+    // such a thread loads and stores nothing.
+    if (A.act && idx < idx_end) {
+        const int r0 = (idx & (G - 1)) * R;
+        bool any = false;
+#pragma unroll
+        for (int r = 0; r < R; ++r) any |= __ldg(A.act + (size_t)(r0 + r) * A.act_stride) != 0;
+        if (!any) idx = idx_end;
+    }
     for (; idx < idx_end; idx += stride) {
         const int cb = A.cb_begin + (idx >> lgG);
         const int r0 = (idx & (G - 1)) * R;
-        if (A.act) {  // right-hand sides that have converged (or stopped) need no hop
-            bool any = false;
-#pragma unroll
-            for (int r = 0; r < R; ++r) any |= __ldg(A.act + (size_t)(r0 + r) * A.act_stride) != 0;
-            if (!any) continue;
-        }
         const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
         cx<T> acc[R][12];
         if constexpr (X2 != 0 && sizeof(S) == 4 && R == 1) {

@@ -210,11 +210,15 @@ __device__ __forceinline__ void hop_body_pair(const HopArgs &A) {
     float2 dr[NV], di[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) dr[k] = di[k] = make_float2(0.f, 0.f);
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (A.act && idx < total) {  // the thread's two right-hand sides are the same at every site
+        const int r0 = (idx & (G - 1)) * 2;
+        if (__ldg(A.act + (size_t)r0 * A.act_stride) == 0 && __ldg(A.act + (size_t)(r0 + 1) * A.act_stride) == 0)
+            idx = total;  // both have stopped
+    }
+    for (; idx < total; idx += gridDim.x * blockDim.x) {
         const int cb = A.cb_begin + (idx >> lgG);
         const int r0 = (idx & (G - 1)) * 2;
-        if (A.act && __ldg(A.act + (size_t)r0 * A.act_stride) == 0 && __ldg(A.act + (size_t)(r0 + 1) * A.act_stride) == 0)
-            continue;  // both right-hand sides have stopped
         const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
         P2 acc[12];
 #pragma unroll
