@@ -448,8 +448,9 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     c->cur = c->stream;
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
-    float best = 1e30f;
+    float best = 1e30f, best0 = 1e30f;  // all kinds; the direct kernel (kind 0)
     int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_kind[prec][l];
+    int b0R = bR, b0B = bB;
     const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
     // Two sweeps over the shapes, keeping each shape's faster time, so that a
     // shape timed while the GPU was still ramping its clocks or finishing other
@@ -484,8 +485,21 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                     bB = B;
                     bP = pf;
                 }
+                if (pf == 0 && ms > 0.f && ms < best0) {
+                    best0 = ms;
+                    b0R = R;
+                    b0B = B;
+                }
             }
         }
+    }
+    // Another kind replaces the direct kernel only when it is faster by more than
+    // 2%: closer than that, which one wins is timing noise (on GB300 the
+    // warp-staged kernel and the direct one are within 1% at some widths).
+    if (bP != 0 && best0 < 1e30f && best > 0.98f * best0) {
+        bR = b0R;
+        bB = b0B;
+        bP = 0;
     }
     c->hop_R[prec][l] = bR;
     c->hop_block[prec][l] = bB;

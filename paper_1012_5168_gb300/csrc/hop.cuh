@@ -431,6 +431,12 @@ template <typename S, int MODE, int RED>
 __global__ void __launch_bounds__(256) hop_kernel_clov(HopArgs A) {
     hop_body<S, 1, MODE, RED, 0, 0, 1>(A);
 }
+// The same under the direct FP32 kernels' register caps, with the width a
+// compile-time constant.
+template <typename S, int MODE, int RED, int CAP, int NC>
+__global__ void __maxnreg__(CAP) hop_kernel_clov_cap(HopArgs A) {
+    hop_body<S, 1, MODE, RED, NC, 0, 1>(A);
+}
 
 // Packed-arithmetic direct kernel (FP32 storage, one right-hand side per thread).
 template <int MODE, int RED, int CAP, int NC = 0>

@@ -32,6 +32,14 @@ template <typename S, int R, int MODE, int RED>
 cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
     if (a.clovinv) {  // clover: the direct kernel with A^-1 in the epilogue, one right-hand side per thread
         if constexpr (R == 1) {
+            constexpr int ccap = HopRegCap<S, 1, MODE, RED>::n;
+            if constexpr (ccap > 0) {
+                if (a.N == 32) {
+                    clamp_grid(l, resident_blocks(hop_kernel_clov_cap<S, MODE, RED, ccap, 32>, l.block, l.smem));
+                    hop_kernel_clov_cap<S, MODE, RED, ccap, 32><<<l.grid, l.block, l.smem, l.stream>>>(a);
+                    return cudaGetLastError();
+                }
+            }
             clamp_grid(l, resident_blocks(hop_kernel_clov<S, MODE, RED>, l.block, l.smem));
             hop_kernel_clov<S, MODE, RED><<<l.grid, l.block, l.smem, l.stream>>>(a);
             return cudaGetLastError();
