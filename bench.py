@@ -98,22 +98,33 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-def read_traffic(kind: str):
-    """Per-launch DRAM bytes of the hop kernel from the committed ncu summary, if current."""
+# The ncu summary of the FP32 hop at the bench width, and the source files each
+# kernel kind it covers is built from: its figures count only while those are unchanged.
+TRAFFIC_PROFILE = os.path.join("profiles", "hop_f32_fused_n32_16x16x16x32.md")
+TRAFFIC_SOURCES = {0: ["hop.cuh"], 4: ["hop.cuh", "hop_tma.cuh", "hop_ws.cuh"]}
+
+
+def sources_sha(hop_kind: int):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "hop_f32_fused_n32_16x16x16x32.md")
-    src = os.path.join(ROOT, "paper_1012_5168_gb300", "csrc", "hop.cuh")
-    if not os.path.exists(path):
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES[hop_kind]:
+        h.update(open(os.path.join(ROOT, "paper_1012_5168_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kind: str, hop_kind: int):
+    """Per-launch DRAM bytes of the hop kernel kind from the committed ncu summary, if current."""
+    path = os.path.join(ROOT, TRAFFIC_PROFILE)
+    if hop_kind not in TRAFFIC_SOURCES or not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         if ":" in line and line.startswith("- "):
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("hop.cuh sha256") != sha:
+    if vals.get(f"kind {hop_kind} sources sha256") != sources_sha(hop_kind):
         return None
-    key = f"{kind} dram bytes per launch"
+    key = f"kind {hop_kind} {kind} dram bytes per launch"
     return float(vals[key]) if key in vals else None
 
 
@@ -249,7 +260,9 @@ def hop_profile(spec: str):
     ctx.load_gauge(synthetic.gauge_field(w["dims"], w["eps"], w["seed"]))
     ctx.set_kappa(w["kappa"])
     shape = ctx.tune_hop(prec, n, force_R=force_r, force_block=force_b, force_pf=kind)
-    out = {"precision": parts[0], "n_rhs": n, "R": shape[0], "block": shape[1], "kind": shape[2]}
+    plain = ctx.hop_shape(prec, n, False)
+    out = {"precision": parts[0], "n_rhs": n, "R": shape[0], "block": shape[1], "kind": shape[2],
+           "plain_shape": {"R": plain[0], "block": plain[1], "kind": plain[2]}}
     for fused, name in ((0, "plain"), (1, "fused"), (2, "fused_bicg")):
         ms, by = ctx.bench_hop(prec, n, fused, reps=5)
         out[name] = {"ms": round(ms, 5), "GB/s": round(by / ms / 1e6, 1)}
@@ -806,7 +819,8 @@ def main():
 
     # ---- the hop's launch shape for this width (the tuner the solver would run), then warm-up
     # (captures the CUDA graphs with their timing events, fills caches)
-    hop_R, hop_block, hop_kind, _ = ctx.tune_hop(prec, args.batch, force_pf=args.hop_kind)
+    ctx.tune_hop(prec, args.batch, force_pf=args.hop_kind)
+    hop_shape = [ctx.hop_shape(prec, args.batch, fused) for fused in (False, True)]  # (R, block, kind)
     ctx.set_timing(True)
     for s in range(args.warmup):
         run_step(ctx, dl, 1000 + s, noise0, params, store)
@@ -879,15 +893,29 @@ def main():
     per_launch_ms = tim["hop_ms"][dom] / max(tim["hop_launches"][dom], 1)
     per_launch_bytes = tim["hop_bytes"][dom] / max(tim["hop_launches"][dom], 1)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = read_traffic(kinds[dom]) if hop_kind == 0 and args.batch == 32 and args.precision == "f32" else None
+    dR, dB, dk = hop_shape[dom % 2]  # the launch shape of the dominant class (plain 0, fused 1)
+    traffic = read_traffic(kinds[dom], dk) if args.batch == 32 and args.precision == "f32" else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": f"{HOP_KIND_NAMES.get(hop_kind, hop_kind)} {kinds[dom]} ({args.precision} storage, "
-                          f"batch {args.batch}, {hop_R} right-hand side(s) per thread, block {hop_block})",
-                "hop_kind": hop_kind,
+                "kernel": f"{HOP_KIND_NAMES.get(dk, dk)} {kinds[dom]} ({args.precision} storage, "
+                          f"batch {args.batch}, {dR} right-hand side(s) per thread, block {dB})",
+                "hop_kind": dk,
                 "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": per_launch_bytes,
                 "launches": tim["hop_launches"][dom], "ms_per_launch": round(per_launch_ms, 5),
                 "hop_share_of_step": round(sum(tim["hop_ms"]) / ms, 3) if ms > 0 else None}
+    # the other low-precision hop class of the same steps (plain D_oe p and D_oe s, or the fused ones)
+    other = 1 - dom if dom < 2 else None
+    if other is not None and tim["hop_launches"][other] > 0:
+        o_ms = tim["hop_ms"][other] / tim["hop_launches"][other]
+        o_bytes = tim["hop_bytes"][other] / tim["hop_launches"][other]
+        oR, oB, ok = hop_shape[other]
+        roofline["other_hop"] = {"class": kinds[other], "kernel": HOP_KIND_NAMES.get(ok, ok), "hop_kind": ok,
+                                 "R": oR, "block": oB, "ms_per_launch": round(o_ms, 5),
+                                 "achieved": round(o_bytes / (o_ms / 1e3) / 1e9, 1),
+                                 "frac": round(o_bytes / (o_ms / 1e3) / 1e9 / peak, 4),
+                                 "algorithmic_bytes_per_launch": o_bytes,
+                                 "traffic": read_traffic(kinds[other], ok)
+                                 if args.batch == 32 and args.precision == "f32" else None}
 
     # defect-correction hops (b_hat, reconstruction, residual) of the timed steps
     n_oh = tim["hop_launches"][2] + tim["hop_launches"][3]

@@ -429,16 +429,28 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
  * kernel kind: 0 direct, 1 cp.async-prefetching, 2 bulk-copy staged, 3 direct
  * with one contiguous range of sites per (widest resident) block, 4 warp-staged
  * (one site per warp with its own ring of bulk copies; only where
- * n_rhs = 32 R, i.e. widths 32 and 64).  Each
- * candidate runs one plain and one fused hop on random fields, in two sweeps
- * over all candidates; the fastest is kept for this context.
- * force_R / force_block > 0 and force_pf >= 0 restrict the candidates.  Solves
- * tune their (precision, batch) on first use.  *R_out, *block_out, *pf_out and
- * *ms_out (may be NULL) receive the choice and its time for one plain plus one
- * fused hop.  The call overwrites the context's inner workspace, so make it
- * between solves. */
+ * n_rhs = 32 R, i.e. widths 32 and 64), 5 BF16 on the tensor cores (n_rhs =
+ * 32 R), 6 packed FP32 arithmetic; on the paired FP32 layout
+ * (DLOOPS_F32_PAIRS=1, even widths) 0, 7 and 8 (packed, uncapped and capped)
+ * and 9 (packed, warp-staged; widths 32 and 64).  Each candidate times the
+ * plain hop and the fused hop with the five BiCGStab reductions on random
+ * fields, in two sweeps over all candidates, and the fastest is kept for each
+ * of the two separately (so the plain and the fused hops may use different
+ * kernels); another kind replaces the direct kernel only when it is more than
+ * 2% faster.  force_R / force_block > 0 and force_pf >= 0 restrict the
+ * candidates (for both).  Solves tune their (precision, batch) on first use.
+ * *R_out, *block_out, *pf_out receive the fused hop's choice and *ms_out the
+ * time of one plain plus one fused hop (each may be NULL).  The call
+ * overwrites the context's inner workspace, so make it between solves.
+ * Errors: DL_EINVAL (arguments, or a kind the storage layout lacks),
+ * DL_ESTATE (no gauge field), DL_ECUDA. */
 int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_block, int force_pf,
                 int *R_out, int *block_out, int *pf_out, double *ms_out);
+/* The launch shape the context currently uses for the plain (fused = 0) or the
+ * fused (fused != 0) Wilson hops of width n_rhs in the inner storage for
+ * `precision`: right-hand sides per thread, threads per block and kernel kind
+ * (outputs may be NULL).  No tuning, no GPU work.  Errors: DL_EINVAL. */
+int dl_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int fused, int *R_out, int *block_out, int *kind_out);
 
 /* Fused-multiply-add rate of the current device at `precision` (DL_PREC_F64 or
  * DL_PREC_F32), in TFLOP/s (2 flops per FMA), from one launch of independent

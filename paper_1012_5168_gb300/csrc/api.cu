@@ -136,9 +136,12 @@ struct dl_ctx {
     std::vector<cudaEvent_t> event_pool;
     dl_timing tim;
     int64_t kernel_launches = 0;
-    int hop_R[5][8];      // right-hand sides per thread, [prec][log2 N]
-    int hop_block[5][8];  // threads per block
-    int hop_kind[5][8];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
+    // Launch shape of the Wilson hop per [prec][log2 N][m], m = 0 for the plain hop
+    // (D_oe p, D_oe s) and 1 for the fused ones (XPAY with reductions): each is
+    // tuned on its own, so the two may use different kernels.
+    int hop_R[5][8][2];      // right-hand sides per thread
+    int hop_block[5][8][2];  // threads per block
+    int hop_kind[5][8][2];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
                           // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic, 7 paired layout with
                           // packed FP32 arithmetic, 8 the same under a 128-register cap, 9 paired and
                           // warp-staged
@@ -266,14 +269,15 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
                 : prec == P_F64 ? (const void *)c->d_clovinv64
                 : f32           ? (const void *)c->d_clovinv32
                                 : (const void *)c->d_clovinv16;
-    int R = (wide || clov) ? 1 : c->hop_R[prec][ilog2(N)];
+    const int m = (mode == MODE_PLAIN && red == RED_NONE) ? 0 : 1;  // the shape tables' plain / fused entry
+    int R = (wide || clov) ? 1 : c->hop_R[prec][ilog2(N)][m];
     if (R > N) R = N;
     const int G = N / R;
-    int block = prec == P_DFF ? 192 : c->hop_block[prec][ilog2(N)];  // P_DFF: a multiple of 3 N
+    int block = prec == P_DFF ? 192 : c->hop_block[prec][ilog2(N)][m];  // P_DFF: a multiple of 3 N
     if (block % G) block = 128;  // a multiple of G (N <= 64)
     const long total = (long)(cb1 - cb0) * G * (prec == P_DFF ? 3 : 1);
     const int NV = red == RED_BICG ? 5 : (red == RED_NONE ? 0 : 1);
-    const int kind = (wide || clov) ? 0 : c->hop_kind[prec][ilog2(N)];
+    const int kind = (wide || clov) ? 0 : c->hop_kind[prec][ilog2(N)][m];
     size_t smem = NV ? (size_t)(block / 32) * std::min(G, 32) * R * NV * (wide ? 16 : 8) : 0;
     int per_sm = wide ? 4 : 8;
     long items = total;
@@ -414,10 +418,12 @@ static int ensure_partials(dl_ctx *c, size_t elems) {
 // ---------------------------------------------------------------------------
 // autotuner: right-hand sides per thread and block size of the Wilson hop
 // ---------------------------------------------------------------------------
-// Times one inner-iteration's worth of hops (two plain, two fused) for each
-// candidate launch shape on random fields of width N and keeps the fastest.
-// Uses the inner workspace, so it runs before a solve fills it.
-static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out) {
+// Times, for each candidate launch shape on random fields of width N, the plain
+// hop and the fused hop with the five BiCGStab reductions (one of each per
+// inner half-iteration), and keeps the fastest shape for each.  Uses the inner
+// workspace, so it runs before a solve fills it.
+// which: bit 0 the plain hop, bit 1 the fused one.
+static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int which = 3) {
     const int Vh = (int)c->Vh;
     cudaEvent_t e0 = get_event(c), e1 = get_event(c);
     const bool was = c->timing;
@@ -425,9 +431,10 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out) {
     int rc = DL_OK;
     for (int it = -1; it < reps && rc == DL_OK; ++it) {
         if (it == 0) cudaEventRecord(e0, c->cur);
-        rc = do_hop(c, prec, MODE_PLAIN, RED_NONE, c->lo[7], c->lo[3], nullptr, nullptr, nullptr, 1, N, 1.0, 0, Vh,
-                    nullptr, nullptr);
-        if (rc == DL_OK)
+        if (which & 1)
+            rc = do_hop(c, prec, MODE_PLAIN, RED_NONE, c->lo[7], c->lo[3], nullptr, nullptr, nullptr, 1, N, 1.0, 0,
+                        Vh, nullptr, nullptr);
+        if (rc == DL_OK && (which & 2))
             rc = do_hop(c, prec, MODE_XPAY, RED_BICG, c->lo[6], c->lo[7], c->lo[5], nullptr, c->lo[2], 0, N, -0.02, 0,
                         Vh, c->d_partials, nullptr);
     }
@@ -448,9 +455,13 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     c->cur = c->stream;
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
-    float best = 1e30f, best0 = 1e30f;  // all kinds; the direct kernel (kind 0)
-    int bR = c->hop_R[prec][l], bB = c->hop_block[prec][l], bP = c->hop_kind[prec][l];
-    int b0R = bR, b0B = bB;
+    float best[2] = {1e30f, 1e30f}, best0[2] = {1e30f, 1e30f};  // [plain, fused]: all kinds; kind 0
+    int bR[2], bB[2], bP[2], b0R[2], b0B[2];
+    for (int m = 0; m < 2; ++m) {
+        bR[m] = b0R[m] = c->hop_R[prec][l][m];
+        bB[m] = b0B[m] = c->hop_block[prec][l][m];
+        bP[m] = c->hop_kind[prec][l][m];
+    }
     const int Rs[3] = {1, 2, 4}, Bs[3] = {64, 128, 256};
     // Two sweeps over the shapes, keeping each shape's faster time, so that a
     // shape timed while the GPU was still ramping its clocks or finishing other
@@ -474,21 +485,25 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                 if (pf >= 7 && R != 2) continue;                            // paired layout: two per thread
                 if (pf == 9 && (bi > 0 || (N != 32 && N != 64))) continue;  // warp-staged pairs: N = 32, 64
                 if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
-                c->hop_R[prec][l] = R;
-                c->hop_block[prec][l] = B;
-                c->hop_kind[prec][l] = pf;
-                float ms = 0.f;
-                TRY(time_hops(c, prec, N, 5, &ms));
-                if (ms > 0.f && ms < best) {
-                    best = ms;
-                    bR = R;
-                    bB = B;
-                    bP = pf;
+                for (int m = 0; m < 2; ++m) {
+                    c->hop_R[prec][l][m] = R;
+                    c->hop_block[prec][l][m] = B;
+                    c->hop_kind[prec][l][m] = pf;
                 }
-                if (pf == 0 && ms > 0.f && ms < best0) {
-                    best0 = ms;
-                    b0R = R;
-                    b0B = B;
+                for (int m = 0; m < 2; ++m) {
+                    float ms = 0.f;
+                    TRY(time_hops(c, prec, N, 5, &ms, 1 << m));
+                    if (ms > 0.f && ms < best[m]) {
+                        best[m] = ms;
+                        bR[m] = R;
+                        bB[m] = B;
+                        bP[m] = pf;
+                    }
+                    if (pf == 0 && ms > 0.f && ms < best0[m]) {
+                        best0[m] = ms;
+                        b0R[m] = R;
+                        b0B[m] = B;
+                    }
                 }
             }
         }
@@ -496,14 +511,16 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // Another kind replaces the direct kernel only when it is faster by more than
     // 2%: closer than that, which one wins is timing noise (on GB300 the
     // warp-staged kernel and the direct one are within 1% at some widths).
-    if (bP != 0 && best0 < 1e30f && best > 0.98f * best0) {
-        bR = b0R;
-        bB = b0B;
-        bP = 0;
+    for (int m = 0; m < 2; ++m) {
+        if (bP[m] != 0 && best0[m] < 1e30f && best[m] > 0.98f * best0[m]) {
+            bR[m] = b0R[m];
+            bB[m] = b0B[m];
+            bP[m] = 0;
+        }
+        c->hop_R[prec][l][m] = bR[m];
+        c->hop_block[prec][l][m] = bB[m];
+        c->hop_kind[prec][l][m] = bP[m];
     }
-    c->hop_R[prec][l] = bR;
-    c->hop_block[prec][l] = bB;
-    c->hop_kind[prec][l] = bP;
     c->hop_tuned[prec][l] = true;
     invalidate_graphs(c);
     return DL_OK;
@@ -521,14 +538,27 @@ extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int
         return fail(DL_EINVAL, "kernel kind not available for this storage layout");
     TRY(tune_hop(c, ip, N, force_R, force_block, force_pf));
     const int l = ilog2(N);
-    if (R_out) *R_out = c->hop_R[ip][l];
-    if (block_out) *block_out = c->hop_block[ip][l];
-    if (pf_out) *pf_out = c->hop_kind[ip][l];
+    if (R_out) *R_out = c->hop_R[ip][l][1];
+    if (block_out) *block_out = c->hop_block[ip][l][1];
+    if (pf_out) *pf_out = c->hop_kind[ip][l][1];
     if (ms_out) {
         float ms = 0.f;
         TRY(time_hops(c, ip, N, 10, &ms));
         *ms_out = ms;
     }
+    return DL_OK;
+}
+
+// The launch shape the context uses for the plain (fused = 0) or fused hops of
+// width n_rhs in the inner solver's storage for `precision` (no tuning).
+extern "C" int dl_hop_shape(dl_ctx *c, int precision, int n_rhs, int fused, int *R_out, int *block_out,
+                            int *kind_out) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
+    const int N = pow2_at_least(n_rhs), l = ilog2(N), ip = inner_prec(c, precision, N), m = fused ? 1 : 0;
+    if (R_out) *R_out = c->hop_R[ip][l][m];
+    if (block_out) *block_out = c->hop_block[ip][l][m];
+    if (kind_out) *kind_out = c->hop_kind[ip][l][m];
     return DL_OK;
 }
 
@@ -642,9 +672,11 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     memset(&c->tim, 0, sizeof(c->tim));
     for (int p = 0; p < 5; ++p)
         for (int l = 0; l < 8; ++l) {
-            c->hop_R[p][l] = 2;
-            c->hop_block[p][l] = 128;
-            c->hop_kind[p][l] = 0;
+            for (int m = 0; m < 2; ++m) {
+                c->hop_R[p][l][m] = 2;
+                c->hop_block[p][l][m] = 128;
+                c->hop_kind[p][l][m] = 0;
+            }
             c->hop_tuned[p][l] = false;
         }
     // coordinates table
