@@ -56,9 +56,10 @@ def parse():
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--hop-kind", type=int, default=-1,
-                    help="Wilson-hop kernel kind for the benchmark line (default -1: the autotuner's choice); "
-                         "lets a profiler run use the kernel the timed run chose, whose kind the line records")
+    ap.add_argument("--hop-shape", default=None, metavar="R:BLOCK:KIND,R:BLOCK:KIND",
+                    help="launch shapes of the plain and the fused Wilson hops for the benchmark line (default: "
+                         "the autotuner's choice); lets a profiler run use the kernels the timed run chose, "
+                         "which the line records")
     ap.add_argument("--kappa-literal", action="store_true",
                     help="the benchmark workload at kappa 0.157 on eps 0.60 links instead of kappa 0.140 on eps 0.45")
     ap.add_argument("--workload", default="stochastic",
@@ -819,7 +820,12 @@ def main():
 
     # ---- the hop's launch shape for this width (the tuner the solver would run), then warm-up
     # (captures the CUDA graphs with their timing events, fills caches)
-    ctx.tune_hop(prec, args.batch, force_pf=args.hop_kind)
+    if args.hop_shape:
+        for fused, spec in zip((False, True), args.hop_shape.split(",")):
+            r_, b_, k_ = (int(v) for v in spec.split(":"))
+            ctx.set_hop_shape(prec, args.batch, fused, r_, b_, k_)
+    else:
+        ctx.tune_hop(prec, args.batch)
     hop_shape = [ctx.hop_shape(prec, args.batch, fused) for fused in (False, True)]  # (R, block, kind)
     ctx.set_timing(True)
     for s in range(args.warmup):

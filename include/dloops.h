@@ -451,6 +451,11 @@ int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_bl
  * `precision`: right-hand sides per thread, threads per block and kernel kind
  * (outputs may be NULL).  No tuning, no GPU work.  Errors: DL_EINVAL. */
 int dl_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int fused, int *R_out, int *block_out, int *kind_out);
+/* Set that launch shape explicitly (R in {1, 2, 4}, block in {64, 128, 256},
+ * kind as dl_tune_hop; kinds 3-5 and 9 take block 64 and size their own
+ * blocks); the width then counts as tuned.  Errors: DL_EINVAL for a shape the
+ * precision, width or storage layout does not allow. */
+int dl_set_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int fused, int R, int block, int kind);
 
 /* Fused-multiply-add rate of the current device at `precision` (DL_PREC_F64 or
  * DL_PREC_F32), in TFLOP/s (2 flops per FMA), from one launch of independent

@@ -40,7 +40,7 @@ SYMBOLS = (
     "dl_create", "dl_destroy", "dl_last_error", "dl_status_string", "dl_load_gauge", "dl_set_kappa", "dl_set_clover",
     "dl_set_timing", "dl_get_timing", "dl_make_sources", "dl_make_point_sources", "dl_solve",
     "dl_solve_adjoint", "dl_apply_hop", "dl_apply_m", "dl_apply_dm_dkappa", "dl_apply_clover", "dl_apply_smear", "dl_apply_gamma_weights",
-    "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop", "dl_hop_shape",
+    "dl_trace_loops", "dl_exact_loops", "dl_tsm_estimate", "dl_bench_hop", "dl_tune_hop", "dl_hop_shape", "dl_set_hop_shape",
     "dl_trace_loops_noalloc", "dl_bench_fma", "dl_trace_loops_mom", "dl_meson_correlators", "dl_disconnected",
     "dl_apply_hop_prec", "dl_dilution_error",
 )
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
         "dl_bench_hop": (i, [vp, i, i, i, i, P(d), P(d)]),
         "dl_tune_hop": (i, [vp, i, i, i, i, i, P(i), P(i), P(i), P(d)]),
         "dl_hop_shape": (i, [vp, i, i, i, P(i), P(i), P(i)]),
+        "dl_set_hop_shape": (i, [vp, i, i, i, i, i, i]),
         "dl_trace_loops_noalloc": (i, [vp, vp, i, P(i), i, i, vp, vp]),
         "dl_bench_fma": (i, [i, vp, P(d), P(d)]),
         "dl_trace_loops_mom": (i, [vp, vp, vp, i, i, P(Smear), P(i), i, P(i), i, vp]),
@@ -554,3 +555,7 @@ class Context:
         _check(lib().dl_hop_shape(self._h, precision, n_rhs, int(fused), ctypes.byref(R), ctypes.byref(B),
                                   ctypes.byref(k)))
         return R.value, B.value, k.value
+
+    def set_hop_shape(self, precision: int, n_rhs: int, fused: bool, R: int, block: int, kind: int):
+        """Pin the launch shape of the plain or the fused hops of this width."""
+        _check(lib().dl_set_hop_shape(self._h, precision, n_rhs, int(fused), R, block, kind))

@@ -448,6 +448,24 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int wh
     return rc;
 }
 
+// Whether kernel kind pf can run the hop of width N in storage prec with R
+// right-hand sides per thread and B threads per block (bi: B's index in
+// {64, 128, 256}).
+static bool shape_ok(int prec, int N, int R, int B, int bi, int pf) {
+    if (prec == P_F32P ? (pf != 0 && pf < 7) : pf >= 7) return false;  // the paired layout: kinds 0, 7, 8, 9
+    if (pf < 0 || pf > 9 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
+    if (R > N || B % (N / R)) return false;
+    if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) return false;
+    if ((pf == 3 || pf == 4 || pf == 5) && bi > 0) return false;  // the launcher picks the block
+    if ((pf == 4 || pf == 5) && N != 32 * R) return false;         // one site per warp
+    if (pf == 5 && (prec != P_BF16 || R > 2)) return false;         // tensor cores: BF16 storage
+    if (pf == 6 && (prec != P_F32 || R != 1)) return false;         // packed FP32 arithmetic
+    if (pf >= 7 && R != 2) return false;                            // paired layout: two per thread
+    if (pf == 9 && (bi > 0 || (N != 32 && N != 64))) return false;  // warp-staged pairs: N = 32, 64
+    if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) return false;
+    return true;
+}
+
 static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, int force_pf) {
     const int l = ilog2(N);
     TRY(ensure_ws(c, N));
@@ -469,22 +487,13 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     for (int sweep = 0; sweep < 2; ++sweep)
     for (int pf = 0; pf < (prec == P_F64 ? 1 : 10); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
-        if (prec == P_F32P ? (pf != 0 && pf < 7) : pf >= 7) continue;  // the paired layout: kinds 0, 7, 8, 9
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
-            if (prec == P_F64 && R != 1) continue;
-            if (R > N || (force_R && R != force_R)) continue;
+            if (force_R && R != force_R) continue;
             for (int bi = 0; bi < 3; ++bi) {
                 const int B = Bs[bi];
-                if (B % (N / R) || (force_block && B != force_block)) continue;
-                if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) continue;
-                if ((pf == 3 || pf == 4 || pf == 5) && bi > 0) continue;  // the launcher picks the block
-                if ((pf == 4 || pf == 5) && N != 32 * R) continue;         // one site per warp
-                if (pf == 5 && (prec != P_BF16 || R > 2)) continue;         // tensor cores: BF16 storage
-                if (pf == 6 && (prec != P_F32 || R != 1)) continue;         // packed FP32 arithmetic
-                if (pf >= 7 && R != 2) continue;                            // paired layout: two per thread
-                if (pf == 9 && (bi > 0 || (N != 32 && N != 64))) continue;  // warp-staged pairs: N = 32, 64
-                if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) continue;
+                if (force_block && B != force_block) continue;
+                if (!shape_ok(prec, N, R, B, bi, pf)) continue;
                 for (int m = 0; m < 2; ++m) {
                     c->hop_R[prec][l][m] = R;
                     c->hop_block[prec][l][m] = B;
@@ -559,6 +568,23 @@ extern "C" int dl_hop_shape(dl_ctx *c, int precision, int n_rhs, int fused, int 
     if (R_out) *R_out = c->hop_R[ip][l][m];
     if (block_out) *block_out = c->hop_block[ip][l][m];
     if (kind_out) *kind_out = c->hop_kind[ip][l][m];
+    return DL_OK;
+}
+
+// Set the launch shape of the plain (fused = 0) or fused hops of this width
+// explicitly (it then counts as tuned).
+extern "C" int dl_set_hop_shape(dl_ctx *c, int precision, int n_rhs, int fused, int R, int block, int kind) {
+    if (!c) return fail(DL_EINVAL, "null context");
+    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
+    const int N = pow2_at_least(n_rhs), l = ilog2(N), ip = inner_prec(c, precision, N), m = fused ? 1 : 0;
+    const int bi = block == 64 ? 0 : (block == 128 ? 1 : (block == 256 ? 2 : -1));
+    if ((R != 1 && R != 2 && R != 4) || bi < 0 || !shape_ok(ip, N, R, block, bi, kind))
+        return fail(DL_EINVAL, "launch shape not available for this precision, width and layout");
+    c->hop_R[ip][l][m] = R;
+    c->hop_block[ip][l][m] = block;
+    c->hop_kind[ip][l][m] = kind;
+    c->hop_tuned[ip][l] = true;
+    invalidate_graphs(c);
     return DL_OK;
 }
 

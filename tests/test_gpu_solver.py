@@ -430,3 +430,26 @@ def test_skipping_stopped_rhs_changes_nothing(lib, prec, kind, monkeypatch):
     assert np.array_equal(sols["1"][0], sols["0"][0])
     assert sols["1"][1] == sols["0"][1]
     assert len(set(sols["1"][1])) > 1  # the batch really held right-hand sides that stopped early
+
+
+def test_plain_and_fused_hops_on_different_kernels(lib):
+    """The plain and the fused hops take their launch shapes separately: a solve with the direct
+    kernel for the plain hops and the warp-staged one for the fused hops (the tuner's choice on GB300
+    at width 32) reaches the tolerance, and shapes a width cannot run are refused."""
+    dims, kappa = (8, 8, 8, 24), 0.12
+    U = synthetic.gauge_field(dims, eps=0.45, seed=13)
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    c.set_kappa(kappa)
+    b = synthetic.random_spinor(dims, seed=23, n=32)
+    c.set_hop_shape(1, 32, False, 1, 128, 0)
+    c.set_hop_shape(1, 32, True, 1, 64, 4)
+    assert c.hop_shape(1, 32, False) == (1, 128, 0) and c.hop_shape(1, 32, True) == (1, 64, 4)
+    x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=1, batch=32))
+    assert all(s["status"] == 0 for s in st), st
+    res = residual(U, x.cpu().numpy()[[0, 31]], b[[0, 31]], kappa)
+    assert np.all(res <= 1e-11), res
+    for bad in ((1, 128, 4), (2, 64, 4), (1, 64, 5), (1, 64, 7), (3, 64, 0), (1, 96, 0)):
+        with pytest.raises(lib.DlError):
+            c.set_hop_shape(1, 32, True, *bad)
+    c.close()
