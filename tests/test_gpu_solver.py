@@ -170,7 +170,7 @@ def test_solve_full_size(lib, prec):
 
 def plain_f32_layout(monkeypatch, prec, kind):
     """FP32 fields of the contexts made now: paired for kinds 7-9, which read that layout only."""
-    if prec == 1 and kind >= 7:
+    if prec == 1 and 7 <= kind <= 9:
         monkeypatch.setenv("DLOOPS_F32_PAIRS", "1")
 
 
@@ -179,7 +179,7 @@ def plain_f32_layout(monkeypatch, prec, kind):
 def test_hop_kernel_kinds(lib, prec, kind, batch, monkeypatch):
     """Direct, cp.async-prefetching, bulk-copy-staged, blocked-mapping and hypercube-ordered hops, and
     the paired-layout packed-FP32 hops (kinds 7, 8: FP32 of even width), all solve to tolerance."""
-    if kind >= 7 and batch == 1:
+    if 7 <= kind <= 9 and batch == 1:
         pytest.skip("the paired layout holds two right-hand sides per group: even widths only")
     if kind == 9 and batch != 64:
         pytest.skip("the warp-staged paired hop serves widths 32 and 64")
