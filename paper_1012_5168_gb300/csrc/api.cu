@@ -460,7 +460,7 @@ static bool shape_ok(int prec, int N, int R, int B, int bi, int pf) {
     if ((pf == 4 || pf == 5) && N != 32 * R) return false;         // one site per warp
     if (pf == 5 && (prec != P_BF16 || R > 2)) return false;         // tensor cores: BF16 storage
     if (pf == 6 && (prec != P_F32 || R != 1)) return false;         // packed FP32 arithmetic
-    if (pf >= 7 && R != 2) return false;                            // paired layout: two per thread
+    if (pf >= 7 && pf <= 9 && R != 2) return false;                 // paired layout: two per thread
     if (pf == 9 && (bi > 0 || (N != 32 && N != 64))) return false;  // warp-staged pairs: N = 32, 64
     if (pf == 2 && (B / (N / R) < 1 || tma_smem_bytes(prec, N, B / (N / R)) > 200 * 1024)) return false;
     return true;
