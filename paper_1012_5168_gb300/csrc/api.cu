@@ -144,7 +144,7 @@ struct dl_ctx {
     int hop_kind[5][8][2];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
                           // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic, 7 paired layout with
                           // packed FP32 arithmetic, 8 the same under a 128-register cap, 9 paired and
-                          // warp-staged, 10 direct over the sites in hypercube order
+                          // warp-staged
     bool hop_tuned[5][8];
     bool autotune = true;
 };
@@ -452,7 +452,7 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int wh
 // right-hand sides per thread and B threads per block (bi: B's index in
 // {64, 128, 256}).
 static bool shape_ok(int prec, int N, int R, int B, int bi, int pf) {
-    if (pf < 0 || pf > 10 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
+    if (pf < 0 || pf > 9 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
     if (prec == P_F32P ? (pf != 0 && (pf < 7 || pf > 9)) : (pf >= 7 && pf <= 9)) return false;  // paired: 0, 7-9
     if (R > N || B % (N / R)) return false;
     if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) return false;
@@ -485,7 +485,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // shape timed while the GPU was still ramping its clocks or finishing other
     // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 11); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 10); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];

@@ -57,8 +57,7 @@ struct HopArgs {
     Geom g;
     const void *gauge8;     // [2][Vh][8][9] complex, site-major links (staged kernel)
     int *err;               // [2]: the staged kernel sets [0] when a bounded wait runs out, [1] when a drain wait does too
-    int blocked;            // direct kernel: 0 cyclic site mapping, 1 one contiguous range per block,
-                            // 2 cyclic over 2^4 hypercubes (full-lattice launches only)
+    int blocked;            // direct kernel: 0 cyclic site mapping, 1 one contiguous range per block
     const float4 *gauge8q;  // [2][Vh][8][9] FP32 quads (Re V, Re V, -Im V, Im V), V = U (forward) or U^dag
                             // (backward, already conjugated): the packed-arithmetic kernel's links
     const int *act;         // per right-hand side r: act[r * act_stride] != 0 if it takes part in this
@@ -280,21 +279,6 @@ __device__ __forceinline__ void hop_dir_x2(const HopArgs &A, const Site &st, int
 // NC > 0: the number of right-hand sides in the layout is the compile-time
 // constant NC (= A.N), so component offsets fold into the load and store
 // instructions; NC = 0 reads it from A.N.
-// Site s of parity p in hypercube order: the lattice is cut into 2^4
-// hypercubes, numbered x-fastest by their origin (2X, 2Y, 2Z, 2T), and each
-// holds 8 sites of each parity, s & 7 picking the offsets (a, b, c) from its
-// bits and d from the parity.  Consecutive sites (and so the threads of one
-// block) then share most of their neighbours: four of the eight neighbours of
-// each site lie inside its hypercube, each reached from four sites.
-__device__ __forceinline__ int hypercube_cb(int s, int p, const Geom &g) {
-    const unsigned k = (unsigned)s & 7u, grp = (unsigned)s >> 3;
-    const unsigned hx = (unsigned)g.L[0] >> 1, hy = (unsigned)g.L[1] >> 1, hz = (unsigned)g.L[2] >> 1;
-    const unsigned X = grp % hx, r1 = grp / hx, Y = r1 % hy, r2 = r1 / hy, Z = r2 % hz, T = r2 / hz;
-    const unsigned a = k & 1u, b = (k >> 1) & 1u, c = (k >> 2) & 1u, d = ((unsigned)p - a - b - c) & 1u;
-    const int x = (int)(2 * X + a), y = (int)(2 * Y + b), z = (int)(2 * Z + c), t = (int)(2 * T + d);
-    return (x + g.stride[1] * y + g.stride[2] * z + g.stride[3] * t) >> 1;
-}
-
 template <typename S, int R, int MODE, int RED, int NC = 0, int X2 = 0, int CLOV = 0>
 __device__ __forceinline__ void hop_body(const HopArgs &A) {
     typedef typename Real<S>::type T;
@@ -317,7 +301,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
     // range of sites, so the neighbours loaded for one step (the same and the adjacent
     // x-rows of the other parity) are still in L1 for the next steps.
     int idx = blockIdx.x * blockDim.x + threadIdx.x, idx_end = total, stride = gridDim.x * blockDim.x;
-    if (A.blocked == 1) {
+    if (A.blocked) {
         const int per = ((total + (int)gridDim.x - 1) / (int)gridDim.x + (int)blockDim.x - 1) / (int)blockDim.x *
                         (int)blockDim.x;
         idx = blockIdx.x * per + threadIdx.x;
@@ -335,7 +319,7 @@ __device__ __forceinline__ void hop_body(const HopArgs &A) {
         if (!any) idx = idx_end;
     }
     for (; idx < idx_end; idx += stride) {
-        const int cb = A.blocked == 2 ? hypercube_cb(idx >> lgG, A.p, A.g) : A.cb_begin + (idx >> lgG);
+        const int cb = A.cb_begin + (idx >> lgG);
         const int r0 = (idx & (G - 1)) * R;
         const Site st = decode(__ldg(A.coords + (size_t)A.p * A.g.Vh + cb), A.g);
         cx<T> acc[R][12];

@@ -51,18 +51,16 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
         if constexpr (cap > 0) return hop_kernel_cap<S, R, MODE, RED, cap>;
         else return hop_kernel<S, R, MODE, RED>;
     }();
-    if (kind == 0 || kind == 10) {
-        HopArgs b = a;  // kind 10: the direct kernel over the sites in hypercube order
-        if (kind == 10 && a.cb_begin == 0 && a.cb_end == a.g.Vh) b.blocked = 2;
+    if (kind == 0) {
         if constexpr (cap > 0) {
             if (a.N == 32) {  // the benchmark width: offsets as compile-time constants
                 clamp_grid(l, resident_blocks(hop_kernel_cap<S, R, MODE, RED, cap, 32>, l.block, l.smem));
-                hop_kernel_cap<S, R, MODE, RED, cap, 32><<<l.grid, l.block, l.smem, l.stream>>>(b);
+                hop_kernel_cap<S, R, MODE, RED, cap, 32><<<l.grid, l.block, l.smem, l.stream>>>(a);
                 return cudaGetLastError();
             }
         }
         clamp_grid(l, resident_blocks(direct, l.block, l.smem));
-        direct<<<l.grid, l.block, l.smem, l.stream>>>(b);
+        direct<<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
     }
     if (kind == 1) {
