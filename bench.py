@@ -44,7 +44,8 @@ HOP_KIND_NAMES = {0: "hop_kernel_cap (direct)", 1: "hop_kernel_pf (cp.async pref
                   2: "hop_kernel_tma (block-staged)", 3: "hop_kernel (blocked order)",
                   4: "hop_kernel_ws (warp-staged)", 5: "hop_kernel_mma (tensor cores)",
                   6: "hop_kernel_x2 (packed FP32)", 7: "hop_kernel_pair (paired layout)",
-                  8: "hop_kernel_pair_cap (paired layout)", 9: "hop_kernel_ws_pair (paired, warp-staged)"}
+                  8: "hop_kernel_pair_cap (paired layout)", 9: "hop_kernel_ws_pair (paired, warp-staged)",
+                  10: "hop_kernel_cap (direct, wider register cap)"}
 
 
 def parse():
@@ -56,10 +57,10 @@ def parse():
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--hop-shape", default=None, metavar="R:BLOCK:KIND,R:BLOCK:KIND",
-                    help="launch shapes of the plain and the fused Wilson hops for the benchmark line (default: "
-                         "the autotuner's choice); lets a profiler run use the kernels the timed run chose, "
-                         "which the line records")
+    ap.add_argument("--hop-shape", default=None, metavar="R:BLOCK:KIND,R:BLOCK:KIND,R:BLOCK:KIND",
+                    help="launch shapes of the plain, the <rhat, v>-fused and the five-reduction fused Wilson "
+                         "hops for the benchmark line (default: the autotuner's choice); lets a profiler run "
+                         "use the kernels the timed run chose, which the line records")
     ap.add_argument("--kappa-literal", action="store_true",
                     help="the benchmark workload at kappa 0.157 on eps 0.60 links instead of kappa 0.140 on eps 0.45")
     ap.add_argument("--workload", default="stochastic",
@@ -99,10 +100,11 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
-# The ncu summary of the FP32 hop at the bench width, and the source files each
+# The ncu summary of the FP32 hops at the bench width, and the source files each
 # kernel kind it covers is built from: its figures count only while those are unchanged.
+# Its per-launch DRAM lines are keyed by kind and hop: plain, r0dot, bicg.
 TRAFFIC_PROFILE = os.path.join("profiles", "hop_f32_fused_n32_16x16x16x32.md")
-TRAFFIC_SOURCES = {0: ["hop.cuh"], 4: ["hop.cuh", "hop_tma.cuh", "hop_ws.cuh"]}
+TRAFFIC_SOURCES = {0: ["hop.cuh"], 4: ["hop.cuh", "hop_tma.cuh", "hop_ws.cuh"], 10: ["hop.cuh", "hop_launch.cuh"]}
 
 
 def sources_sha(hop_kind: int):
@@ -261,9 +263,9 @@ def hop_profile(spec: str):
     ctx.load_gauge(synthetic.gauge_field(w["dims"], w["eps"], w["seed"]))
     ctx.set_kappa(w["kappa"])
     shape = ctx.tune_hop(prec, n, force_R=force_r, force_block=force_b, force_pf=kind)
-    plain = ctx.hop_shape(prec, n, False)
-    out = {"precision": parts[0], "n_rhs": n, "R": shape[0], "block": shape[1], "kind": shape[2],
-           "plain_shape": {"R": plain[0], "block": plain[1], "kind": plain[2]}}
+    out = {"precision": parts[0], "n_rhs": n,
+           "shapes": {name: dict(zip(("R", "block", "kind"), ctx.hop_shape(prec, n, cls)))
+                      for cls, name in enumerate(("plain", "fused", "fused_bicg"))}}
     for fused, name in ((0, "plain"), (1, "fused"), (2, "fused_bicg")):
         ms, by = ctx.bench_hop(prec, n, fused, reps=5)
         out[name] = {"ms": round(ms, 5), "GB/s": round(by / ms / 1e6, 1)}
@@ -821,12 +823,12 @@ def main():
     # ---- the hop's launch shape for this width (the tuner the solver would run), then warm-up
     # (captures the CUDA graphs with their timing events, fills caches)
     if args.hop_shape:
-        for fused, spec in zip((False, True), args.hop_shape.split(",")):
+        for cls, spec in enumerate(args.hop_shape.split(",")):
             r_, b_, k_ = (int(v) for v in spec.split(":"))
-            ctx.set_hop_shape(prec, args.batch, fused, r_, b_, k_)
+            ctx.set_hop_shape(prec, args.batch, cls, r_, b_, k_)
     else:
         ctx.tune_hop(prec, args.batch)
-    hop_shape = [ctx.hop_shape(prec, args.batch, fused) for fused in (False, True)]  # (R, block, kind)
+    hop_shape = [ctx.hop_shape(prec, args.batch, cls) for cls in (0, 1, 2)]  # (R, block, kind) per class
     ctx.set_timing(True)
     for s in range(args.warmup):
         run_step(ctx, dl, 1000 + s, noise0, params, store)
@@ -899,13 +901,26 @@ def main():
     per_launch_ms = tim["hop_ms"][dom] / max(tim["hop_launches"][dom], 1)
     per_launch_bytes = tim["hop_bytes"][dom] / max(tim["hop_launches"][dom], 1)
     achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
-    dR, dB, dk = hop_shape[dom % 2]  # the launch shape of the dominant class (plain 0, fused 1)
-    traffic = read_traffic(kinds[dom], dk) if args.batch == 32 and args.precision == "f32" else None
+    def traffic_of(name, kind):  # name: plain, r0dot or bicg
+        return read_traffic(name, kind) if args.batch == 32 and args.precision == "f32" else None
+
+    def shape_desc(sh):
+        return f"{HOP_KIND_NAMES.get(sh[2], sh[2])} ({sh[0]} right-hand side(s) per thread, block {sh[1]})"
+
+    def class_info(k):  # kernel description, kind(s) and ncu traffic of timing class k
+        if k == 0:
+            return f"plain hop: {shape_desc(hop_shape[0])}", hop_shape[0][2], traffic_of("plain", hop_shape[0][2])
+        if k == 1:
+            t1, t2 = traffic_of("r0dot", hop_shape[1][2]), traffic_of("bicg", hop_shape[2][2])
+            return (f"fused hops: <rhat, v> {shape_desc(hop_shape[1])}; five reductions {shape_desc(hop_shape[2])}",
+                    [hop_shape[1][2], hop_shape[2][2]], (t1 + t2) / 2 if t1 and t2 else None)
+        return "hop_kernel<double> (FP64)", 0, None
+
+    dkernel, dkind, traffic = class_info(dom)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": f"{HOP_KIND_NAMES.get(dk, dk)} {kinds[dom]} ({args.precision} storage, "
-                          f"batch {args.batch}, {dR} right-hand side(s) per thread, block {dB})",
-                "hop_kind": dk,
+                "kernel": f"{kinds[dom]} ({args.precision} storage, batch {args.batch}): {dkernel}",
+                "hop_kind": dkind,
                 "peak_source": f"{peak_src} hbm_gbs", "algorithmic_bytes_per_launch": per_launch_bytes,
                 "launches": tim["hop_launches"][dom], "ms_per_launch": round(per_launch_ms, 5),
                 "hop_share_of_step": round(sum(tim["hop_ms"]) / ms, 3) if ms > 0 else None}
@@ -914,14 +929,12 @@ def main():
     if other is not None and tim["hop_launches"][other] > 0:
         o_ms = tim["hop_ms"][other] / tim["hop_launches"][other]
         o_bytes = tim["hop_bytes"][other] / tim["hop_launches"][other]
-        oR, oB, ok = hop_shape[other]
-        roofline["other_hop"] = {"class": kinds[other], "kernel": HOP_KIND_NAMES.get(ok, ok), "hop_kind": ok,
-                                 "R": oR, "block": oB, "ms_per_launch": round(o_ms, 5),
+        okernel, okind, otraffic = class_info(other)
+        roofline["other_hop"] = {"class": kinds[other], "kernel": okernel, "hop_kind": okind,
+                                 "ms_per_launch": round(o_ms, 5),
                                  "achieved": round(o_bytes / (o_ms / 1e3) / 1e9, 1),
                                  "frac": round(o_bytes / (o_ms / 1e3) / 1e9 / peak, 4),
-                                 "algorithmic_bytes_per_launch": o_bytes,
-                                 "traffic": read_traffic(kinds[other], ok)
-                                 if args.batch == 32 and args.precision == "f32" else None}
+                                 "algorithmic_bytes_per_launch": o_bytes, "traffic": otraffic}
 
     # defect-correction hops (b_hat, reconstruction, residual) of the timed steps
     n_oh = tim["hop_launches"][2] + tim["hop_launches"][3]

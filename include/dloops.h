@@ -432,30 +432,33 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
  * n_rhs = 32 R, i.e. widths 32 and 64), 5 BF16 on the tensor cores (n_rhs =
  * 32 R), 6 packed FP32 arithmetic; on the paired FP32 layout
  * (DLOOPS_F32_PAIRS=1, even widths) 0, 7 and 8 (packed, uncapped and capped)
- * and 9 (packed, warp-staged; widths 32 and 64).  Each candidate times the
- * plain hop and the fused hop with the five BiCGStab reductions on random
- * fields, in two sweeps over all candidates, and the fastest is kept for each
- * of the two separately (so the plain and the fused hops may use different
+ * and 9 (packed, warp-staged; widths 32 and 64); 10 the direct FP32 kernel
+ * under a wider register cap (R = 1).  Each candidate times three classes of
+ * hops on random fields: the plain hop (class 0), the fused hop with <rhat, v>
+ * (class 1, which also serves the other fused hops) and the fused hop with the
+ * five BiCGStab reductions (class 2), in two sweeps over all candidates, and
+ * the fastest is kept for each class separately (so they may use different
  * kernels); another kind replaces the direct kernel only when it is more than
  * 2% faster.  force_R / force_block > 0 and force_pf >= 0 restrict the
- * candidates (for both).  Solves tune their (precision, batch) on first use.
- * *R_out, *block_out, *pf_out receive the fused hop's choice and *ms_out the
- * time of one plain plus one fused hop (each may be NULL).  The call
+ * candidates (for all classes).  Solves tune their (precision, batch) on first
+ * use.  *R_out, *block_out, *pf_out receive the class-2 choice and *ms_out the
+ * time of one plain plus one class-2 hop (each may be NULL).  The call
  * overwrites the context's inner workspace, so make it between solves.
  * Errors: DL_EINVAL (arguments, or a kind the storage layout lacks),
  * DL_ESTATE (no gauge field), DL_ECUDA. */
 int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_block, int force_pf,
                 int *R_out, int *block_out, int *pf_out, double *ms_out);
-/* The launch shape the context currently uses for the plain (fused = 0) or the
- * fused (fused != 0) Wilson hops of width n_rhs in the inner storage for
- * `precision`: right-hand sides per thread, threads per block and kernel kind
- * (outputs may be NULL).  No tuning, no GPU work.  Errors: DL_EINVAL. */
-int dl_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int fused, int *R_out, int *block_out, int *kind_out);
+/* The launch shape the context currently uses for one class of Wilson hops
+ * (cls: 0 plain, 1 fused, 2 fused with the five BiCGStab reductions; see
+ * dl_tune_hop) of width n_rhs in the inner storage for `precision`:
+ * right-hand sides per thread, threads per block and kernel kind (outputs may
+ * be NULL).  No tuning, no GPU work.  Errors: DL_EINVAL. */
+int dl_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int cls, int *R_out, int *block_out, int *kind_out);
 /* Set that launch shape explicitly (R in {1, 2, 4}, block in {64, 128, 256},
  * kind as dl_tune_hop; kinds 3-5 and 9 take block 64 and size their own
  * blocks); the width then counts as tuned.  Errors: DL_EINVAL for a shape the
  * precision, width or storage layout does not allow. */
-int dl_set_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int fused, int R, int block, int kind);
+int dl_set_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int cls, int R, int block, int kind);
 
 /* Fused-multiply-add rate of the current device at `precision` (DL_PREC_F64 or
  * DL_PREC_F32), in TFLOP/s (2 flops per FMA), from one launch of independent

@@ -549,13 +549,14 @@ class Context:
                                  ctypes.byref(B), ctypes.byref(pf), ctypes.byref(ms)))
         return R.value, B.value, pf.value, ms.value
 
-    def hop_shape(self, precision: int, n_rhs: int, fused: bool):
-        """(R, block, kind) the context uses for the plain or the fused hops of this width."""
+    def hop_shape(self, precision: int, n_rhs: int, cls: int):
+        """(R, block, kind) the context uses for a class of hops of this width: 0 plain, 1 fused,
+        2 fused with the five BiCGStab reductions."""
         R, B, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(lib().dl_hop_shape(self._h, precision, n_rhs, int(fused), ctypes.byref(R), ctypes.byref(B),
+        _check(lib().dl_hop_shape(self._h, precision, n_rhs, int(cls), ctypes.byref(R), ctypes.byref(B),
                                   ctypes.byref(k)))
         return R.value, B.value, k.value
 
-    def set_hop_shape(self, precision: int, n_rhs: int, fused: bool, R: int, block: int, kind: int):
-        """Pin the launch shape of the plain or the fused hops of this width."""
-        _check(lib().dl_set_hop_shape(self._h, precision, n_rhs, int(fused), R, block, kind))
+    def set_hop_shape(self, precision: int, n_rhs: int, cls: int, R: int, block: int, kind: int):
+        """Pin the launch shape of a class of hops of this width (classes as hop_shape)."""
+        _check(lib().dl_set_hop_shape(self._h, precision, n_rhs, int(cls), R, block, kind))

@@ -136,15 +136,16 @@ struct dl_ctx {
     std::vector<cudaEvent_t> event_pool;
     dl_timing tim;
     int64_t kernel_launches = 0;
-    // Launch shape of the Wilson hop per [prec][log2 N][m], m = 0 for the plain hop
-    // (D_oe p, D_oe s) and 1 for the fused ones (XPAY with reductions): each is
-    // tuned on its own, so the two may use different kernels.
-    int hop_R[5][8][2];      // right-hand sides per thread
-    int hop_block[5][8][2];  // threads per block
-    int hop_kind[5][8][2];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
+    // Launch shape of the Wilson hop per [prec][log2 N][m]: m = 0 the plain hop
+    // (D_oe p, D_oe s), 1 the fused hops other than BiCGStab's second (XPAY with
+    // <rhat, v> or a norm), 2 the fused hop with the five BiCGStab reductions.
+    // Each is tuned on its own, so they may use different kernels.
+    int hop_R[5][8][3];      // right-hand sides per thread
+    int hop_block[5][8][3];  // threads per block
+    int hop_kind[5][8][3];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
                           // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic, 7 paired layout with
                           // packed FP32 arithmetic, 8 the same under a 128-register cap, 9 paired and
-                          // warp-staged
+                          // warp-staged, 10 direct under a wider register cap
     bool hop_tuned[5][8];
     bool autotune = true;
 };
@@ -230,6 +231,11 @@ static void record(dl_ctx *c, cudaEvent_t e) {
 
 // Wilson hop launch.  kind >= 0 marks launches timed with CUDA events.
 // P_DFF: `in` is float-float; ffmt flags FF_Y / FF_OUT give the formats of y and out.
+// The tuning class of a hop: 0 plain, 1 fused (other than BICG), 2 fused with the five reductions.
+static int hop_class(int mode, int red) {
+    return (mode == MODE_PLAIN && red == RED_NONE) ? 0 : (red == RED_BICG ? 2 : 1);
+}
+
 // clov: the clover solve's inner hop A^-1 D (A^-1 of the output parity p in the epilogue;
 // FP64, FP32 or BF16 storage, the direct kernel with one right-hand side per thread).
 static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void *in, const void *y, const void *z,
@@ -269,7 +275,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
                 : prec == P_F64 ? (const void *)c->d_clovinv64
                 : f32           ? (const void *)c->d_clovinv32
                                 : (const void *)c->d_clovinv16;
-    const int m = (mode == MODE_PLAIN && red == RED_NONE) ? 0 : 1;  // the shape tables' plain / fused entry
+    const int m = hop_class(mode, red);  // the shape tables' entry
     int R = (wide || clov) ? 1 : c->hop_R[prec][ilog2(N)][m];
     if (R > N) R = N;
     const int G = N / R;
@@ -422,7 +428,8 @@ static int ensure_partials(dl_ctx *c, size_t elems) {
 // hop and the fused hop with the five BiCGStab reductions (one of each per
 // inner half-iteration), and keeps the fastest shape for each.  Uses the inner
 // workspace, so it runs before a solve fills it.
-// which: bit 0 the plain hop, bit 1 the fused one.
+// which: bit 0 the plain hop, bit 1 the fused one with the five reductions, bit 2
+// the fused one with <rhat, v>.
 static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int which = 3) {
     const int Vh = (int)c->Vh;
     cudaEvent_t e0 = get_event(c), e1 = get_event(c);
@@ -436,6 +443,9 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int wh
                         Vh, nullptr, nullptr);
         if (rc == DL_OK && (which & 2))
             rc = do_hop(c, prec, MODE_XPAY, RED_BICG, c->lo[6], c->lo[7], c->lo[5], nullptr, c->lo[2], 0, N, -0.02, 0,
+                        Vh, c->d_partials, nullptr);
+        if (rc == DL_OK && (which & 4))
+            rc = do_hop(c, prec, MODE_XPAY, RED_R0DOT, c->lo[4], c->lo[7], c->lo[3], nullptr, c->lo[2], 0, N, -0.02, 0,
                         Vh, c->d_partials, nullptr);
     }
     cudaEventRecord(e1, c->cur);
@@ -452,7 +462,8 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int wh
 // right-hand sides per thread and B threads per block (bi: B's index in
 // {64, 128, 256}).
 static bool shape_ok(int prec, int N, int R, int B, int bi, int pf) {
-    if (pf < 0 || pf > 9 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
+    if (pf < 0 || pf > 10 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
+    if (pf == 10 && (prec != P_F32 || R != 1)) return false;       // wider-cap direct: FP32, one per thread
     if (prec == P_F32P ? (pf != 0 && (pf < 7 || pf > 9)) : (pf >= 7 && pf <= 9)) return false;  // paired: 0, 7-9
     if (R > N || B % (N / R)) return false;
     if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) return false;
@@ -473,9 +484,10 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     c->cur = c->stream;
     const size_t ne = half_elems(c, N);
     for (int k = 0; k < 8; ++k) CK(launch_fill(prec, c->lo[k], ne, 77u + k, c->stream));
-    float best[2] = {1e30f, 1e30f}, best0[2] = {1e30f, 1e30f};  // [plain, fused]: all kinds; kind 0
-    int bR[2], bB[2], bP[2], b0R[2], b0B[2];
-    for (int m = 0; m < 2; ++m) {
+    float best[3] = {1e30f, 1e30f, 1e30f}, best0[3] = {1e30f, 1e30f, 1e30f};  // per class: all kinds; kind 0
+    int bR[3], bB[3], bP[3], b0R[3], b0B[3];
+    const int which_of[3] = {1, 4, 2};  // the hop time_hops times for each class
+    for (int m = 0; m < 3; ++m) {
         bR[m] = b0R[m] = c->hop_R[prec][l][m];
         bB[m] = b0B[m] = c->hop_block[prec][l][m];
         bP[m] = c->hop_kind[prec][l][m];
@@ -485,7 +497,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // shape timed while the GPU was still ramping its clocks or finishing other
     // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 10); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 11); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];
@@ -494,14 +506,14 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
                 const int B = Bs[bi];
                 if (force_block && B != force_block) continue;
                 if (!shape_ok(prec, N, R, B, bi, pf)) continue;
-                for (int m = 0; m < 2; ++m) {
+                for (int m = 0; m < 3; ++m) {
                     c->hop_R[prec][l][m] = R;
                     c->hop_block[prec][l][m] = B;
                     c->hop_kind[prec][l][m] = pf;
                 }
-                for (int m = 0; m < 2; ++m) {
+                for (int m = 0; m < 3; ++m) {
                     float ms = 0.f;
-                    TRY(time_hops(c, prec, N, 5, &ms, 1 << m));
+                    TRY(time_hops(c, prec, N, 5, &ms, which_of[m]));
                     if (ms > 0.f && ms < best[m]) {
                         best[m] = ms;
                         bR[m] = R;
@@ -520,7 +532,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // Another kind replaces the direct kernel only when it is faster by more than
     // 2%: closer than that, which one wins is timing noise (on GB300 the
     // warp-staged kernel and the direct one are within 1% at some widths).
-    for (int m = 0; m < 2; ++m) {
+    for (int m = 0; m < 3; ++m) {
         if (bP[m] != 0 && best0[m] < 1e30f && best[m] > 0.98f * best0[m]) {
             bR[m] = b0R[m];
             bB[m] = b0B[m];
@@ -548,9 +560,9 @@ extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int
         return fail(DL_EINVAL, "kernel kind not available for this storage layout");
     TRY(tune_hop(c, ip, N, force_R, force_block, force_pf));
     const int l = ilog2(N);
-    if (R_out) *R_out = c->hop_R[ip][l][1];
-    if (block_out) *block_out = c->hop_block[ip][l][1];
-    if (pf_out) *pf_out = c->hop_kind[ip][l][1];
+    if (R_out) *R_out = c->hop_R[ip][l][2];
+    if (block_out) *block_out = c->hop_block[ip][l][2];
+    if (pf_out) *pf_out = c->hop_kind[ip][l][2];
     if (ms_out) {
         float ms = 0.f;
         TRY(time_hops(c, ip, N, 10, &ms));
@@ -559,25 +571,28 @@ extern "C" int dl_tune_hop(dl_ctx *c, int precision, int n_rhs, int force_R, int
     return DL_OK;
 }
 
-// The launch shape the context uses for the plain (fused = 0) or fused hops of
-// width n_rhs in the inner solver's storage for `precision` (no tuning).
-extern "C" int dl_hop_shape(dl_ctx *c, int precision, int n_rhs, int fused, int *R_out, int *block_out,
+// The launch shape the context uses for one class of hops (0 plain, 1 fused,
+// 2 fused with the five reductions) of width n_rhs in the inner solver's
+// storage for `precision` (no tuning).
+extern "C" int dl_hop_shape(dl_ctx *c, int precision, int n_rhs, int cls, int *R_out, int *block_out,
                             int *kind_out) {
     if (!c) return fail(DL_EINVAL, "null context");
-    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
-    const int N = pow2_at_least(n_rhs), l = ilog2(N), ip = inner_prec(c, precision, N), m = fused ? 1 : 0;
+    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64 || cls < 0 || cls > 2)
+        return fail(DL_EINVAL, "bad arguments");
+    const int N = pow2_at_least(n_rhs), l = ilog2(N), ip = inner_prec(c, precision, N), m = cls;
     if (R_out) *R_out = c->hop_R[ip][l][m];
     if (block_out) *block_out = c->hop_block[ip][l][m];
     if (kind_out) *kind_out = c->hop_kind[ip][l][m];
     return DL_OK;
 }
 
-// Set the launch shape of the plain (fused = 0) or fused hops of this width
-// explicitly (it then counts as tuned).
-extern "C" int dl_set_hop_shape(dl_ctx *c, int precision, int n_rhs, int fused, int R, int block, int kind) {
+// Set the launch shape of one class of hops of this width explicitly (it then
+// counts as tuned).
+extern "C" int dl_set_hop_shape(dl_ctx *c, int precision, int n_rhs, int cls, int R, int block, int kind) {
     if (!c) return fail(DL_EINVAL, "null context");
-    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64) return fail(DL_EINVAL, "bad arguments");
-    const int N = pow2_at_least(n_rhs), l = ilog2(N), ip = inner_prec(c, precision, N), m = fused ? 1 : 0;
+    if (precision < 0 || precision > 2 || n_rhs < 1 || n_rhs > 64 || cls < 0 || cls > 2)
+        return fail(DL_EINVAL, "bad arguments");
+    const int N = pow2_at_least(n_rhs), l = ilog2(N), ip = inner_prec(c, precision, N), m = cls;
     const int bi = block == 64 ? 0 : (block == 128 ? 1 : (block == 256 ? 2 : -1));
     if ((R != 1 && R != 2 && R != 4) || bi < 0 || !shape_ok(ip, N, R, block, bi, kind))
         return fail(DL_EINVAL, "launch shape not available for this precision, width and layout");
@@ -699,7 +714,7 @@ extern "C" int dl_create(dl_ctx **out, const int dims[4], int t_bc, void *cuda_s
     memset(&c->tim, 0, sizeof(c->tim));
     for (int p = 0; p < 5; ++p)
         for (int l = 0; l < 8; ++l) {
-            for (int m = 0; m < 2; ++m) {
+            for (int m = 0; m < 3; ++m) {
                 c->hop_R[p][l][m] = 2;
                 c->hop_block[p][l][m] = 128;
                 c->hop_kind[p][l][m] = 0;

@@ -63,6 +63,16 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
         direct<<<l.grid, l.block, l.smem, l.stream>>>(a);
         return cudaGetLastError();
     }
+    if (kind == 10) {  // the direct FP32 kernel under a wider register cap (80 plain, 96 fused)
+        if constexpr (std::is_same<S, float>::value && R == 1) {
+            constexpr int wcap = MODE == MODE_PLAIN ? 80 : 96;
+            auto k = a.N == 32 ? hop_kernel_cap<S, 1, MODE, RED, wcap, 32> : hop_kernel_cap<S, 1, MODE, RED, wcap>;
+            clamp_grid(l, resident_blocks(k, l.block, l.smem));
+            k<<<l.grid, l.block, l.smem, l.stream>>>(a);
+            return cudaGetLastError();
+        }
+        return cudaErrorInvalidValue;
+    }
     if (kind == 1) {
         static size_t opted = 0;
         static std::mutex m;

@@ -74,7 +74,7 @@ def test_low_precision_hop_error_every_kernel(lib, prec, pairs, monkeypatch):
     c.load_gauge(U)
     psi = synthetic.random_spinor(dims, seed=42, n=7)
     ref = wilson.hop(U, psi, -1.0)
-    for kind in ((0, 7, 8) if paired else (0, 1, 2, 3)):
+    for kind in ((0, 7, 8) if paired else ((0, 1, 2, 3, 10) if prec == 1 else (0, 1, 2, 3))):
         R, B, k, _ = c.tune_hop(prec, 8, force_pf=kind)
         assert k == kind
         got = c.apply_hop(to_gpu(psi), precision=prec).cpu().numpy()

@@ -174,7 +174,7 @@ def plain_f32_layout(monkeypatch, prec, kind):
         monkeypatch.setenv("DLOOPS_F32_PAIRS", "1")
 
 
-@pytest.mark.parametrize("prec, kind", [(p, k) for p in (1, 2) for k in (0, 1, 2, 3)] + [(1, 7), (1, 8), (1, 9)])
+@pytest.mark.parametrize("prec, kind", [(p, k) for p in (1, 2) for k in (0, 1, 2, 3)] + [(1, 7), (1, 8), (1, 9), (1, 10)])
 @pytest.mark.parametrize("batch", [1, 4, 16, 64])
 def test_hop_kernel_kinds(lib, prec, kind, batch, monkeypatch):
     """Direct, cp.async-prefetching, bulk-copy-staged and blocked-mapping hops, and the paired-layout
@@ -233,7 +233,7 @@ def test_hop_kernel_kinds_full_size(lib, monkeypatch):
     w = synthetic.WORKLOADS["wilson_16x16x16x32"]
     U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
     sols = []
-    for pairs, kinds in (("0", (0, 1, 2, 3, 4)), ("1", (0, 7, 8, 9))):
+    for pairs, kinds in (("0", (0, 1, 2, 3, 4, 10)), ("1", (0, 7, 8, 9))):
         monkeypatch.setenv("DLOOPS_F32_PAIRS", pairs)
         c = lib.Context(w["dims"])
         c.load_gauge(U)
@@ -433,23 +433,26 @@ def test_skipping_stopped_rhs_changes_nothing(lib, prec, kind, monkeypatch):
 
 
 def test_plain_and_fused_hops_on_different_kernels(lib):
-    """The plain and the fused hops take their launch shapes separately: a solve with the direct
-    kernel for the plain hops and the warp-staged one for the fused hops (the tuner's choice on GB300
-    at width 32) reaches the tolerance, and shapes a width cannot run are refused."""
+    """The plain and the two fused hops take their launch shapes separately: a solve with the direct
+    kernel for the plain hops, the wider-cap direct one for <rhat, v> and the warp-staged one for the
+    five-reduction hop reaches the tolerance, and shapes a width cannot run are refused."""
     dims, kappa = (8, 8, 8, 24), 0.12
     U = synthetic.gauge_field(dims, eps=0.45, seed=13)
     c = lib.Context(dims)
     c.load_gauge(U)
     c.set_kappa(kappa)
     b = synthetic.random_spinor(dims, seed=23, n=32)
-    c.set_hop_shape(1, 32, False, 1, 128, 0)
-    c.set_hop_shape(1, 32, True, 1, 64, 4)
-    assert c.hop_shape(1, 32, False) == (1, 128, 0) and c.hop_shape(1, 32, True) == (1, 64, 4)
+    c.set_hop_shape(1, 32, 0, 1, 128, 0)
+    c.set_hop_shape(1, 32, 1, 1, 64, 10)
+    c.set_hop_shape(1, 32, 2, 1, 64, 4)
+    assert [c.hop_shape(1, 32, k) for k in (0, 1, 2)] == [(1, 128, 0), (1, 64, 10), (1, 64, 4)]
     x, st = c.solve(to_gpu(b), lib.Params(tol=1e-11, precision=1, batch=32))
     assert all(s["status"] == 0 for s in st), st
     res = residual(U, x.cpu().numpy()[[0, 31]], b[[0, 31]], kappa)
     assert np.all(res <= 1e-11), res
-    for bad in ((1, 128, 4), (2, 64, 4), (1, 64, 5), (1, 64, 7), (3, 64, 0), (1, 96, 0)):
+    for bad in ((1, 128, 4), (2, 64, 4), (1, 64, 5), (1, 64, 7), (3, 64, 0), (1, 96, 0), (2, 64, 10)):
         with pytest.raises(lib.DlError):
-            c.set_hop_shape(1, 32, True, *bad)
+            c.set_hop_shape(1, 32, 2, *bad)
+    with pytest.raises(lib.DlError):
+        c.set_hop_shape(1, 32, 3, 1, 64, 0)
     c.close()
