@@ -419,7 +419,8 @@ def test_skipping_stopped_rhs_changes_nothing(lib, prec, kind, monkeypatch):
         c = lib.Context(dims)
         c.load_gauge(U)
         c.set_kappa(kappa)
-        c.tune_hop(prec, 16, force_pf=kind)
+        # one fixed launch shape for both contexts: the reductions' summation order follows it
+        c.tune_hop(prec, 16, force_R=2 if kind == 7 else 1, force_block=64, force_pf=kind)
         b = torch.cat([c.make_point_sources(12 * 37, 8), c.make_sources(seed=6, noise_first=0, n_noise=8,
                                                                           dilution=0)]).contiguous()
         x, st = c.solve(b, lib.Params(tol=1e-11, precision=prec, batch=16))
