@@ -296,7 +296,7 @@ static int do_hop(dl_ctx *c, int prec, int mode, int red, void *out, const void 
         per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(220 * 1024) / smem));
         items = (long)((cb1 - cb0 + sites - 1) / sites) * block;  // one chunk per block at a time
     }
-    Launch l = make_launch(c, items, block, smem, kind == 0 ? 16 : per_sm);
+    Launch l = make_launch(c, items, block, smem, (kind == 0 || kind == 10) ? 16 : per_sm);
     // the direct and warp-staged kernels size their grid from residency
     if (kind == 0 || kind >= 3) l.num_sms = c->num_sms;
     const bool timed = c->timing;
