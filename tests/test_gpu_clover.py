@@ -182,3 +182,25 @@ def test_clover_gradcheck_tiny(lib):
     f = lambda e, kk: loop_trace(e, kk, c, params)  # noqa: E731
     assert torch.autograd.gradcheck(f, (eta, k), eps=1e-6, atol=1e-6, rtol=1e-5, fast_mode=True)
     c.close()
+
+
+def test_clover_argument_errors(lib):
+    """Non-finite c_sw is refused; -dM/dkappa with clover needs kappa != 0; A^-1 A is the identity
+    only where A exists, and c_sw = 0 leaves -dM/dkappa = D."""
+    dims = (4, 4, 4, 4)
+    U = synthetic.gauge_field(dims, eps=0.4, seed=56)
+    x = to_gpu(synthetic.random_spinor(dims, seed=57, n=1))
+    c = lib.Context(dims)
+    c.load_gauge(U)
+    for bad in (float("nan"), float("inf")):
+        with pytest.raises(lib.DlError) as e:
+            c.set_clover(bad)
+        assert e.value.status == 1
+    c.set_kappa(0.0)
+    c.set_clover(1.0)
+    with pytest.raises(lib.DlError) as e:
+        c.apply_dm_dkappa(x)
+    assert e.value.status == 1
+    c.set_clover(0.0)
+    assert torch.equal(c.apply_dm_dkappa(x), c.apply_hop(x))
+    c.close()
