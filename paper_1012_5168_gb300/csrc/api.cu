@@ -949,6 +949,11 @@ extern "C" int dl_get_timing(dl_ctx *c, dl_timing *out, int reset) {
 // ---------------------------------------------------------------------------
 // layout conversion
 // ---------------------------------------------------------------------------
+// Whole-lattice batches of width 16 to 64 convert tile by tile (fields.cuh).
+static bool tiled_conversion(const dl_ctx *c, int N, int cb0, int cb1, const int *tcol) {
+    return !tcol && cb0 == 0 && cb1 == c->Vh && N >= 16 && N <= CONV_TILE && c->Vh % (CONV_TILE / N) == 0;
+}
+
 static int canon_to_eo(dl_ctx *c, const double *canon, double *eo, int n, int N, int g5, int cb0, int cb1,
                        const int *tcol = nullptr) {
     ConvArgs a;
@@ -960,6 +965,14 @@ static int canon_to_eo(dl_ctx *c, const double *canon, double *eo, int n, int N,
     a.n = n;
     a.N = N;
     a.gamma5 = g5;
+    if (tiled_conversion(c, N, cb0, cb1, tcol)) {
+        const size_t smem = (size_t)2 * 12 * (CONV_TILE + CONV_TILE / N) * sizeof(double2);
+        const int grid = (int)std::min<long>(c->Vh / (CONV_TILE / N), (long)c->num_sms * 8);
+        canon_to_eo_tiled<<<grid, 256, smem, c->cur>>>(a, canon, eo);
+        c->kernel_launches++;
+        CK(cudaGetLastError());
+        return DL_OK;
+    }
     Launch l = make_launch(c, 2L * (cb1 - cb0) * N, 256, 0, 8);
     canon_to_eo_kernel<<<l.grid, l.block, 0, l.stream>>>(a, canon, eo);
     c->kernel_launches++;
@@ -978,6 +991,14 @@ static int eo_to_canon(dl_ctx *c, const double *eo, double *canon, int n, int N,
     a.n = n;
     a.N = N;
     a.gamma5 = g5;
+    if (tiled_conversion(c, N, cb0, cb1, tcol)) {
+        const size_t smem = (size_t)2 * 12 * (CONV_TILE + CONV_TILE / N) * sizeof(double2);
+        const int grid = (int)std::min<long>(c->Vh / (CONV_TILE / N), (long)c->num_sms * 8);
+        eo_to_canon_tiled<<<grid, 256, smem, c->cur>>>(a, eo, canon);
+        c->kernel_launches++;
+        CK(cudaGetLastError());
+        return DL_OK;
+    }
     Launch l = make_launch(c, 2L * (cb1 - cb0) * n, 256, 0, 8);
     eo_to_canon_kernel<<<l.grid, l.block, 0, l.stream>>>(a, eo, canon);
     c->kernel_launches++;

@@ -68,6 +68,69 @@ static __global__ void eo_to_canon_kernel(ConvArgs a, const double *eo, double *
     }
 }
 
+// Tiled conversions for whole-lattice batches (cb range [0, Vh), no per-column
+// timeslices) of width N >= 16.  A block moves one tile: the cb range
+// [cb0, cb0 + TS) of both parities, TS = 64 / N, which holds exactly the
+// lexicographic sites [2 cb0, 2 cb0 + 2 TS).  The EO side of a tile is one
+// contiguous run [TS][12][N] per parity and the canonical side one contiguous
+// run [2 TS][12] per right-hand side, so both sides are read and written in
+// coalesced runs, through shared memory [2][TS][12][N + 1] complex (the pad
+// keeps the column reads apart in the banks).  Site i = 2 cb0 + o has the
+// parity of o + y + z + t, since its x has the parity of i (L_x even).
+constexpr int CONV_TILE = 64;  // TS N
+__device__ __forceinline__ int lex_parity(int i, const Geom &g) {
+    const int R = i / g.L[0];                   // x-row: y + Ly (z + Lz t)
+    const int R2 = R / g.L[1], R3 = R2 / g.L[2];  // z + Lz t, t
+    return (i + R + R2 + R3) & 1;                 // x + y + z + t mod 2 (the extents are even)
+}
+static __global__ void __launch_bounds__(256) eo_to_canon_tiled(ConvArgs a, const double *eo, double *canon) {
+    extern __shared__ double2 cvt[];
+    const int N = a.N, TS = CONV_TILE / N, NP = N + 1, run = TS * 12 * N, per = 2 * TS * 12;
+    const int V = 2 * a.g.Vh;
+    for (int tile = blockIdx.x; tile < a.g.Vh / TS; tile += gridDim.x) {
+        const int cb0 = tile * TS;
+        for (int k = threadIdx.x; k < 2 * run; k += blockDim.x) {
+            const int p = k / run, r = k - p * run;  // r = (s 12 + c) N + j
+            cvt[(p * TS * 12 + r / N) * NP + r % N] =
+                reinterpret_cast<const double2 *>(eo)[((size_t)p * a.g.Vh + cb0) * 12 * N + r];
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < a.n * per; k += blockDim.x) {
+            const int j = k / per, q = k - j * per, o = q / 12, c = q - o * 12;
+            const int i = 2 * cb0 + o, p = lex_parity(i, a.g);
+            double2 v = cvt[(p * TS * 12 + (o >> 1) * 12 + c) * NP + j];
+            if (a.gamma5 && c >= 6) { v.x = -v.x; v.y = -v.y; }
+            reinterpret_cast<double2 *>(canon)[((size_t)j * V + i) * 12 + c] = v;
+        }
+        __syncthreads();
+    }
+}
+static __global__ void __launch_bounds__(256) canon_to_eo_tiled(ConvArgs a, const double *canon, double *eo) {
+    extern __shared__ double2 cvt[];
+    const int N = a.N, TS = CONV_TILE / N, NP = N + 1, run = TS * 12 * N, per = 2 * TS * 12;
+    const int V = 2 * a.g.Vh;
+    for (int tile = blockIdx.x; tile < a.g.Vh / TS; tile += gridDim.x) {
+        const int cb0 = tile * TS;
+        for (int k = threadIdx.x; k < N * per; k += blockDim.x) {
+            const int j = k / per, q = k - j * per, o = q / 12, c = q - o * 12;
+            const int i = 2 * cb0 + o, p = lex_parity(i, a.g);
+            double2 v = make_double2(0.0, 0.0);  // columns j >= n are zero
+            if (j < a.n) {
+                v = reinterpret_cast<const double2 *>(canon)[((size_t)j * V + i) * 12 + c];
+                if (a.gamma5 && c >= 6) { v.x = -v.x; v.y = -v.y; }
+            }
+            cvt[(p * TS * 12 + (o >> 1) * 12 + c) * NP + j] = v;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < 2 * run; k += blockDim.x) {
+            const int p = k / run, r = k - p * run;
+            reinterpret_cast<double2 *>(eo)[((size_t)p * a.g.Vh + cb0) * 12 * N + r] =
+                cvt[(p * TS * 12 + r / N) * NP + r % N];
+        }
+        __syncthreads();
+    }
+}
+
 // gauge: canonical [V][4][3][3] complex128 -> EO [2][Vh][4][9] complex in S
 template <typename S>
 static __global__ void gauge_reorder_kernel(const uint32_t *coords, Geom g, const double *canon, S *eo) {
