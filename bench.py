@@ -45,7 +45,7 @@ HOP_KIND_NAMES = {0: "hop_kernel_cap (direct)", 1: "hop_kernel_pf (cp.async pref
                   4: "hop_kernel_ws (warp-staged)", 5: "hop_kernel_mma (tensor cores)",
                   6: "hop_kernel_x2 (packed FP32)", 7: "hop_kernel_pair (paired layout)",
                   8: "hop_kernel_pair_cap (paired layout)", 9: "hop_kernel_ws_pair (paired, warp-staged)",
-                  10: "hop_kernel_cap (direct, wider register cap)"}
+                  10: "hop_kernel_cap (direct, wider register cap)", 11: "hop_kernel_ws (warp-staged, two stages)"}
 
 
 def parse():
@@ -104,7 +104,8 @@ def read_peaks():
 # kernel kind it covers is built from: its figures count only while those are unchanged.
 # Its per-launch DRAM lines are keyed by kind and hop: plain, r0dot, bicg.
 TRAFFIC_PROFILE = os.path.join("profiles", "hop_f32_fused_n32_16x16x16x32.md")
-TRAFFIC_SOURCES = {0: ["hop.cuh"], 4: ["hop.cuh", "hop_tma.cuh", "hop_ws.cuh"], 10: ["hop.cuh", "hop_launch.cuh"]}
+TRAFFIC_SOURCES = {0: ["hop.cuh"], 4: ["hop.cuh", "hop_tma.cuh", "hop_ws.cuh"], 10: ["hop.cuh", "hop_launch.cuh"],
+                   11: ["hop.cuh", "hop_tma.cuh", "hop_ws.cuh"]}
 
 
 def sources_sha(hop_kind: int):

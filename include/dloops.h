@@ -433,7 +433,8 @@ int dl_bench_hop(dl_ctx *ctx, int precision, int n_rhs, int fused, int reps,
  * 32 R), 6 packed FP32 arithmetic; on the paired FP32 layout
  * (DLOOPS_F32_PAIRS=1, even widths) 0, 7 and 8 (packed, uncapped and capped)
  * and 9 (packed, warp-staged; widths 32 and 64); 10 the direct FP32 kernel
- * under a wider register cap (R = 1).  Each candidate times three classes of
+ * under a wider register cap (R = 1); 11 warp-staged with two stages per warp
+ * (widths 32 R, twice the warps per SM of kind 4).  Each candidate times three classes of
  * hops on random fields: the plain hop (class 0), the fused hop with <rhat, v>
  * (class 1, which also serves the other fused hops) and the fused hop with the
  * five BiCGStab reductions (class 2), in two sweeps over all candidates, and
@@ -455,7 +456,7 @@ int dl_tune_hop(dl_ctx *ctx, int precision, int n_rhs, int force_R, int force_bl
  * be NULL).  No tuning, no GPU work.  Errors: DL_EINVAL. */
 int dl_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int cls, int *R_out, int *block_out, int *kind_out);
 /* Set that launch shape explicitly (R in {1, 2, 4}, block in {64, 128, 256},
- * kind as dl_tune_hop; kinds 3-5 and 9 take block 64 and size their own
+ * kind as dl_tune_hop; kinds 3-5, 9 and 11 take block 64 and size their own
  * blocks); the width then counts as tuned.  Errors: DL_EINVAL for a shape the
  * precision, width or storage layout does not allow. */
 int dl_set_hop_shape(dl_ctx *ctx, int precision, int n_rhs, int cls, int R, int block, int kind);

@@ -145,7 +145,7 @@ struct dl_ctx {
     int hop_kind[5][8][3];   // 0 direct, 1 cp.async prefetching, 2 bulk-copy staged, 3 blocked, 4 warp-staged,
                           // 5 tensor cores (BF16), 6 direct with packed FP32 arithmetic, 7 paired layout with
                           // packed FP32 arithmetic, 8 the same under a 128-register cap, 9 paired and
-                          // warp-staged, 10 direct under a wider register cap
+                          // warp-staged, 10 direct under a wider register cap, 11 warp-staged with two stages
     bool hop_tuned[5][8];
     bool autotune = true;
 };
@@ -462,13 +462,14 @@ static int time_hops(dl_ctx *c, int prec, int N, int reps, float *ms_out, int wh
 // right-hand sides per thread and B threads per block (bi: B's index in
 // {64, 128, 256}).
 static bool shape_ok(int prec, int N, int R, int B, int bi, int pf) {
-    if (pf < 0 || pf > 10 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
+    if (pf < 0 || pf > 11 || (prec == P_F64 && (pf != 0 || R != 1))) return false;
     if (pf == 10 && (prec != P_F32 || R != 1)) return false;       // wider-cap direct: FP32, one per thread
     if (prec == P_F32P ? (pf != 0 && (pf < 7 || pf > 9)) : (pf >= 7 && pf <= 9)) return false;  // paired: 0, 7-9
+    if (pf == 11 && prec == P_F32P) return false;
     if (R > N || B % (N / R)) return false;
     if (pf == 1 && 2 * pf_stage_bytes(prec, R) * B > 200 * 1024) return false;
-    if ((pf == 3 || pf == 4 || pf == 5) && bi > 0) return false;  // the launcher picks the block
-    if ((pf == 4 || pf == 5) && N != 32 * R) return false;         // one site per warp
+    if ((pf == 3 || pf == 4 || pf == 5 || pf == 11) && bi > 0) return false;  // the launcher picks the block
+    if ((pf == 4 || pf == 5 || pf == 11) && N != 32 * R) return false;         // one site per warp
     if (pf == 5 && (prec != P_BF16 || R > 2)) return false;         // tensor cores: BF16 storage
     if (pf == 6 && (prec != P_F32 || R != 1)) return false;         // packed FP32 arithmetic
     if (pf >= 7 && pf <= 9 && R != 2) return false;                 // paired layout: two per thread
@@ -497,7 +498,7 @@ static int tune_hop(dl_ctx *c, int prec, int N, int force_R, int force_block, in
     // shape timed while the GPU was still ramping its clocks or finishing other
     // work gets a second chance.
     for (int sweep = 0; sweep < 2; ++sweep)
-    for (int pf = 0; pf < (prec == P_F64 ? 1 : 11); ++pf) {
+    for (int pf = 0; pf < (prec == P_F64 ? 1 : 12); ++pf) {
         if (force_pf >= 0 && pf != force_pf) continue;
         for (int ri = 0; ri < 3; ++ri) {
             const int R = Rs[ri];

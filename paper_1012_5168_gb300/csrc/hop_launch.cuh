@@ -110,14 +110,14 @@ cudaError_t go_hop(const HopArgs &a, Launch &l, int kind) {
         direct<<<l.grid, l.block, l.smem, l.stream>>>(b);
         return cudaGetLastError();
     }
-    if (kind == 4) {  // warp-staged: one site per warp, so N = 32 R
+    if (kind == 4 || kind == 11) {  // warp-staged: one site per warp, so N = 32 R; kind 11 with two stages
         if (a.N != 32 * R) return cudaErrorInvalidValue;
-        static size_t opted = 0;
-        static std::mutex m;
-        auto kern = hop_kernel_ws<S, R, MODE, RED>;
+        static size_t opted = 0, opted2 = 0;
+        static std::mutex m, m2;
+        auto kern = kind == 4 ? hop_kernel_ws<S, R, MODE, RED> : hop_kernel_ws<S, R, MODE, RED, 2>;
         l.block = WS_WARPS * 32;
-        l.smem = WsShape<S, R>::WB * WS_WARPS;
-        const cudaError_t e = opt_in_smem(kern, l.smem, opted, m);
+        l.smem = (kind == 4 ? WsShape<S, R>::WB : WsShape<S, R, 2>::WB) * WS_WARPS;
+        const cudaError_t e = kind == 4 ? opt_in_smem(kern, l.smem, opted, m) : opt_in_smem(kern, l.smem, opted2, m2);
         if (e != cudaSuccess) return e;
         const int res = resident_blocks(kern, l.block, l.smem);
         l.grid = (l.num_sms > 0 ? l.num_sms : 1) * (res < 16 ? res : 16);

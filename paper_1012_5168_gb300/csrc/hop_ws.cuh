@@ -30,13 +30,16 @@ namespace dl {
 
 constexpr int WS_WARPS = 4;  // warps per block of the warp-staged hop
 
-// Stages per warp: enough blocks in flight to cover the memory latency, small
-// enough that four 4-warp blocks fit in one SM's shared memory.
-template <typename S, int R>
+// Stages per warp (NSTO = 0): enough blocks in flight to cover the memory
+// latency, small enough that four 4-warp blocks fit in one SM's shared memory.
+// NSTO = 2 (kernel kind 11) keeps one copy in flight and so fits about twice
+// the warps per SM: on GB300 that runs the fused hops faster (their epilogue
+// loads gain from the extra warps) and the plain hop slower.
+template <typename S, int R, int NSTO = 0>
 struct WsShape {
     static constexpr uint32_t SB = 12u * 32u * R * cbytes<S>();  // one neighbour block [12][N]
     static constexpr uint32_t LB = 8u * 9u * cbytes<S>();        // one site's eight links
-    static constexpr int NST = SB <= 1536 ? 6 : (SB <= 3072 ? 4 : 3);
+    static constexpr int NST = NSTO ? NSTO : (SB <= 1536 ? 6 : (SB <= 3072 ? 4 : 3));
     static constexpr size_t WB = 64 + (size_t)NST * SB + 2 * (size_t)LB;  // bytes per warp
 };
 
@@ -58,10 +61,10 @@ __device__ __forceinline__ int nbr_of_dir(const Site &s, const Geom &g, int d) {
     return i >> 1;
 }
 
-template <typename S, int R, int MODE, int RED>
+template <typename S, int R, int MODE, int RED, int NSTO = 0>
 __global__ void __launch_bounds__(WS_WARPS * 32) hop_kernel_ws(HopArgs A) {
     typedef typename Real<S>::type T;
-    typedef WsShape<S, R> W;
+    typedef WsShape<S, R, NSTO> W;
     constexpr int N = 32 * R;
     constexpr int NST = W::NST;
     constexpr int NV = RedCount<RED>::n > 0 ? RedCount<RED>::n : 1;
@@ -207,8 +210,9 @@ __global__ void __launch_bounds__(WS_WARPS * 32) hop_kernel_ws(HopArgs A) {
     if (lane == 0)
         for (int i = 0; i < NST; ++i) mbar_inval(full + i);
     if (RED != RED_NONE) {
-        // Every warp's copies have landed: the reduction reuses warp 0's staging
-        // memory (WS_WARPS * 32 * R * NV complex, below one warp's NST * SB bytes).
+        // Every warp's copies have landed and its barriers are retired: the
+        // reduction reuses the staging memory from byte 64 on (WS_WARPS * 32 * R *
+        // NV complex, at most 10 kB, below the WS_WARPS * WB bytes of the block).
         __syncthreads();
         block_reduce<R, NV, T>(red, 32, N, A.partials, smem + 64);
     }

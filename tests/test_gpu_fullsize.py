@@ -84,7 +84,7 @@ def test_low_precision_hop_error_every_kernel(lib, prec, pairs, monkeypatch):
     exact = c.apply_hop(to_gpu(psi)).cpu().numpy()  # the FP64 hop of the same context
     assert hop_error(exact, ref) < 1e-14
     # the warp-staged kernels serve widths 32 and 64 only; kind 5 (tensor cores) BF16 only
-    for kind in ((7, 8, 9) if paired else ((4, 5) if prec == 2 else (4, 6))):
+    for kind in ((7, 8, 9) if paired else ((4, 5, 11) if prec == 2 else (4, 6, 11))):
         for n in (32, 64):
             wide = synthetic.random_spinor(dims, seed=43, n=n)
             ref_w = wilson.hop(U, wide, -1.0)

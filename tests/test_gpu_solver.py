@@ -201,7 +201,7 @@ def test_hop_kernel_kinds(lib, prec, kind, batch, monkeypatch):
     c.close()
 
 
-@pytest.mark.parametrize("prec, kind", [(1, 4), (2, 4), (2, 5), (1, 6), (1, 7), (1, 8), (1, 9)])
+@pytest.mark.parametrize("prec, kind", [(1, 4), (2, 4), (2, 5), (1, 6), (1, 7), (1, 8), (1, 9), (1, 11), (2, 11)])
 @pytest.mark.parametrize("batch", [32, 64])
 def test_warp_staged_hop_solves(lib, prec, kind, batch, monkeypatch):
     """The warp-staged hops (one site per warp, N = 32 R: kind 4 on the CUDA cores, kind 5 on the
@@ -233,7 +233,7 @@ def test_hop_kernel_kinds_full_size(lib, monkeypatch):
     w = synthetic.WORKLOADS["wilson_16x16x16x32"]
     U = synthetic.gauge_field(w["dims"], w["eps"], w["seed"])
     sols = []
-    for pairs, kinds in (("0", (0, 1, 2, 3, 4, 10)), ("1", (0, 7, 8, 9))):
+    for pairs, kinds in (("0", (0, 1, 2, 3, 4, 10, 11)), ("1", (0, 7, 8, 9))):
         monkeypatch.setenv("DLOOPS_F32_PAIRS", pairs)
         c = lib.Context(w["dims"])
         c.load_gauge(U)
