@@ -3,6 +3,8 @@
 
 namespace dl {
 
+// The link U_mu at (x, y, z, t), coordinates taken modulo the extents, from the
+// FP64 field in even-odd site order [2][Vh][4][9].
 __device__ __forceinline__ void m3_load(const double2 *g64, const Geom &g, int x, int y, int z, int t, int mu,
                                         cx<double> (&u)[9]) {
     x = (x + g.L[0]) % g.L[0];
@@ -15,7 +17,8 @@ __device__ __forceinline__ void m3_load(const double2 *g64, const Geom &g, int x
 #pragma unroll
     for (int k = 0; k < 9; ++k) u[k] = mk(src[k].x, src[k].y);
 }
-// c = a b, a^dag b, a b^dag
+// c = op(a) op(b) for 3 x 3 complex matrices, op the conjugate transpose where
+// DA (for a) or DB (for b) is set.
 template <bool DA, bool DB>
 __device__ __forceinline__ void m3_mul(const cx<double> (&a)[9], const cx<double> (&b)[9], cx<double> (&c)[9]) {
 #pragma unroll
